@@ -1,0 +1,312 @@
+"""Benchmark: SSSP in DAIC form on a seeded R-MAT graph (scale 20, edge factor
+16, uint32 weights uniform in [1, 255]), 8 sources run one after another, every
+run to the exact fixed point (no pending vertex).  One step = the 8 sources.
+
+Metric: GTEPS = (sources x m) / device time of the step, with the graph
+resident in HBM.  Beside it: time to solution per source, GTEPS over the edge
+pushes actually performed, the push kernel's fraction of the measured HBM
+copy bandwidth, an end-to-end figure through the C ABI from pinned host
+buffers, and the CPU oracle (Dijkstra, one core) on the machine's host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun): the sources are independent problems, so each rank runs
+its own 8 sources on its own copy of the graph (weak scaling, no collective on
+the data path; a barrier and a max over ranks frame the timing).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen  # noqa: E402
+
+METRIC = "GTEPS and time-to-tolerance (1e-6 / exact) vs plain form, % of HBM roofline"
+SCALE, EF, NSRC = 20, 16, 8
+# algorithmic bytes of the SSSP push kernel (an atomic read-modify-write counts
+# as a read plus a write):
+#   per edge push:      4 B target + 4 B weight + 8 B Delta_k RMW       = 16 B
+#   per updated vertex: 8 B row offsets + 8 B Delta_j + 8 B v_j RMW     = 24 B
+BYTES_PER_EDGE = 16
+BYTES_PER_VERTEX = 24
+L2_FLUSH_BYTES = 256 << 20
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(g, sources, budget_s=25.0):
+    """The oracle as it stands (Dijkstra, binary heap, one core) on a bounded
+    sample of the same workload: as many of the sources as fit the budget."""
+    import oracle
+    oracle.dijkstra(g, int(sources[0]))  # load the library, warm the caches
+    t0 = time.perf_counter()
+    done = 0
+    for s in sources:
+        oracle.dijkstra(g, int(s))
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done * g.m / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"Dijkstra from {done} of the {len(sources)} sources on the full "
+                      f"R-MAT scale-{SCALE} graph ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, one bounded sample of the workload per step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    g = graphgen.rmat(SCALE, EF, weights=True)
+    sources = graphgen.sssp_sources(g, NSRC)
+    for k in range(args.warmup):
+        oracle.dijkstra(g, int(sources[k % NSRC]))
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.dijkstra(g, int(sources[k % NSRC]))
+    dt = time.perf_counter() - t0
+    value = args.steps * g.m / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"sssp-rmat{SCALE}-ef{EF}", "sources_per_step": 1,
+                   "n": g.n, "m": g.m},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": "Dijkstra from one source of the full graph per step"},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import paper_1710_05785_b300 as mt
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    g = graphgen.rmat(SCALE, EF, weights=True)
+    all_src = graphgen.sssp_sources(g, NSRC * world)
+    sources = [int(s) for s in all_src[rank * NSRC:(rank + 1) * NSRC]]
+    rp_d = torch.from_numpy(g.row_ptr).to(dev)
+    col_d = torch.from_numpy(g.col).to(dev)
+    w_d = torch.from_numpy(g.w.view(np.int32)).to(dev)
+    G = mt.Graph(rp_d, col_d, w_d, device=local)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    res = [None]
+    stats = []
+
+    def step(record=False):
+        for s in sources:
+            res[0] = mt.run(G, mt.OP_MIN_U32, source=s, result=res[0],
+                            stream=stream.cuda_stream)
+            if record:
+                stats.append(res[0].stats())
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k)                      # evict the graph from L2 between steps
+            ev[k][0].record(stream)
+            step(record=True)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    edges_per_step = NSRC * g.m * world
+    value = edges_per_step / (ms_per_step * 1e-3) / 1e9
+
+    # kernel-level roofline: the same 8 runs with per-kernel events
+    prof = []
+    for s in sources:
+        r = mt.run(G, mt.OP_MIN_U32, source=s, flags=mt.FLAG_PROFILE_KERNELS,
+                   stream=stream.cuda_stream)
+        prof.append(r.stats())
+        r.close()
+    push_ms = sum(p["push_ms"] for p in prof)
+    push_launches = sum(p["push_launches"] for p in prof)
+    alg_bytes = sum(BYTES_PER_EDGE * p["edge_pushes"] + BYTES_PER_VERTEX * p["activations"]
+                    for p in prof)
+    peaks, peak_kind = measured_peaks()
+    achieved = alg_bytes / (push_ms * 1e-3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get("k_push_sssp_rmat20")
+    except (OSError, ValueError):
+        pass
+
+    # end to end through the C ABI from pinned host buffers, per step:
+    # upload the CSR, run the 8 sources, read every distance vector back
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    w_h = torch.from_numpy(g.w.view(np.int32)).pin_memory()
+    out_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    h2d = rp_h.numel() * 8 + col_h.numel() * 4 + w_h.numel() * 4
+    d2h = NSRC * g.n * 4
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        Gh = mt.Graph(rp_h, col_h, w_h, device=local)
+        rr = None
+        for s in sources:
+            rr = mt.run(Gh, mt.OP_MIN_U32, source=s, result=rr, stream=stream.cuda_stream)
+            rr.state(out_h)
+        rr.close()
+        Gh.close()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / max(e2e_steps, 1)
+    e2e_value = NSRC * g.m * world / e2e_s / 1e9 if e2e_steps else None
+
+    launches = sum(s["kernel_launches"] for s in stats) + args.steps  # + the L2 flush fill
+    tts = [s["elapsed_ms"] for s in stats]
+    line = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"sssp-rmat{SCALE}-ef{EF}-{NSRC}src", "n": g.n, "m": g.m,
+                   "sources_per_rank": NSRC, "weights": "u32 uniform [1,255]",
+                   "engine": "sync (CUDA graph, device-side WHILE)", "sched": "all pending",
+                   "l2": f"{L2_FLUSH_BYTES >> 20} MiB write between steps (outside the events)",
+                   "parallelism": f"independent sources x{world}"},
+        "time_to_solution_ms": {"mean": float(np.mean(tts)), "max": float(np.max(tts))},
+        "gteps_work": float(sum(s["edge_pushes"] for s in stats) / (total_ms * 1e-3) / 1e9),
+        "rounds_per_source": float(np.mean([s["rounds"] for s in stats])),
+        "roofline": {"bound": "hbm", "kernel": "k_push<OpMinU32>", "achieved": achieved,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "push_launches": push_launches,
+                     "push_ms_per_launch": push_ms / max(push_launches, 1),
+                     "alg_bytes_per_launch": alg_bytes / max(push_launches, 1)},
+        "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "wall_s_timed": t_wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, sources)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * maiter.h - C ABI of a single-GPU (B300, sm_103a) engine for delta-based
+ * accumulative iterative computation (DAIC), after "Maiter: An Asynchronous
+ * Graph Processing Framework for Delta-based Accumulative Iterative
+ * Computation" (Zhang, Gao, Gao, Wang).
+ *
+ * What the engine computes.  A DAIC is the tuple (g_{j,k}, (+), v0, Delta1)
+ * (Section 4.1, Table 1).  Each activated vertex j performs the update of the
+ * asynchronous DAIC (Eq. 5):
+ *     v_j <- v_j (+) Delta_j;
+ *     for every out-edge (j, k): Delta_k <- Delta_k (+) g_{j,k}(Delta_j),
+ *         skipped when the message equals the identity 0 of (+);
+ *     Delta_j <- 0.
+ * Vertices are activated by a scheduling policy (Section 3.5): all pending
+ * vertices (round-robin), those above a threshold, or a top fraction by
+ * priority |v_j (+) Delta_j - v_j|.  The run stops when the termination test
+ * of Section 5.1 holds: sum_j |Delta_j| < eps for (+) = +, no pending vertex
+ * for (+) = min.  By Theorems 1 and 3 the result is the fixed point of the
+ * plain iteration v = f(v) (Eq. 1) whatever the schedule.
+ *
+ * Only (+, g) pairs that satisfy the four DAIC conditions of Section 3.1 are
+ * offered: + with a linear g, and min with g(x) = x + w.  No user callbacks
+ * cross this boundary.
+ *
+ * Conventions for every call:
+ *  - Every call returns a maiter_status (0 = success) and never aborts; on
+ *    failure maiter_last_error() returns a message (thread-local).
+ *  - Array arguments may be host or device pointers; the kind is detected
+ *    with cudaPointerGetAttributes.  Inputs are copied; the caller keeps
+ *    ownership of everything it passes.
+ *  - Graph layout: CSR of OUT-edges.  row_ptr[n+1] (int64, row_ptr[0] = 0,
+ *    non-decreasing, row_ptr[n] = m), col[m] (int32, 0 <= col < n), optional
+ *    w[m] (uint32 edge weights).  Multi-edges and self-loops are allowed.
+ *    Limits: n < 2^31, m < 2^31.
+ *  - The engine runs on the device given at maiter_graph_create and on the
+ *    stream given in the run parameters; calls are synchronous w.r.t. the
+ *    host (they return after the device work they issued has finished),
+ *    except where stated.
+ */
+#ifndef MAITER_H
+#define MAITER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct maiter_graph maiter_graph;    /* opaque: device copy of the CSR */
+typedef struct maiter_result maiter_result;  /* opaque: device v, Delta, workspace, stats */
+
+typedef enum {
+  MAITER_OK = 0,
+  MAITER_ERR_INVALID_ARG = -1,   /* bad pointer, size, enum, CSR or value */
+  MAITER_ERR_OOM = -2,           /* device or pinned allocation failed */
+  MAITER_ERR_CUDA = -3,          /* a CUDA call failed; message has details */
+  MAITER_ERR_NOT_CONVERGED = -4, /* max_rounds reached; state is readable */
+  MAITER_ERR_TIMEOUT = -5,       /* a bounded device wait ran out; state readable */
+  MAITER_ERR_UNSUPPORTED = -6    /* valid request this build does not serve */
+} maiter_status;
+
+/* The accumulation operator (+) and the precision of each field. */
+typedef enum {
+  MAITER_OP_SUM_F64 = 0,   /* (+) = +; v, Delta, coefficients, residual FP64 */
+  MAITER_OP_SUM_MIXED = 1, /* (+) = +; Delta and coefficients FP32, v and the
+                              residual reduction FP64 */
+  MAITER_OP_MIN_U32 = 2    /* (+) = min over uint32, identity UINT32_MAX (inf) */
+} maiter_op;
+
+/* The message function g_{j,k}. */
+typedef enum {
+  MAITER_G_SCALE_BY_SRC = 0, /* g_{j,k}(x) = coef[j] * x.  With coef == NULL,
+                                coef[j] = damping / outdeg(j) (PageRank,
+                                Section 4.2, sender's out-degree). */
+  MAITER_G_ADD_EDGE = 1      /* g_{j,k}(x) = x + w[e] (SSSP, Table 1), saturating
+                                at UINT32_MAX; needs edge weights */
+} maiter_g;
+
+/* Which vertices an iteration activates (Section 3.5, Section 5.1). */
+typedef enum {
+  MAITER_SCHED_ALL = 0,       /* every vertex with a pending delta
+                                 (Delta_j != 0 for +, Delta_j < v_j for min) */
+  MAITER_SCHED_THRESHOLD = 1, /* +: |Delta_j| > threshold; min: as ALL */
+  MAITER_SCHED_TOPFRAC = 2    /* the top_frac fraction of pending vertices by
+                                 priority, ties included (priority queue of
+                                 Section 5.1) */
+} maiter_sched;
+
+typedef enum {
+  MAITER_ENGINE_SYNC = 0      /* round loop: frontier, then push; the loop and its
+                                 termination test run on the device (CUDA graph
+                                 with a conditional node), no host round trip */
+} maiter_engine;
+
+/* Run flags (bit set). */
+typedef enum {
+  MAITER_FLAG_PROFILE_KERNELS = 1  /* drive the round loop from the host, one
+                                      launch per kernel with CUDA events around
+                                      each, and report per-kernel device time in
+                                      maiter_stats (same kernels and launch
+                                      shapes; one host sync per round) */
+} maiter_flags;
+
+typedef struct maiter_run_params {
+  int32_t op;          /* maiter_op */
+  int32_t g;           /* maiter_g; must be SCALE_BY_SRC for sums, ADD_EDGE for min */
+  int32_t sched;       /* maiter_sched */
+  int32_t engine;      /* maiter_engine */
+  int32_t flags;       /* maiter_flags */
+  int32_t reserved0;   /* must be 0 */
+  const void* coef;    /* n per-source coefficients (double for SUM_F64, float for
+                          SUM_MIXED), host or device, or NULL (see damping) */
+  double damping;      /* d in coef[j] = d / outdeg(j) when coef == NULL */
+  const void* v0;      /* n initial states (double for sums, uint32 for min), or
+                          NULL: the identity (0 for +, UINT32_MAX for min) */
+  const void* delta0;  /* n initial deltas (double / float / uint32), or NULL:
+                          1 - damping everywhere for sums (PageRank, Table 1),
+                          0 at `source` and UINT32_MAX elsewhere for min */
+  int64_t source;      /* min with delta0 == NULL: the source vertex */
+  double threshold;    /* THRESHOLD: activate |Delta_j| > threshold.  When a
+                          round selects nothing while the residual is still
+                          >= eps, the threshold is divided by 10 (down to 0) so
+                          every run terminates. */
+  double top_frac;     /* TOPFRAC: fraction q in (0, 1] */
+  double eps;          /* sums: stop when sum_j |Delta_j| < eps (FP64 reduction) */
+  int64_t max_rounds;  /* round cap; <= 0 means 1,000,000 */
+  int64_t timeout_ms;  /* reserved for bounded device waits; 0 = default */
+  void* stream;        /* cudaStream_t to run on; NULL = the default stream */
+} maiter_run_params;
+
+typedef struct maiter_stats {
+  int64_t rounds;        /* frontier/push rounds executed */
+  int64_t activations;   /* vertex updates performed */
+  int64_t edge_pushes;   /* messages sent (sum of out-degrees of updated vertices) */
+  double residual;       /* final sum_j |Delta_j| (sums) or pending count (min) */
+  double elapsed_ms;     /* device time of the run (CUDA events) */
+  int32_t status;        /* maiter_status of the run */
+  int32_t converged;     /* 1 if the termination test held */
+  int64_t kernel_launches; /* kernels this run launched */
+  /* Filled only under MAITER_FLAG_PROFILE_KERNELS (else 0): */
+  double push_ms;        /* summed device time of the push (update+scatter) kernel */
+  double scan_ms;        /* summed device time of the frontier/termination kernel */
+  int64_t push_launches;
+  int64_t scan_launches;
+} maiter_stats;
+
+/* Fills *p with defaults: PageRank-style sum in FP64, d = 0.8, sched ALL,
+ * eps = 1e-8, threshold = 0, top_frac = 0.01, source = -1, max_rounds 1e6. */
+void maiter_params_default(maiter_run_params* p);
+
+/* Uploads and validates a CSR of out-edges (layout above) on `device`.
+ * w may be NULL (no weights; min runs then fail with INVALID_ARG).
+ * On success *out owns device copies; free with maiter_graph_destroy.
+ * Errors: INVALID_ARG (sizes, ordering, col range), OOM, CUDA. */
+maiter_status maiter_graph_create(int64_t n, int64_t m, const int64_t* row_ptr,
+                                  const int32_t* col, const uint32_t* w, int device,
+                                  maiter_graph** out);
+
+void maiter_graph_destroy(maiter_graph* g);
+
+/* Runs a DAIC to termination (Eq. 5 updates, Section 3.5 schedules).
+ * If *out is NULL a new result is allocated; otherwise *out must be a result
+ * earlier returned for this graph and is reused without allocation (its
+ * previous state is overwritten).  The result is left readable on every
+ * return except INVALID_ARG/OOM, including NOT_CONVERGED.
+ * Errors: INVALID_ARG, OOM, CUDA, NOT_CONVERGED, UNSUPPORTED. */
+maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p,
+                         maiter_result** out);
+
+/* Copies the n states v into `out` (host or device): double for sums, uint32
+ * for min.  count must equal n. */
+maiter_status maiter_get_state(const maiter_result* r, void* out, int64_t count);
+
+/* Copies the n pending deltas Delta into `out`: double (SUM_F64), float
+ * (SUM_MIXED) or uint32 (min).  count must equal n. */
+maiter_status maiter_get_delta(const maiter_result* r, void* out, int64_t count);
+
+maiter_status maiter_get_stats(const maiter_result* r, maiter_stats* out);
+
+void maiter_result_destroy(maiter_result* r);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* maiter_last_error(void);
+
+/* Library version string. */
+const char* maiter_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAITER_H */

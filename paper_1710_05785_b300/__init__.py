@@ -1,0 +1,275 @@
+"""Python binding of libmaiter, the B300 (sm_103a) engine for delta-based
+accumulative iterative computation (DAIC).
+
+Argument marshalling only: every step of a run executes in the CUDA kernels of
+``libmaiter.so`` behind the C ABI declared in ``include/maiter.h``.  There is
+no CPU fallback; if the library is missing or no GPU is present, calls raise.
+
+Arrays may be numpy arrays (host memory) or CUDA tensors (device memory, any
+object with ``data_ptr()``); the library detects the pointer kind itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmaiter.so")
+
+# maiter_status
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_OOM = -2
+ERR_CUDA = -3
+ERR_NOT_CONVERGED = -4
+ERR_TIMEOUT = -5
+ERR_UNSUPPORTED = -6
+_STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CONVERGED",
+                 -5: "TIMEOUT", -6: "UNSUPPORTED"}
+
+# maiter_op / maiter_g / maiter_sched / maiter_engine
+OP_SUM_F64, OP_SUM_MIXED, OP_MIN_U32 = 0, 1, 2
+G_SCALE_BY_SRC, G_ADD_EDGE = 0, 1
+SCHED_ALL, SCHED_THRESHOLD, SCHED_TOPFRAC = 0, 1, 2
+ENGINE_SYNC = 0
+FLAG_PROFILE_KERNELS = 1
+
+INF32 = 0xFFFFFFFF
+
+_STATE_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float64, OP_MIN_U32: np.uint32}
+_DELTA_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float32, OP_MIN_U32: np.uint32}
+_COEF_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float32}
+
+
+class RunParams(ctypes.Structure):
+    """Mirror of ``maiter_run_params``."""
+    _fields_ = [
+        ("op", ctypes.c_int32), ("g", ctypes.c_int32), ("sched", ctypes.c_int32),
+        ("engine", ctypes.c_int32), ("flags", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("coef", ctypes.c_void_p), ("damping", ctypes.c_double),
+        ("v0", ctypes.c_void_p), ("delta0", ctypes.c_void_p),
+        ("source", ctypes.c_int64),
+        ("threshold", ctypes.c_double), ("top_frac", ctypes.c_double), ("eps", ctypes.c_double),
+        ("max_rounds", ctypes.c_int64), ("timeout_ms", ctypes.c_int64),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class Stats(ctypes.Structure):
+    """Mirror of ``maiter_stats``."""
+    _fields_ = [
+        ("rounds", ctypes.c_int64), ("activations", ctypes.c_int64),
+        ("edge_pushes", ctypes.c_int64), ("residual", ctypes.c_double),
+        ("elapsed_ms", ctypes.c_double), ("status", ctypes.c_int32),
+        ("converged", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
+        ("push_ms", ctypes.c_double), ("scan_ms", ctypes.c_double),
+        ("push_launches", ctypes.c_int64), ("scan_launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class MaiterError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"maiter {_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libmaiter.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libmaiter.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        L.maiter_graph_create.argtypes = [i64, i64, P, P, P, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_void_p)]
+        L.maiter_graph_create.restype = i32
+        L.maiter_graph_destroy.argtypes = [P]
+        L.maiter_run.argtypes = [P, ctypes.POINTER(RunParams), ctypes.POINTER(ctypes.c_void_p)]
+        L.maiter_run.restype = i32
+        L.maiter_get_state.argtypes = [P, P, i64]
+        L.maiter_get_state.restype = i32
+        L.maiter_get_delta.argtypes = [P, P, i64]
+        L.maiter_get_delta.restype = i32
+        L.maiter_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+        L.maiter_get_stats.restype = i32
+        L.maiter_result_destroy.argtypes = [P]
+        L.maiter_params_default.argtypes = [ctypes.POINTER(RunParams)]
+        L.maiter_last_error.restype = ctypes.c_char_p
+        L.maiter_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().maiter_last_error().decode()
+
+
+def _check(status: int, allow=(OK,)):
+    if status not in allow:
+        raise MaiterError(status, last_error())
+    return status
+
+
+def _addr(x):
+    """Raw address of a host numpy array or a device tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_contiguous") and not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _as(x, dtype, n, name):
+    """Host arrays are converted to the exact dtype; device tensors are checked."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray) or isinstance(x, (list, tuple)):
+        a = np.ascontiguousarray(x, dtype=dtype)
+        if a.shape != (n,):
+            raise ValueError(f"{name} must have shape ({n},)")
+        return a
+    if hasattr(x, "element_size"):
+        if x.numel() != n or x.element_size() != np.dtype(dtype).itemsize:
+            raise ValueError(f"{name}: need {n} elements of {np.dtype(dtype).name}")
+    return x
+
+
+def params_default() -> RunParams:
+    p = RunParams()
+    lib().maiter_params_default(ctypes.byref(p))
+    return p
+
+
+class Graph:
+    """``maiter_graph``: a device copy of a CSR of out-edges."""
+
+    def __init__(self, row_ptr, col, w=None, device: int = 0):
+        n = int(len(row_ptr)) - 1
+        if isinstance(row_ptr, np.ndarray) or isinstance(row_ptr, (list, tuple)):
+            row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        if isinstance(col, np.ndarray) or isinstance(col, (list, tuple)):
+            col = np.ascontiguousarray(col, dtype=np.int32)
+        if w is not None and (isinstance(w, np.ndarray) or isinstance(w, (list, tuple))):
+            w = np.ascontiguousarray(w, dtype=np.uint32)
+        m = int(len(col))
+        h = ctypes.c_void_p()
+        _check(lib().maiter_graph_create(n, m, _addr(row_ptr), _addr(col), _addr(w), device,
+                                         ctypes.byref(h)))
+        self.handle = h
+        self.n, self.m, self.device = n, m, device
+        self.weighted = w is not None
+
+    @classmethod
+    def from_csr(cls, g, device: int = 0):
+        """From any object with row_ptr, col and (optional) w attributes."""
+        return cls(g.row_ptr, g.col, getattr(g, "w", None), device)
+
+    def close(self):
+        if self.handle:
+            lib().maiter_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Result:
+    """``maiter_result``: device v and Delta of a run, plus its statistics."""
+
+    def __init__(self, handle, graph: Graph, op: int):
+        self.handle = handle
+        self.graph = graph
+        self.op = op
+
+    def state(self, out=None):
+        """v (float64 for sums, uint32 for min); into ``out`` if given."""
+        if out is None:
+            out = np.empty(self.graph.n, dtype=_STATE_DTYPE[self.op])
+        _check(lib().maiter_get_state(self.handle, _addr(out), self.graph.n))
+        return out
+
+    def delta(self, out=None):
+        """Delta (float64 / float32 / uint32 by op); into ``out`` if given."""
+        if out is None:
+            out = np.empty(self.graph.n, dtype=_DELTA_DTYPE[self.op])
+        _check(lib().maiter_get_delta(self.handle, _addr(out), self.graph.n))
+        return out
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().maiter_get_stats(self.handle, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if self.handle:
+            lib().maiter_result_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def run(graph: Graph, op: int = OP_SUM_F64, *, coef=None, damping: float = 0.8, v0=None,
+        delta0=None, source: int = -1, sched: int = SCHED_ALL, threshold: float = 0.0,
+        top_frac: float = 0.01, eps: float = 1e-8, max_rounds: int = 1000000,
+        timeout_ms: int = 0, stream=None, engine: int = ENGINE_SYNC, flags: int = 0,
+        result: Result | None = None, allow_not_converged: bool = False) -> Result:
+    """``maiter_run``: one DAIC run to termination.  ``stream`` is a raw
+    cudaStream_t handle (e.g. ``torch.cuda.current_stream().cuda_stream``)."""
+    n = graph.n
+    p = params_default()
+    p.op = op
+    p.g = G_ADD_EDGE if op == OP_MIN_U32 else G_SCALE_BY_SRC
+    p.sched, p.engine, p.flags = sched, engine, flags
+    keep = []
+    if coef is not None:
+        coef = _as(coef, _COEF_DTYPE[op], n, "coef")
+        keep.append(coef)
+        p.coef = _addr(coef)
+    p.damping = damping
+    if v0 is not None:
+        v0 = _as(v0, _STATE_DTYPE[op], n, "v0")
+        keep.append(v0)
+        p.v0 = _addr(v0)
+    if delta0 is not None:
+        delta0 = _as(delta0, _DELTA_DTYPE[op], n, "delta0")
+        keep.append(delta0)
+        p.delta0 = _addr(delta0)
+    p.source = source
+    p.threshold, p.top_frac, p.eps = threshold, top_frac, eps
+    p.max_rounds, p.timeout_ms = max_rounds, timeout_ms
+    p.stream = stream
+    h = ctypes.c_void_p(result.handle.value if result is not None else None)
+    allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
+    st = lib().maiter_run(graph.handle, ctypes.byref(p), ctypes.byref(h))
+    if result is None and h.value:
+        result = Result(h, graph, op)
+    _check(st, allow)
+    return result
+
+
+def version() -> str:
+    return lib().maiter_version().decode()

@@ -1,0 +1,85 @@
+// Host-side internals shared by the translation units of libmaiter.
+#pragma once
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/maiter.h"
+#include "daic_kernels.cuh"
+
+namespace maiter {
+
+void set_error(const char* fmt, ...);
+
+#define MAITER_CUDA(call)                                                              \
+  do {                                                                                 \
+    cudaError_t err_ = (call);                                                         \
+    if (err_ != cudaSuccess) {                                                         \
+      ::maiter::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(err_),    \
+                          __FILE__, __LINE__);                                         \
+      return err_ == cudaErrorMemoryAllocation ? MAITER_ERR_OOM : MAITER_ERR_CUDA;     \
+    }                                                                                  \
+  } while (0)
+
+#define MAITER_REQUIRE(cond, ...)                     \
+  do {                                                \
+    if (!(cond)) {                                    \
+      ::maiter::set_error(__VA_ARGS__);               \
+      return MAITER_ERR_INVALID_ARG;                  \
+    }                                                 \
+  } while (0)
+
+// Restores the calling thread's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool is_device_pointer(const void* p);
+
+// Degree cut-offs of the push kernel's three granularities and launch shape.
+struct Tuning {
+  int cut_warp = 32;    // out-degree below this: warp-gathered small path
+  int cut_cta = 2048;   // out-degree at or above this: one CTA per vertex
+  int push_blocks_per_sm = 0;   // 0 = occupancy maximum
+  int scan_blocks_per_sm = 4;
+};
+
+}  // namespace maiter
+
+struct maiter_graph {
+  int device = 0;
+  int64_t n = 0, m = 0;
+  int* rp = nullptr;           // n + 1 int32 offsets
+  int* col = nullptr;          // m targets
+  uint32_t* w = nullptr;       // m weights or null
+  int num_sms = 0;
+};
+
+struct maiter_result {
+  const maiter_graph* g = nullptr;
+  int op = -1;
+  int64_t n = 0;
+  void* v = nullptr;           // n x V
+  void* delta = nullptr;       // n x D
+  void* coef = nullptr;        // n x C (allocated on first use)
+  int* list[maiter::kBuckets] = {nullptr, nullptr, nullptr};
+  maiter::DevCtl* ctl = nullptr;
+  maiter::DevCtl* h_ctl = nullptr;   // pinned mirror
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // cached executable graph of the round loop
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t exec_key = 0;
+  maiter_stats stats{};
+};

@@ -1,0 +1,517 @@
+// C ABI of libmaiter: graph upload and validation, result management, and the
+// round-synchronous engine whose round loop is a CUDA graph with a device-side
+// WHILE condition.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace maiter {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+bool is_device_pointer(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------ graph validation
+
+// Checks the CSR and narrows row_ptr to int32.  Bit 0: row_ptr[0] != 0 or not
+// non-decreasing or row_ptr[n] != m; bit 1: a target outside [0, n).
+__global__ void k_validate_rowptr(const int64_t* __restrict__ rp64, int64_t n, int64_t m,
+                                  int* __restrict__ rp32, unsigned* flag) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i <= n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t x = rp64[i];
+    bool bad = x < 0 || x > m;
+    if (i == 0) bad |= (x != 0);
+    if (i == n) bad |= (x != m);
+    if (i < n) bad |= (rp64[i + 1] < x);
+    if (bad) atomicOr(flag, 1u);
+    rp32[i] = static_cast<int>(x);
+  }
+}
+
+__global__ void k_validate_col(const int* __restrict__ col, int64_t m, int64_t n, unsigned* flag) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < m;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int k = col[e];
+    if (k < 0 || k >= n) atomicOr(flag, 2u);
+  }
+}
+
+}  // namespace maiter
+
+using namespace maiter;
+
+extern "C" {
+
+const char* maiter_last_error(void) { return g_err; }
+
+const char* maiter_version(void) { return "maiter-b300 0.1 (sm_103a)"; }
+
+void maiter_params_default(maiter_run_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->op = MAITER_OP_SUM_F64;
+  p->g = MAITER_G_SCALE_BY_SRC;
+  p->sched = MAITER_SCHED_ALL;
+  p->engine = MAITER_ENGINE_SYNC;
+  p->coef = nullptr;
+  p->damping = 0.8;
+  p->source = -1;
+  p->threshold = 0.0;
+  p->top_frac = 0.01;
+  p->eps = 1e-8;
+  p->max_rounds = 1000000;
+  p->timeout_ms = 0;
+  p->stream = nullptr;
+}
+
+void maiter_graph_destroy(maiter_graph* g) {
+  if (!g) return;
+  DeviceGuard guard(g->device);
+  cudaFree(g->rp);
+  cudaFree(g->col);
+  cudaFree(g->w);
+  delete g;
+}
+
+maiter_status maiter_graph_create(int64_t n, int64_t m, const int64_t* row_ptr,
+                                  const int32_t* col, const uint32_t* w, int device,
+                                  maiter_graph** out) {
+  g_err[0] = '\0';
+  MAITER_REQUIRE(out, "maiter_graph_create: out is NULL");
+  *out = nullptr;
+  MAITER_REQUIRE(n >= 0 && n < (int64_t(1) << 31) - 1, "n = %lld out of range [0, 2^31-1)",
+                 (long long)n);
+  MAITER_REQUIRE(m >= 0 && m < (int64_t(1) << 31), "m = %lld out of range [0, 2^31)",
+                 (long long)m);
+  MAITER_REQUIRE(row_ptr, "row_ptr is NULL");
+  MAITER_REQUIRE(m == 0 || col, "col is NULL with m > 0");
+  int ndev = 0;
+  MAITER_CUDA(cudaGetDeviceCount(&ndev));
+  MAITER_REQUIRE(device >= 0 && device < ndev, "device %d out of range (%d devices)", device, ndev);
+  DeviceGuard guard(device);
+
+  maiter_graph* g = new (std::nothrow) maiter_graph();
+  MAITER_REQUIRE(g, "host allocation failed");
+  g->device = device;
+  g->n = n;
+  g->m = m;
+  cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, device);
+
+  int64_t* rp64 = nullptr;
+  unsigned* flag = nullptr;
+  auto fail = [&](maiter_status s) {
+    cudaFree(rp64);
+    cudaFree(flag);
+    maiter_graph_destroy(g);
+    return s;
+  };
+#define GC_CUDA(call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      set_error("%s failed: %s", #call, cudaGetErrorString(e_));                       \
+      return fail(e_ == cudaErrorMemoryAllocation ? MAITER_ERR_OOM : MAITER_ERR_CUDA); \
+    }                                                                                  \
+  } while (0)
+  GC_CUDA(cudaMalloc(&g->rp, sizeof(int) * (n + 1)));
+  GC_CUDA(cudaMalloc(&g->col, sizeof(int) * (m > 0 ? m : 1)));
+  if (w) GC_CUDA(cudaMalloc(&g->w, sizeof(uint32_t) * (m > 0 ? m : 1)));
+  GC_CUDA(cudaMalloc(&rp64, sizeof(int64_t) * (n + 1)));
+  GC_CUDA(cudaMalloc(&flag, sizeof(unsigned)));
+  GC_CUDA(cudaMemset(flag, 0, sizeof(unsigned)));
+  GC_CUDA(cudaMemcpy(rp64, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDefault));
+  if (m > 0) GC_CUDA(cudaMemcpy(g->col, col, sizeof(int) * m, cudaMemcpyDefault));
+  if (w && m > 0) GC_CUDA(cudaMemcpy(g->w, w, sizeof(uint32_t) * m, cudaMemcpyDefault));
+  const int blocks = g->num_sms * 4;
+  k_validate_rowptr<<<blocks, 256>>>(rp64, n, m, g->rp, flag);
+  if (m > 0) k_validate_col<<<blocks, 256>>>(g->col, m, n, flag);
+  GC_CUDA(cudaGetLastError());
+  unsigned h_flag = 0;
+  GC_CUDA(cudaMemcpy(&h_flag, flag, sizeof(unsigned), cudaMemcpyDeviceToHost));
+#undef GC_CUDA
+  if (h_flag & 1u) {
+    set_error("row_ptr must start at 0, be non-decreasing and end at m = %lld", (long long)m);
+    return fail(MAITER_ERR_INVALID_ARG);
+  }
+  if (h_flag & 2u) {
+    set_error("col holds a target outside [0, n = %lld)", (long long)n);
+    return fail(MAITER_ERR_INVALID_ARG);
+  }
+  cudaFree(rp64);
+  cudaFree(flag);
+  *out = g;
+  return MAITER_OK;
+}
+
+void maiter_result_destroy(maiter_result* r) {
+  if (!r) return;
+  DeviceGuard guard(r->g ? r->g->device : 0);
+  if (r->exec) cudaGraphExecDestroy(r->exec);
+  if (r->graph) cudaGraphDestroy(r->graph);
+  cudaFree(r->v);
+  cudaFree(r->delta);
+  cudaFree(r->coef);
+  for (int b = 0; b < kBuckets; ++b) cudaFree(r->list[b]);
+  cudaFree(r->ctl);
+  if (r->h_ctl) cudaFreeHost(r->h_ctl);
+  if (r->ev0) cudaEventDestroy(r->ev0);
+  if (r->ev1) cudaEventDestroy(r->ev1);
+  delete r;
+}
+
+}  // extern "C"
+
+namespace maiter {
+
+static size_t state_bytes(int op) { return op == MAITER_OP_MIN_U32 ? 4 : 8; }
+static size_t delta_bytes(int op) { return op == MAITER_OP_SUM_F64 ? 8 : 4; }
+static size_t coef_bytes(int op) { return op == MAITER_OP_SUM_F64 ? 8 : 4; }
+
+static maiter_status alloc_result(const maiter_graph* g, int op, maiter_result** out) {
+  maiter_result* r = new (std::nothrow) maiter_result();
+  MAITER_REQUIRE(r, "host allocation failed");
+  r->g = g;
+  r->op = op;
+  r->n = g->n;
+  const size_t n = static_cast<size_t>(g->n > 0 ? g->n : 1);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&r->v, n * state_bytes(op));
+  if (e == cudaSuccess) e = cudaMalloc(&r->delta, n * delta_bytes(op));
+  for (int b = 0; b < kBuckets && e == cudaSuccess; ++b) e = cudaMalloc(&r->list[b], n * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&r->ctl, sizeof(DevCtl));
+  if (e == cudaSuccess) e = cudaMallocHost(&r->h_ctl, sizeof(DevCtl));
+  if (e == cudaSuccess) e = cudaEventCreate(&r->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
+  if (e != cudaSuccess) {
+    set_error("result allocation failed: %s", cudaGetErrorString(e));
+    maiter_result_destroy(r);
+    return e == cudaErrorMemoryAllocation ? MAITER_ERR_OOM : MAITER_ERR_CUDA;
+  }
+  *out = r;
+  return MAITER_OK;
+}
+
+static int grid_for(const void* fn, int block, int num_sms, int per_sm_cap) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  if (per_sm_cap > 0 && per_sm > per_sm_cap) per_sm = per_sm_cap;
+  return num_sms * per_sm;
+}
+
+constexpr int kBlock = 256;
+
+template <class Op>
+static KArgs<Op> make_args(const maiter_graph* g, maiter_result* r, const void* coef,
+                           double damping, const Tuning& tu) {
+  KArgs<Op> a{};
+  a.n = static_cast<int>(g->n);
+  a.rp = g->rp;
+  a.edges.col = g->col;
+  a.edges.w = g->w;
+  a.coef = static_cast<const typename Op::C*>(coef);
+  a.damping = damping;
+  a.v = static_cast<typename Op::V*>(r->v);
+  a.delta = static_cast<typename Op::D*>(r->delta);
+  for (int b = 0; b < kBuckets; ++b) a.list[b] = r->list[b];
+  a.ctl = r->ctl;
+  a.cut_warp = tu.cut_warp;
+  a.cut_cta = tu.cut_cta;
+  return a;
+}
+
+// Builds the executable graph  WHILE(cond) { k_push ; k_scan }.  The first
+// body pass pushes an empty frontier (the control block starts with zero
+// counts) and k_scan builds the first one; k_scan's last block sets cond.
+template <class Op>
+static void loop_grids(const maiter_graph* g, const Tuning& tu, int* push_grid, int* scan_grid) {
+  *push_grid = grid_for(reinterpret_cast<const void*>(&k_push<Op, kBlock>), kBlock, g->num_sms,
+                        tu.push_blocks_per_sm);
+  int sg = g->num_sms * tu.scan_blocks_per_sm;
+  const int need = static_cast<int>((g->n + kBlock - 1) / kBlock);
+  if (need < sg) sg = need > 0 ? need : 1;
+  *scan_grid = sg;
+}
+
+template <class Op>
+static maiter_status build_loop(const maiter_graph* g, maiter_result* r, const void* coef,
+                                double damping, const Tuning& tu) {
+  if (r->exec) { cudaGraphExecDestroy(r->exec); r->exec = nullptr; }
+  if (r->graph) { cudaGraphDestroy(r->graph); r->graph = nullptr; }
+  KArgs<Op> a = make_args<Op>(g, r, coef, damping, tu);
+  int push_grid, scan_grid;
+  loop_grids<Op>(g, tu, &push_grid, &scan_grid);
+
+  MAITER_CUDA(cudaGraphCreate(&r->graph, 0));
+  cudaGraphConditionalHandle cond;
+  MAITER_CUDA(cudaGraphConditionalHandleCreate(&cond, r->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  MAITER_CUDA(cudaGraphAddNode(&node, r->graph, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+
+  cudaStream_t cap;
+  MAITER_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    k_push<Op, kBlock><<<push_grid, kBlock, 0, cap>>>(a);
+    k_scan<Op, kBlock><<<scan_grid, kBlock, 0, cap>>>(a, cond, 1);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cap, &captured);
+  }
+  cudaStreamDestroy(cap);
+  MAITER_CUDA(e);
+  MAITER_CUDA(cudaGraphInstantiate(&r->exec, r->graph, 0));
+  return MAITER_OK;
+}
+
+template <class Op>
+static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
+                              maiter_result* r, cudaStream_t st) {
+  const Tuning tu{};
+  const void* coef = p->coef ? r->coef : nullptr;
+  // The executable graph bakes in the kernel arguments; rebuild it only when
+  // one of them changes.
+  uint64_t key = 1469598103934665603ull;
+  auto mix = [&](uint64_t x) { key = (key ^ x) * 1099511628211ull; };
+  uint64_t dbits;
+  std::memcpy(&dbits, &p->damping, sizeof(dbits));
+  mix(static_cast<uint64_t>(p->op));
+  mix(coef ? 1 : 0);
+  mix(dbits);
+  mix(static_cast<uint64_t>(tu.cut_warp));
+  mix(static_cast<uint64_t>(tu.cut_cta));
+  if (!r->exec || r->exec_key != key) {
+    maiter_status s = build_loop<Op>(g, r, coef, p->damping, tu);
+    if (s != MAITER_OK) return s;
+    r->exec_key = key;
+  }
+  DevCtl c{};
+  c.tau = (p->sched == MAITER_SCHED_THRESHOLD) ? p->threshold : 0.0;
+  c.eps = p->eps;
+  c.max_rounds = p->max_rounds > 0 ? p->max_rounds : 1000000;
+  c.sched = p->sched;
+  *r->h_ctl = c;
+  MAITER_CUDA(cudaMemcpyAsync(r->ctl, r->h_ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, st));
+  maiter_stats& s = r->stats;
+  s = maiter_stats{};
+  float ms = 0.f;
+  if (p->flags & MAITER_FLAG_PROFILE_KERNELS) {
+    // Host-driven loop: the same kernels and launch shapes as the graph body,
+    // each bracketed by events on the launching stream.
+    KArgs<Op> a = make_args<Op>(g, r, coef, p->damping, tu);
+    int push_grid, scan_grid;
+    loop_grids<Op>(g, tu, &push_grid, &scan_grid);
+    cudaEvent_t e[3];
+    for (auto& x : e) MAITER_CUDA(cudaEventCreate(&x));
+    MAITER_CUDA(cudaEventRecord(r->ev0, st));
+    for (;;) {
+      MAITER_CUDA(cudaEventRecord(e[0], st));
+      k_push<Op, kBlock><<<push_grid, kBlock, 0, st>>>(a);
+      MAITER_CUDA(cudaEventRecord(e[1], st));
+      k_scan<Op, kBlock><<<scan_grid, kBlock, 0, st>>>(a, cudaGraphConditionalHandle{}, 0);
+      MAITER_CUDA(cudaEventRecord(e[2], st));
+      MAITER_CUDA(cudaMemcpyAsync(r->h_ctl, r->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+      MAITER_CUDA(cudaStreamSynchronize(st));
+      float t1 = 0.f, t2 = 0.f;
+      cudaEventElapsedTime(&t1, e[0], e[1]);
+      cudaEventElapsedTime(&t2, e[1], e[2]);
+      s.push_ms += t1;
+      s.scan_ms += t2;
+      s.push_launches++;
+      s.scan_launches++;
+      if (r->h_ctl->status != 0) break;
+    }
+    MAITER_CUDA(cudaEventRecord(r->ev1, st));
+    MAITER_CUDA(cudaStreamSynchronize(st));
+    for (auto& x : e) cudaEventDestroy(x);
+  } else {
+    MAITER_CUDA(cudaEventRecord(r->ev0, st));
+    MAITER_CUDA(cudaGraphLaunch(r->exec, st));
+    MAITER_CUDA(cudaEventRecord(r->ev1, st));
+    MAITER_CUDA(cudaMemcpyAsync(r->h_ctl, r->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+    MAITER_CUDA(cudaStreamSynchronize(st));
+  }
+  cudaEventElapsedTime(&ms, r->ev0, r->ev1);
+  const DevCtl& h = *r->h_ctl;
+  s.rounds = static_cast<int64_t>(h.rounds);
+  s.activations = static_cast<int64_t>(h.activations);
+  s.edge_pushes = static_cast<int64_t>(h.pushes);
+  s.residual = h.residual;
+  s.elapsed_ms = ms;
+  s.converged = h.status == 1;
+  s.kernel_launches += 2 * static_cast<int64_t>(h.rounds + 1);
+  s.status = h.status == 1 ? MAITER_OK : MAITER_ERR_NOT_CONVERGED;
+  if (h.status != 1) {
+    set_error("round cap of %lld reached before the termination test held (residual %g)",
+              (long long)c.max_rounds, h.residual);
+  }
+  return static_cast<maiter_status>(s.status);
+}
+
+// Initial v and Delta: copies when given, else the defaults of Table 1.
+template <class Op>
+static maiter_status init_state(const maiter_graph* g, const maiter_run_params* p,
+                                maiter_result* r, cudaStream_t st, int* launches) {
+  *launches = 0;
+  using V = typename Op::V;
+  using D = typename Op::D;
+  const int64_t n = g->n;
+  if (n == 0) return MAITER_OK;
+  const int blocks = g->num_sms * 4;
+  V* v = static_cast<V*>(r->v);
+  D* d = static_cast<D*>(r->delta);
+  if (p->v0) {
+    MAITER_CUDA(cudaMemcpyAsync(v, p->v0, sizeof(V) * n, cudaMemcpyDefault, st));
+  } else {
+    k_fill<V><<<blocks, 256, 0, st>>>(v, n, Op::kIsSum ? V(0) : V(kInfU32));
+    ++*launches;
+  }
+  if (p->delta0) {
+    MAITER_CUDA(cudaMemcpyAsync(d, p->delta0, sizeof(D) * n, cudaMemcpyDefault, st));
+  } else if (Op::kIsSum) {
+    k_fill<D><<<blocks, 256, 0, st>>>(d, n, static_cast<D>(1.0 - p->damping));
+    ++*launches;
+  } else {
+    k_fill<D><<<blocks, 256, 0, st>>>(d, n, D(kInfU32));
+    k_fill<D><<<1, 32, 0, st>>>(d + p->source, 1, D(0));
+    *launches += 2;
+  }
+  if (p->coef) {
+    if (!r->coef) MAITER_CUDA(cudaMalloc(&r->coef, coef_bytes(r->op) * n));
+    MAITER_CUDA(cudaMemcpyAsync(r->coef, p->coef, coef_bytes(r->op) * n, cudaMemcpyDefault, st));
+  }
+  MAITER_CUDA(cudaGetLastError());
+  return MAITER_OK;
+}
+
+template <class Op>
+static maiter_status run_op(const maiter_graph* g, const maiter_run_params* p, maiter_result* r,
+                            cudaStream_t st) {
+  int init_launches = 0;
+  maiter_status s = init_state<Op>(g, p, r, st, &init_launches);
+  if (s != MAITER_OK) return s;
+  if (g->n == 0) {
+    r->stats = maiter_stats{};
+    r->stats.converged = 1;
+    r->stats.kernel_launches = init_launches;
+    return MAITER_OK;
+  }
+  s = run_sync<Op>(g, p, r, st);
+  r->stats.kernel_launches += init_launches;
+  return s;
+}
+
+}  // namespace maiter
+
+extern "C" {
+
+maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p, maiter_result** out) {
+  g_err[0] = '\0';
+  MAITER_REQUIRE(g && p && out, "maiter_run: NULL argument");
+  MAITER_REQUIRE(p->op >= MAITER_OP_SUM_F64 && p->op <= MAITER_OP_MIN_U32, "unknown op %d", p->op);
+  const bool is_sum = p->op != MAITER_OP_MIN_U32;
+  MAITER_REQUIRE(p->sched >= MAITER_SCHED_ALL && p->sched <= MAITER_SCHED_TOPFRAC,
+                 "unknown sched %d", p->sched);
+  MAITER_REQUIRE(p->engine == MAITER_ENGINE_SYNC, "unknown engine %d", p->engine);
+  MAITER_REQUIRE((p->flags & ~MAITER_FLAG_PROFILE_KERNELS) == 0 && p->reserved0 == 0,
+                 "unknown flags 0x%x", p->flags);
+  if (is_sum) {
+    MAITER_REQUIRE(p->g == MAITER_G_SCALE_BY_SRC, "sum ops take g = MAITER_G_SCALE_BY_SRC");
+    MAITER_REQUIRE(p->coef || std::isfinite(p->damping),
+                   "damping must be finite when coef is NULL");
+    MAITER_REQUIRE(std::isfinite(p->eps) && p->eps >= 0.0, "eps must be finite and >= 0");
+    MAITER_REQUIRE(p->sched != MAITER_SCHED_THRESHOLD ||
+                       (std::isfinite(p->threshold) && p->threshold >= 0.0),
+                   "threshold must be finite and >= 0");
+  } else {
+    MAITER_REQUIRE(p->g == MAITER_G_ADD_EDGE, "min takes g = MAITER_G_ADD_EDGE");
+    MAITER_REQUIRE(g->w || g->m == 0, "min with g = x + w needs edge weights");
+    MAITER_REQUIRE(p->delta0 || (p->source >= 0 && p->source < g->n),
+                   "min without delta0 needs a source in [0, n)");
+  }
+  if (p->sched == MAITER_SCHED_TOPFRAC) {
+    set_error("MAITER_SCHED_TOPFRAC is not available in this build");
+    return MAITER_ERR_UNSUPPORTED;
+  }
+  DeviceGuard guard(g->device);
+  maiter_result* r = *out;
+  bool fresh = false;
+  if (r) {
+    MAITER_REQUIRE(r->g == g && r->op == p->op,
+                   "the result passed for reuse belongs to another graph or op");
+  } else {
+    maiter_status s = alloc_result(g, p->op, &r);
+    if (s != MAITER_OK) return s;
+    fresh = true;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(p->stream);
+  maiter_status s;
+  switch (p->op) {
+    case MAITER_OP_SUM_F64: s = run_op<OpSumF64>(g, p, r, st); break;
+    case MAITER_OP_SUM_MIXED: s = run_op<OpSumMixed>(g, p, r, st); break;
+    default: s = run_op<OpMinU32>(g, p, r, st); break;
+  }
+  if (s == MAITER_OK || s == MAITER_ERR_NOT_CONVERGED) {
+    *out = r;
+  } else if (fresh) {
+    maiter_result_destroy(r);
+  }
+  return s;
+}
+
+static maiter_status copy_out(const maiter_result* r, const void* src, size_t elem, void* out,
+                              int64_t count) {
+  MAITER_REQUIRE(r && out, "NULL argument");
+  MAITER_REQUIRE(count == r->n, "count %lld != n %lld", (long long)count, (long long)r->n);
+  if (count == 0) return MAITER_OK;
+  DeviceGuard guard(r->g->device);
+  MAITER_CUDA(cudaMemcpy(out, src, elem * count, cudaMemcpyDefault));
+  return MAITER_OK;
+}
+
+maiter_status maiter_get_state(const maiter_result* r, void* out, int64_t count) {
+  g_err[0] = '\0';
+  MAITER_REQUIRE(r, "NULL result");
+  return copy_out(r, r->v, state_bytes(r->op), out, count);
+}
+
+maiter_status maiter_get_delta(const maiter_result* r, void* out, int64_t count) {
+  g_err[0] = '\0';
+  MAITER_REQUIRE(r, "NULL result");
+  return copy_out(r, r->delta, delta_bytes(r->op), out, count);
+}
+
+maiter_status maiter_get_stats(const maiter_result* r, maiter_stats* out) {
+  g_err[0] = '\0';
+  MAITER_REQUIRE(r && out, "NULL argument");
+  *out = r->stats;
+  return MAITER_OK;
+}
+
+}  // extern "C"
