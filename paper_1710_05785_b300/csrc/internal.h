@@ -67,7 +67,8 @@ struct maiter_graph {
 };
 
 struct maiter_result {
-  const maiter_graph* g = nullptr;
+  const maiter_graph* g = nullptr;   // identity check only: a result may outlive its graph
+  int device = 0;
   int op = -1;
   int64_t n = 0;
   void* v = nullptr;           // n x V

@@ -19,6 +19,14 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
+// Every entry point starts here: clear this thread's message and any
+// non-sticky CUDA error left by an earlier unchecked runtime call, so a later
+// cudaGetLastError() reports only this call's launches.
+static void begin_call() {
+  g_err[0] = '\0';
+  cudaGetLastError();
+}
+
 bool is_device_pointer(const void* p) {
   if (!p) return false;
   cudaPointerAttributes at{};
@@ -95,7 +103,7 @@ void maiter_graph_destroy(maiter_graph* g) {
 maiter_status maiter_graph_create(int64_t n, int64_t m, const int64_t* row_ptr,
                                   const int32_t* col, const uint32_t* w, int device,
                                   maiter_graph** out) {
-  g_err[0] = '\0';
+  begin_call();
   MAITER_REQUIRE(out, "maiter_graph_create: out is NULL");
   *out = nullptr;
   MAITER_REQUIRE(n >= 0 && n < (int64_t(1) << 31) - 1, "n = %lld out of range [0, 2^31-1)",
@@ -164,7 +172,7 @@ maiter_status maiter_graph_create(int64_t n, int64_t m, const int64_t* row_ptr,
 
 void maiter_result_destroy(maiter_result* r) {
   if (!r) return;
-  DeviceGuard guard(r->g ? r->g->device : 0);
+  DeviceGuard guard(r->device);
   if (r->exec) cudaGraphExecDestroy(r->exec);
   if (r->graph) cudaGraphDestroy(r->graph);
   cudaFree(r->v);
@@ -190,6 +198,7 @@ static maiter_status alloc_result(const maiter_graph* g, int op, maiter_result**
   maiter_result* r = new (std::nothrow) maiter_result();
   MAITER_REQUIRE(r, "host allocation failed");
   r->g = g;
+  r->device = g->device;
   r->op = op;
   r->n = g->n;
   const size_t n = static_cast<size_t>(g->n > 0 ? g->n : 1);
@@ -432,7 +441,7 @@ static maiter_status run_op(const maiter_graph* g, const maiter_run_params* p, m
 extern "C" {
 
 maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p, maiter_result** out) {
-  g_err[0] = '\0';
+  begin_call();
   MAITER_REQUIRE(g && p && out, "maiter_run: NULL argument");
   MAITER_REQUIRE(p->op >= MAITER_OP_SUM_F64 && p->op <= MAITER_OP_MIN_U32, "unknown op %d", p->op);
   const bool is_sum = p->op != MAITER_OP_MIN_U32;
@@ -490,25 +499,25 @@ static maiter_status copy_out(const maiter_result* r, const void* src, size_t el
   MAITER_REQUIRE(r && out, "NULL argument");
   MAITER_REQUIRE(count == r->n, "count %lld != n %lld", (long long)count, (long long)r->n);
   if (count == 0) return MAITER_OK;
-  DeviceGuard guard(r->g->device);
+  DeviceGuard guard(r->device);
   MAITER_CUDA(cudaMemcpy(out, src, elem * count, cudaMemcpyDefault));
   return MAITER_OK;
 }
 
 maiter_status maiter_get_state(const maiter_result* r, void* out, int64_t count) {
-  g_err[0] = '\0';
+  begin_call();
   MAITER_REQUIRE(r, "NULL result");
   return copy_out(r, r->v, state_bytes(r->op), out, count);
 }
 
 maiter_status maiter_get_delta(const maiter_result* r, void* out, int64_t count) {
-  g_err[0] = '\0';
+  begin_call();
   MAITER_REQUIRE(r, "NULL result");
   return copy_out(r, r->delta, delta_bytes(r->op), out, count);
 }
 
 maiter_status maiter_get_stats(const maiter_result* r, maiter_stats* out) {
-  g_err[0] = '\0';
+  begin_call();
   MAITER_REQUIRE(r && out, "NULL argument");
   *out = r->stats;
   return MAITER_OK;
