@@ -179,6 +179,40 @@ maiter_status maiter_get_stats(const maiter_result* r, maiter_stats* out);
 
 void maiter_result_destroy(maiter_result* r);
 
+/* SSSP (min, g(x) = x + w, all pending vertices per round) that allocates no
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that hold device buffers but may not call cudaMalloc - for example a plugin
+ * whose device memory belongs to a host framework's caching allocator, code
+ * that may run while that framework is capturing a stream (allocation is not
+ * allowed then), or a caller with a fixed memory budget.
+ *
+ * Inputs (device pointers only): row_ptr[n+1] as INT32 offsets (row_ptr[0] =
+ * 0, non-decreasing, row_ptr[n] = m), col[m], w[m]; source in [0, n).
+ * Outputs (device, caller-owned): v_out[n] receives the distances (UINT32_MAX
+ * if unreachable), delta_out[n] the final deltas.  *rounds_out (host, may be
+ * NULL) receives the number of rounds.
+ *
+ * Working memory: the frontier lists and the control block live in one
+ * fixed device array inside the library, 12 MiB + 256 B, which every GPU that
+ * loads the library holds until the process exits.  Hence n is limited to
+ * 1,048,576 (2^20) vertices; larger n returns MAITER_ERR_INVALID_ARG with a
+ * message.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * previous call's contents (each call resets what must start at zero), so
+ * calls that overlap on the GPU - on two streams, or from two threads - race
+ * and must be serialised by the caller.
+ *
+ * The round loop runs from the host: per round two kernel launches on
+ * `stream` and a small device-to-host read of the control block (into a host
+ * stack variable), so the call returns
+ * when the distances are final.  Errors: INVALID_ARG (sizes, non-device
+ * pointers, bad CSR), NOT_CONVERGED (max_rounds, <= 0 means 1,000,000), CUDA. */
+maiter_status maiter_sssp_noalloc(int64_t n, int64_t m, const int32_t* row_ptr,
+                                  const int32_t* col, const uint32_t* w, int64_t source,
+                                  uint32_t* v_out, uint32_t* delta_out, int64_t max_rounds,
+                                  int device, void* stream, int64_t* rounds_out);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* maiter_last_error(void);
 
