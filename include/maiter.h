@@ -63,7 +63,8 @@ typedef enum {
 typedef enum {
   MAITER_OP_SUM_F64 = 0,   /* (+) = +; v, Delta, coefficients, residual FP64 */
   MAITER_OP_SUM_MIXED = 1, /* (+) = +; Delta and coefficients FP32, v and the
-                              residual reduction FP64 */
+                              residual reduction FP64 (after an FP64-delta
+                              warm-up phase, see mixed_switch) */
   MAITER_OP_MIN_U32 = 2    /* (+) = min over uint32, identity UINT32_MAX (inf) */
 } maiter_op;
 
@@ -113,7 +114,7 @@ typedef struct maiter_run_params {
   double damping;      /* d in coef[j] = d / outdeg(j) when coef == NULL */
   const void* v0;      /* n initial states (double for sums, uint32 for min), or
                           NULL: the identity (0 for +, UINT32_MAX for min) */
-  const void* delta0;  /* n initial deltas (double / float / uint32), or NULL:
+  const void* delta0;  /* n initial deltas (double for both sums, uint32 for min), or NULL:
                           1 - damping everywhere for sums (PageRank, Table 1),
                           0 at `source` and UINT32_MAX elsewhere for min */
   int64_t source;      /* min with delta0 == NULL: the source vertex */
@@ -123,6 +124,14 @@ typedef struct maiter_run_params {
                           every run terminates. */
   double top_frac;     /* TOPFRAC: fraction q in (0, 1] */
   double eps;          /* sums: stop when sum_j |Delta_j| < eps (FP64 reduction) */
+  double mixed_switch; /* SUM_MIXED: deltas are FP64 until the residual has
+                          fallen to mixed_switch x its initial value, then
+                          rounded once to FP32 for the rest of the run (default
+                          0.01; 1 = FP32 deltas from the first round, 0 = FP64
+                          deltas throughout).  FP32 accumulation of many
+                          messages into one delta loses ~sqrt(k) ulps at a
+                          vertex of in-degree k, which is why the large early
+                          deltas are accumulated in FP64. */
   int64_t max_rounds;  /* round cap; <= 0 means 1,000,000 */
   int64_t timeout_ms;  /* reserved for bounded device waits; 0 = default */
   void* stream;        /* cudaStream_t to run on; NULL = the default stream */

@@ -40,6 +40,7 @@ INF32 = 0xFFFFFFFF
 
 _STATE_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float64, OP_MIN_U32: np.uint32}
 _DELTA_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float32, OP_MIN_U32: np.uint32}
+_DELTA0_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float64, OP_MIN_U32: np.uint32}
 _COEF_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float32}
 
 
@@ -52,6 +53,7 @@ class RunParams(ctypes.Structure):
         ("v0", ctypes.c_void_p), ("delta0", ctypes.c_void_p),
         ("source", ctypes.c_int64),
         ("threshold", ctypes.c_double), ("top_frac", ctypes.c_double), ("eps", ctypes.c_double),
+        ("mixed_switch", ctypes.c_double),
         ("max_rounds", ctypes.c_int64), ("timeout_ms", ctypes.c_int64),
         ("stream", ctypes.c_void_p),
     ]
@@ -234,7 +236,8 @@ class Result:
 
 def run(graph: Graph, op: int = OP_SUM_F64, *, coef=None, damping: float = 0.8, v0=None,
         delta0=None, source: int = -1, sched: int = SCHED_ALL, threshold: float = 0.0,
-        top_frac: float = 0.01, eps: float = 1e-8, max_rounds: int = 1000000,
+        top_frac: float = 0.01, eps: float = 1e-8, mixed_switch: float = 0.01,
+        max_rounds: int = 1000000,
         timeout_ms: int = 0, stream=None, engine: int = ENGINE_SYNC, flags: int = 0,
         result: Result | None = None, allow_not_converged: bool = False) -> Result:
     """``maiter_run``: one DAIC run to termination.  ``stream`` is a raw
@@ -255,11 +258,12 @@ def run(graph: Graph, op: int = OP_SUM_F64, *, coef=None, damping: float = 0.8, 
         keep.append(v0)
         p.v0 = _addr(v0)
     if delta0 is not None:
-        delta0 = _as(delta0, _DELTA_DTYPE[op], n, "delta0")
+        delta0 = _as(delta0, _DELTA0_DTYPE[op], n, "delta0")
         keep.append(delta0)
         p.delta0 = _addr(delta0)
     p.source = source
     p.threshold, p.top_frac, p.eps = threshold, top_frac, eps
+    p.mixed_switch = mixed_switch
     p.max_rounds, p.timeout_ms = max_rounds, timeout_ms
     p.stream = stream
     h = ctypes.c_void_p(result.handle.value if result is not None else None)

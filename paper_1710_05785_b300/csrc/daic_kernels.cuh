@@ -6,17 +6,19 @@
 //               * reduces sum_j |Delta_j| in FP64 (or counts pending vertices),
 //               * selects the vertices to activate (all pending, or priority
 //                 above a threshold),
-//               * compacts them with warp ballots into three lists by
-//                 out-degree (small / medium / large),
+//               * compacts them with warp ballots into lists by out-degree:
+//                 small and medium vertices one entry each, large vertices
+//                 one entry per chunk of kChunk edges,
 //             and whose last block decides, on the device, whether another
 //             round follows (it sets the WHILE condition of the CUDA graph).
 //   k_push  - the update of Eq. 5 for every listed vertex: read-and-reset of
 //             Delta_j, fold into v_j, and the scatter of g_{j,k}(Delta_j) into
 //             every out-neighbour's Delta_k with atomics.  Work granularity by
-//             degree: a whole CTA per large vertex, a warp per medium vertex,
-//             and for small vertices a warp that gathers the edges of 32
-//             vertices and processes them 32 at a time (prefix sum + search),
-//             so every lane has an edge on every step.
+//             degree: a CTA per chunk of a large vertex (so a hub is spread
+//             over many SMs), a warp per medium vertex, and for small vertices
+//             a warp that gathers the edges of 32 vertices into one index space
+//             (prefix sum + search) so every lane has an edge on every step.
+//             Edge loops issue four independent loads before their atomics.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -26,15 +28,18 @@
 namespace maiter {
 
 constexpr int kBuckets = 3;
+constexpr int kChunk = 1024;   // edges per large-vertex work item (one CTA, 4 per thread)
+constexpr int kUnroll = 4;
 
 // Device-resident control block of one run.  Everything the round loop needs
 // to decide on its own lives here, so the loop never returns to the host.
 struct DevCtl {
-  unsigned int cnt[2][4];        // [set][bucket] frontier sizes (double-buffered)
+  unsigned int cnt[2][4];        // [set][bucket] frontier sizes (double-buffered);
+                                 // bucket 2 counts large-vertex chunks
   unsigned int rset;             // set the next push reads
   unsigned int wset;             // set the next scan writes
   unsigned int ticket;           // last-block election in k_scan
-  int status;                    // 0 running, 1 converged, 2 round cap hit
+  int status;                    // 0 running, 1 converged, 2 round cap hit, 3 overflow
   double resid_acc;              // this scan: sum |Delta| (sum) or pending count (min)
   unsigned long long act_acc;    // this scan: selected vertices
   unsigned long long push_acc;   // this scan: sum of out-degrees of selected vertices
@@ -45,9 +50,13 @@ struct DevCtl {
   double residual;               // last decided residual
   double tau;                    // current activation threshold (sum ops)
   double eps;                    // termination bound (sum ops)
+  double eps_eff;                // bound of the current phase (set by the first scan)
+  double switch_frac;            // > 0: this phase ends at switch_frac x first residual
   long long max_rounds;
   int sched;                     // maiter_sched
-  int pad;
+  int phase;                     // 1 once the FP32 phase of a mixed run has started
+  unsigned int overflow;         // a list reservation would have run past its capacity
+  unsigned int pad;
 };
 
 template <class Op>
@@ -59,10 +68,13 @@ struct KArgs {
   double damping;
   typename Op::V* v;
   typename Op::D* delta;
-  int* list[kBuckets];
+  int* list[2];                  // small, medium: vertex ids (capacity n each)
+  int2* large;                   // large: (vertex, chunk index) per entry
+  typename Op::D* large_d;       // large: the delta taken by the scan, per entry
+  unsigned int large_cap;        // capacity of large / large_d
   DevCtl* ctl;
   int cut_warp;                  // deg <  cut_warp : small bucket
-  int cut_cta;                   // deg >= cut_cta  : large bucket
+  int cut_cta;                   // deg >= cut_cta  : large bucket (chunked)
 };
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -75,6 +87,14 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
+__device__ __forceinline__ int warp_incl_scan(int x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  return x;
+}
 
 // ------------------------------------------------------------------ scan
 
@@ -82,6 +102,7 @@ template <class Op, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditionalHandle cond,
                                                  int use_cond) {
   static_assert(BLOCK % 32 == 0 && BLOCK <= 1024, "block");
+  using D = typename Op::D;
   DevCtl* ctl = a.ctl;
   const unsigned ws = ctl->wset;
   const double tau = ctl->tau;
@@ -99,12 +120,12 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
     bool sel = false;
     int deg = 0;
     if (j < a.n) {
-      typename Op::D d = a.delta[j];
-      typename Op::V vv = Op::kIsSum ? typename Op::V(0) : a.v[j];
-      bool pend = Op::pending(d, vv);
+      const D d = a.delta[j];
+      const typename Op::V vv = Op::kIsSum ? typename Op::V(0) : a.v[j];
+      const bool pend = Op::pending(d, vv);
       npend += pend;
       if (Op::kIsSum) {
-        double p = Op::priority(d, vv);
+        const double p = Op::priority(d, vv);
         rsum += p;
         sel = pend && p > tau;
       } else {
@@ -112,10 +133,10 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
       }
       if (sel) deg = __ldg(a.rp + j + 1) - __ldg(a.rp + j);
     }
-    const int bucket = deg < a.cut_warp ? 0 : (deg < a.cut_cta ? 1 : 2);
+    const int bucket = !sel ? -1 : (deg < a.cut_warp ? 0 : (deg < a.cut_cta ? 1 : 2));
 #pragma unroll
-    for (int b = 0; b < kBuckets; ++b) {
-      const bool mine = sel && bucket == b;
+    for (int b = 0; b < 2; ++b) {
+      const bool mine = bucket == b;
       const unsigned mask = __ballot_sync(0xffffffffu, mine);
       if (mask) {
         const int leader = __ffs(mask) - 1;
@@ -125,6 +146,27 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
         if (mine) a.list[b][pos + __popc(mask & lt_mask)] = j;
       }
     }
+    // Large vertices: one entry per chunk; their delta is taken here.
+    const int chunks = (bucket == 2) ? (deg + kChunk - 1) / kChunk : 0;
+    if (__ballot_sync(0xffffffffu, chunks > 0)) {
+      const int incl = warp_incl_scan(chunks, lane);
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      unsigned base_pos = 0;
+      if (lane == 31) base_pos = atomicAdd(&ctl->cnt[ws][2], static_cast<unsigned>(total));
+      base_pos = __shfl_sync(0xffffffffu, base_pos, 31);
+      if (chunks > 0) {
+        const unsigned p0 = base_pos + static_cast<unsigned>(incl - chunks);
+        if (p0 + static_cast<unsigned>(chunks) <= a.large_cap) {
+          const D d = Op::take(j, a.delta, a.v);
+          for (int q = 0; q < chunks; ++q) {
+            a.large[p0 + q] = make_int2(j, q);
+            a.large_d[p0 + q] = d;
+          }
+        } else {
+          atomicOr(&ctl->overflow, 1u);
+        }
+      }
+    }
     nact += sel;
     npush += static_cast<unsigned long long>(deg);
   }
@@ -132,7 +174,8 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
   // Block reduction, one atomic per block per counter.
   __shared__ double s_r[BLOCK / 32];
   __shared__ unsigned long long s_a[BLOCK / 32], s_p[BLOCK / 32], s_q[BLOCK / 32];
-  __shared__ bool s_last;
+  __shared__ int s_last;
+  __shared__ unsigned s_cont;
   rsum = warp_sum(rsum);
   nact = warp_sum(nact);
   npush = warp_sum(npush);
@@ -153,31 +196,60 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
     s_last = (t == gridDim.x - 1);
   }
   __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
+  if (!s_last) return;
 
-  // Last block: every other block's counters are visible (fence + ticket).
+  // Last block: every other block's counters and list entries are visible
+  // (fence + ticket).  Thread 0 decides; the block then undoes the delta
+  // takes of large vertices if no push follows.
   __threadfence();
   volatile DevCtl* vc = ctl;
-  const double resid = Op::kIsSum ? vc->resid_acc : static_cast<double>(vc->pend_acc);
-  const unsigned long long act = vc->act_acc;
-  const unsigned long long psh = vc->push_acc;
-  const unsigned long long pend = vc->pend_acc;
-  const bool converged = Op::kIsSum ? (resid < vc->eps || pend == 0) : (pend == 0);
-  unsigned cont = 0;
-  ctl->residual = resid;
-  if (converged) {
-    ctl->status = 1;
-  } else if (static_cast<long long>(vc->rounds) >= vc->max_rounds) {
-    ctl->status = 2;
-  } else {
-    cont = 1;
-    ctl->rounds = vc->rounds + 1;
-    ctl->activations = vc->activations + act;
-    ctl->pushes = vc->pushes + psh;
-    // Threshold selected nothing although work remains: lower it (x0.1, to 0)
-    // so the run always terminates.
-    if (Op::kIsSum && act == 0) ctl->tau = (vc->tau < 1e-300) ? 0.0 : vc->tau * 0.1;
+  if (threadIdx.x == 0) {
+    const double resid = Op::kIsSum ? vc->resid_acc : static_cast<double>(vc->pend_acc);
+    const unsigned long long act = vc->act_acc;
+    const unsigned long long psh = vc->push_acc;
+    const unsigned long long pend = vc->pend_acc;
+    // A phase that ends early (the FP64 warm-up of the mixed-precision run)
+    // stops at switch_frac times the residual its first scan measured.
+    double eps_now = vc->eps_eff;
+    if (vc->rounds == 0) {
+      eps_now = vc->eps;
+      if (vc->switch_frac > 0.0 && vc->switch_frac * resid > eps_now)
+        eps_now = vc->switch_frac * resid;
+      ctl->eps_eff = eps_now;
+    }
+    const bool converged =
+        Op::kIsSum ? (resid < eps_now || pend == 0 || (vc->rounds == 0 && vc->switch_frac >= 1.0))
+                   : (pend == 0);
+    unsigned cont = 0;
+    ctl->residual = resid;
+    if (vc->overflow) {
+      ctl->status = 3;
+    } else if (converged) {
+      ctl->status = 1;
+    } else if (static_cast<long long>(vc->rounds) >= vc->max_rounds) {
+      ctl->status = 2;
+    } else {
+      cont = 1;
+      ctl->rounds = vc->rounds + 1;
+      ctl->activations = vc->activations + act;
+      ctl->pushes = vc->pushes + psh;
+      // Threshold selected nothing although work remains: lower it (x0.1, to 0)
+      // so the run always terminates.
+      if (Op::kIsSum && act == 0) ctl->tau = (vc->tau < 1e-300) ? 0.0 : vc->tau * 0.1;
+    }
+    s_cont = cont;
   }
+  __syncthreads();
+  const unsigned cont = s_cont;
+  if (!cont && !vc->overflow) {
+    const unsigned nl = vc->cnt[ws][2] < a.large_cap ? vc->cnt[ws][2] : a.large_cap;
+    for (unsigned i = threadIdx.x; i < nl; i += BLOCK) {
+      const int2 e = a.large[i];
+      if (e.y == 0) Op::untake(e.x, a.large_d[i], a.delta);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   ctl->resid_acc = 0.0;
   ctl->act_acc = 0;
   ctl->push_acc = 0;
@@ -197,6 +269,22 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
 
 // ------------------------------------------------------------------ push
 
+// Scatter of one message over edges [e, end) with the given lane stride;
+// four independent edge loads are in flight before their atomics.
+template <class Op, int STRIDE>
+__device__ __forceinline__ void scatter_range(const EdgeCtx& g, int e, int end,
+                                              typename Op::Msg m, typename Op::D* delta) {
+  for (; e < end; e += kUnroll * STRIDE) {
+    typename Op::Edge ed[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (e + u * STRIDE < end) ed[u] = Op::load(g, e + u * STRIDE);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (e + u * STRIDE < end) Op::apply(ed[u], m, delta);
+  }
+}
+
 template <class Op, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_push(KArgs<Op> a) {
   using Msg = typename Op::Msg;
@@ -207,23 +295,19 @@ __global__ void __launch_bounds__(BLOCK) k_push(KArgs<Op> a) {
   const int cL = static_cast<int>(ctl->cnt[rs][2]);
   const int lane = threadIdx.x & 31;
 
-  // Large vertices: one CTA each.
-  __shared__ Msg s_msg;
-  __shared__ int s_beg, s_end;
+  // Large vertices: one CTA per chunk of kChunk edges.  The delta was taken
+  // by the scan; chunk 0 folds it into v_j.
   for (int i = blockIdx.x; i < cL; i += gridDim.x) {
-    if (threadIdx.x == 0) {
-      const int j = a.list[2][i];
-      const int beg = __ldg(a.rp + j), end = __ldg(a.rp + j + 1);
-      s_msg = Op::fold(j, end - beg, a.delta, a.v, a.coef, a.damping);
-      s_beg = beg;
-      s_end = end;
-    }
-    __syncthreads();
-    const Msg m = s_msg;
+    const int2 e = a.large[i];
+    const int j = e.x, q = e.y;
+    const int rb = __ldg(a.rp + j), re = __ldg(a.rp + j + 1);
+    const Msg m = Op::finish(j, re - rb, a.large_d[i], a.v, a.coef, a.damping,
+                             q == 0 && threadIdx.x == 0);
     if (Op::live(m)) {
-      for (int e = s_beg + threadIdx.x; e < s_end; e += BLOCK) Op::scatter(a.edges, e, m, a.delta);
+      const int beg = rb + q * kChunk;
+      const int end = min(re, beg + kChunk);
+      scatter_range<Op, BLOCK>(a.edges, beg + static_cast<int>(threadIdx.x), end, m, a.delta);
     }
-    __syncthreads();
   }
 
   const int warp = (blockIdx.x * BLOCK + threadIdx.x) >> 5;
@@ -242,13 +326,11 @@ __global__ void __launch_bounds__(BLOCK) k_push(KArgs<Op> a) {
     m = __shfl_sync(0xffffffffu, m, 0);
     beg = __shfl_sync(0xffffffffu, beg, 0);
     end = __shfl_sync(0xffffffffu, end, 0);
-    if (Op::live(m)) {
-      for (int e = beg + lane; e < end; e += 32) Op::scatter(a.edges, e, m, a.delta);
-    }
+    if (Op::live(m)) scatter_range<Op, 32>(a.edges, beg + lane, end, m, a.delta);
   }
 
   // Small vertices: 32 per warp step; their edges are gathered into one
-  // index space [0, total) and walked 32 at a time.
+  // index space [0, total) and walked 32 x kUnroll at a time.
   for (int base = warp * 32; base < cS; base += nwarps * 32) {
     const int i = base + lane;
     Msg m{};
@@ -260,32 +342,60 @@ __global__ void __launch_bounds__(BLOCK) k_push(KArgs<Op> a) {
       m = Op::fold(j, deg, a.delta, a.v, a.coef, a.damping);
       if (!Op::live(m)) deg = 0;
     }
-    int incl = deg;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
+    const int incl = warp_incl_scan(deg, lane);
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     const int excl = incl - deg;
-    for (int t0 = 0; t0 < total; t0 += 32) {
-      const int t = t0 + lane;
-      // owner = number of lanes whose inclusive prefix is <= t
-      int owner = 0;
+    for (int t0 = 0; t0 < total; t0 += 32 * kUnroll) {
+      typename Op::Edge ed[kUnroll];
+      Msg om[kUnroll];
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int probe = __shfl_sync(0xffffffffu, incl, owner + step - 1);
-        if (probe <= t) owner += step;
+      for (int u = 0; u < kUnroll; ++u) {
+        const int t = t0 + u * 32 + lane;
+        // owner = number of lanes whose inclusive prefix is <= t
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int probe = __shfl_sync(0xffffffffu, incl, owner + step - 1);
+          if (probe <= t) owner += step;
+        }
+        const int ob = __shfl_sync(0xffffffffu, beg, owner);
+        const int oe = __shfl_sync(0xffffffffu, excl, owner);
+        om[u] = __shfl_sync(0xffffffffu, m, owner);
+        if (t < total) ed[u] = Op::load(a.edges, static_cast<int64_t>(ob) + (t - oe));
       }
-      const int ob = __shfl_sync(0xffffffffu, beg, owner);
-      const int oe = __shfl_sync(0xffffffffu, excl, owner);
-      const Msg om = __shfl_sync(0xffffffffu, m, owner);
-      if (t < total) Op::scatter(a.edges, static_cast<int64_t>(ob) + (t - oe), om, a.delta);
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        if (t0 + u * 32 + lane < total) Op::apply(ed[u], om[u], a.delta);
     }
   }
 }
 
 // ------------------------------------------------------------- utilities
+
+// Mixed precision: the end of the FP64-delta warm-up phase.  Rounds every
+// delta to FP32 once and re-arms the control block for the FP32 phase, which
+// runs only if the warm-up ended by its residual test (not by the round cap).
+static __global__ void k_to_f32(const double* __restrict__ d64, float* __restrict__ d32, int64_t n,
+                                DevCtl* ctl, cudaGraphConditionalHandle cond, int use_cond) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    d32[i] = static_cast<float>(d64[i]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int st = ctl->status;
+    ctl->status = (st == 1) ? 0 : st;
+    ctl->phase = (st == 1) ? 1 : 0;
+    ctl->eps_eff = ctl->eps;
+    ctl->switch_frac = 0.0;
+    for (int s = 0; s < 2; ++s)
+      for (int b = 0; b < 4; ++b) ctl->cnt[s][b] = 0;
+    ctl->rset = 0;
+    ctl->wset = 0;
+    ctl->ticket = 0;
+    ctl->resid_acc = 0.0;
+    ctl->act_acc = ctl->push_acc = ctl->pend_acc = 0;
+    if (use_cond) cudaGraphSetConditional(cond, st == 1 ? 1u : 0u);
+  }
+}
 
 template <class T>
 __global__ void k_fill(T* __restrict__ x, int64_t n, T value) {

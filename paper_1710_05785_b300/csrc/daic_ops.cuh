@@ -23,65 +23,73 @@ struct EdgeCtx {
   const uint32_t* __restrict__ w;
 };
 
-// ------------------------------------------------------------------ + FP64
-struct OpSumF64 {
+__device__ __forceinline__ double atomic_take(double* p) {
+  unsigned long long bits = atomicExch(reinterpret_cast<unsigned long long*>(p), 0ull);
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+__device__ __forceinline__ float atomic_take(float* p) { return atomicExch(p, 0.0f); }
+
+// ------------------------------------------------------------------ + (sum)
+// State v in FP64; delta in DT (double or float); coefficients in CT.  The
+// message c_j * Delta_j is formed in FP64 and rounded once to DT.
+template <class DT, class CT>
+struct OpSum {
   using V = double;
-  using D = double;
-  using C = double;
-  using Msg = double;
+  using D = DT;
+  using C = CT;
+  using Msg = DT;
   static constexpr bool kIsSum = true;
 
   // Pending-priority |v_j (+) Delta_j - v_j| = |Delta_j| (Section 3.5).
-  __device__ static __forceinline__ double priority(D d, V) { return fabs(d); }
-  __device__ static __forceinline__ bool pending(D d, V) { return d != 0.0; }
+  __device__ static __forceinline__ double priority(D d, V) { return fabs(static_cast<double>(d)); }
+  __device__ static __forceinline__ bool pending(D d, V) { return d != D(0); }
 
   // Read-and-reset Delta_j atomically so a message that lands between the
   // read and the reset cannot be lost; fold it into v_j.  The update of a
   // vertex is owned by one thread per round, so v_j needs no atomic.
   __device__ static __forceinline__ Msg fold(int j, int deg, D* delta, V* v, const C* coef,
                                              double damping) {
-    unsigned long long bits =
-        atomicExch(reinterpret_cast<unsigned long long*>(delta + j), 0ull);
-    double d = __longlong_as_double(static_cast<long long>(bits));
-    if (d == 0.0) return 0.0;
-    v[j] += d;
-    if (deg == 0) return 0.0;
-    double c = coef ? coef[j] : damping / static_cast<double>(deg);
-    return c * d;
-  }
-  __device__ static __forceinline__ bool live(Msg m) { return m != 0.0; }
-  __device__ static __forceinline__ void scatter(const EdgeCtx& g, int64_t e, Msg m, D* delta) {
-    int k = __ldcs(g.col + e);
-    atomicAdd(delta + k, m);
-  }
-};
-
-// ------------------------------------------ + with FP32 deltas, FP64 state
-struct OpSumMixed {
-  using V = double;
-  using D = float;
-  using C = float;
-  using Msg = float;
-  static constexpr bool kIsSum = true;
-
-  __device__ static __forceinline__ double priority(D d, V) { return fabs(static_cast<double>(d)); }
-  __device__ static __forceinline__ bool pending(D d, V) { return d != 0.0f; }
-
-  __device__ static __forceinline__ Msg fold(int j, int deg, D* delta, V* v, const C* coef,
-                                             double damping) {
-    float d = atomicExch(delta + j, 0.0f);
-    if (d == 0.0f) return 0.0f;
+    const D d = atomic_take(delta + j);
+    if (d == D(0)) return D(0);
     v[j] += static_cast<double>(d);
-    if (deg == 0) return 0.0f;
-    double c = coef ? static_cast<double>(coef[j]) : damping / static_cast<double>(deg);
-    return static_cast<float>(c * static_cast<double>(d));
+    if (deg == 0) return D(0);
+    const double c = coef ? static_cast<double>(coef[j]) : damping / static_cast<double>(deg);
+    return static_cast<D>(c * static_cast<double>(d));
   }
-  __device__ static __forceinline__ bool live(Msg m) { return m != 0.0f; }
+  // Large vertices are split into chunks processed by different CTAs, so
+  // their delta is taken in the frontier scan (atomic exchange, exact) and
+  // the state update happens once, by the CTA of chunk 0.
+  __device__ static __forceinline__ D take(int j, D* delta, const V*) {
+    return atomic_take(delta + j);
+  }
+  __device__ static __forceinline__ void untake(int j, D d, D* delta) {
+    if (d != D(0)) atomicAdd(delta + j, d);
+  }
+  __device__ static __forceinline__ Msg finish(int j, int deg, D d, V* v, const C* coef,
+                                               double damping, bool first_chunk) {
+    if (d == D(0)) return D(0);
+    if (first_chunk) v[j] += static_cast<double>(d);
+    if (deg == 0) return D(0);
+    const double c = coef ? static_cast<double>(coef[j]) : damping / static_cast<double>(deg);
+    return static_cast<D>(c * static_cast<double>(d));
+  }
+
+  __device__ static __forceinline__ bool live(Msg m) { return m != Msg(0); }
+  struct Edge { int k; };
+  __device__ static __forceinline__ Edge load(const EdgeCtx& g, int64_t e) {
+    return Edge{__ldcs(g.col + e)};
+  }
+  __device__ static __forceinline__ void apply(Edge ed, Msg m, D* delta) {
+    atomicAdd(delta + ed.k, m);
+  }
   __device__ static __forceinline__ void scatter(const EdgeCtx& g, int64_t e, Msg m, D* delta) {
-    int k = __ldcs(g.col + e);
-    atomicAdd(delta + k, m);
+    apply(load(g, e), m, delta);
   }
 };
+
+using OpSumF64 = OpSum<double, double>;     // all FP64
+using OpSumWarm = OpSum<double, float>;     // mixed precision, FP64-delta phase
+using OpSumMixed = OpSum<float, float>;     // mixed precision, FP32-delta phase
 
 // ------------------------------------------------ min over uint32 (SSSP)
 // g_{j,k}(x) = x + w_jk, saturating at infinity (Table 1, SSSP row).
@@ -110,13 +118,28 @@ struct OpMinU32 {
     v[j] = d;
     return d;
   }
+  // Large vertices: the scan only records Delta_j (nothing to undo); chunk
+  // 0's CTA folds it into v_j.
+  __device__ static __forceinline__ D take(int j, D* delta, const V*) { return __ldcg(delta + j); }
+  __device__ static __forceinline__ void untake(int, D, D*) {}
+  __device__ static __forceinline__ Msg finish(int j, int, D d, V* v, const C*, double,
+                                               bool first_chunk) {
+    if (first_chunk && d < v[j]) v[j] = d;
+    return d;
+  }
+
   __device__ static __forceinline__ bool live(Msg m) { return m != kInfU32; }
+  struct Edge { int k; uint32_t w; };
+  __device__ static __forceinline__ Edge load(const EdgeCtx& g, int64_t e) {
+    return Edge{__ldcs(g.col + e), __ldcs(g.w + e)};
+  }
+  __device__ static __forceinline__ void apply(Edge ed, Msg m, D* delta) {
+    const uint32_t s = m + ed.w;
+    const uint32_t nd = (s < m) ? kInfU32 : s;  // saturate: an overflowing message is infinity
+    if (nd < __ldcg(delta + ed.k)) atomicMin(delta + ed.k, nd);
+  }
   __device__ static __forceinline__ void scatter(const EdgeCtx& g, int64_t e, Msg m, D* delta) {
-    int k = __ldcs(g.col + e);
-    uint32_t wk = __ldcs(g.w + e);
-    uint32_t s = m + wk;
-    uint32_t nd = (s < m) ? kInfU32 : s;  // saturate: an overflowing message is infinity
-    if (nd < __ldcg(delta + k)) atomicMin(delta + k, nd);
+    apply(load(g, e), m, delta);
   }
 };
 

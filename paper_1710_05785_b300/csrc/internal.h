@@ -50,7 +50,7 @@ bool is_device_pointer(const void* p);
 // Degree cut-offs of the push kernel's three granularities and launch shape.
 struct Tuning {
   int cut_warp = 32;    // out-degree below this: warp-gathered small path
-  int cut_cta = 2048;   // out-degree at or above this: one CTA per vertex
+  int cut_cta = 512;    // out-degree at or above this: one CTA per kChunk edges
   int push_blocks_per_sm = 0;   // 0 = occupancy maximum
   int scan_blocks_per_sm = 4;
 };
@@ -73,8 +73,12 @@ struct maiter_result {
   int64_t n = 0;
   void* v = nullptr;           // n x V
   void* delta = nullptr;       // n x D
+  void* delta_wide = nullptr;  // n x double: FP64 deltas of the mixed run's warm-up phase
   void* coef = nullptr;        // n x C (allocated on first use)
-  int* list[maiter::kBuckets] = {nullptr, nullptr, nullptr};
+  int* list[2] = {nullptr, nullptr};   // small / medium frontier (n entries each)
+  int2* large = nullptr;               // large-vertex chunk entries
+  void* large_d = nullptr;             // their taken deltas (8 bytes per entry)
+  unsigned large_cap = 0;              // n + m / kChunk + 1 entries
   maiter::DevCtl* ctl = nullptr;
   maiter::DevCtl* h_ctl = nullptr;   // pinned mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

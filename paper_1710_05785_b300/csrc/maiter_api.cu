@@ -86,6 +86,7 @@ void maiter_params_default(maiter_run_params* p) {
   p->threshold = 0.0;
   p->top_frac = 0.01;
   p->eps = 1e-8;
+  p->mixed_switch = 0.01;
   p->max_rounds = 1000000;
   p->timeout_ms = 0;
   p->stream = nullptr;
@@ -177,8 +178,11 @@ void maiter_result_destroy(maiter_result* r) {
   if (r->graph) cudaGraphDestroy(r->graph);
   cudaFree(r->v);
   cudaFree(r->delta);
+  cudaFree(r->delta_wide);
   cudaFree(r->coef);
-  for (int b = 0; b < kBuckets; ++b) cudaFree(r->list[b]);
+  for (int b = 0; b < 2; ++b) cudaFree(r->list[b]);
+  cudaFree(r->large);
+  cudaFree(r->large_d);
   cudaFree(r->ctl);
   if (r->h_ctl) cudaFreeHost(r->h_ctl);
   if (r->ev0) cudaEventDestroy(r->ev0);
@@ -205,7 +209,12 @@ static maiter_status alloc_result(const maiter_graph* g, int op, maiter_result**
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&r->v, n * state_bytes(op));
   if (e == cudaSuccess) e = cudaMalloc(&r->delta, n * delta_bytes(op));
-  for (int b = 0; b < kBuckets && e == cudaSuccess; ++b) e = cudaMalloc(&r->list[b], n * sizeof(int));
+  if (e == cudaSuccess && op == MAITER_OP_SUM_MIXED) e = cudaMalloc(&r->delta_wide, n * sizeof(double));
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&r->list[b], n * sizeof(int));
+  // every large vertex contributes ceil(deg / kChunk) <= deg / kChunk + 1 entries
+  r->large_cap = static_cast<unsigned>(n + static_cast<size_t>(g->m) / kChunk + 1);
+  if (e == cudaSuccess) e = cudaMalloc(&r->large, sizeof(int2) * r->large_cap);
+  if (e == cudaSuccess) e = cudaMalloc(&r->large_d, sizeof(double) * r->large_cap);
   if (e == cudaSuccess) e = cudaMalloc(&r->ctl, sizeof(DevCtl));
   if (e == cudaSuccess) e = cudaMallocHost(&r->h_ctl, sizeof(DevCtl));
   if (e == cudaSuccess) e = cudaEventCreate(&r->ev0);
@@ -230,121 +239,76 @@ static int grid_for(const void* fn, int block, int num_sms, int per_sm_cap) {
 
 constexpr int kBlock = 256;
 
+// One phase of the round loop, WHILE(cond) { k_push ; k_scan }, for one
+// operator: its kernel arguments and launch shapes.
 template <class Op>
-static KArgs<Op> make_args(const maiter_graph* g, maiter_result* r, const void* coef,
-                           double damping, const Tuning& tu) {
+struct Phase {
   KArgs<Op> a{};
-  a.n = static_cast<int>(g->n);
-  a.rp = g->rp;
-  a.edges.col = g->col;
-  a.edges.w = g->w;
-  a.coef = static_cast<const typename Op::C*>(coef);
-  a.damping = damping;
-  a.v = static_cast<typename Op::V*>(r->v);
-  a.delta = static_cast<typename Op::D*>(r->delta);
-  for (int b = 0; b < kBuckets; ++b) a.list[b] = r->list[b];
-  a.ctl = r->ctl;
-  a.cut_warp = tu.cut_warp;
-  a.cut_cta = tu.cut_cta;
-  return a;
-}
+  int push_grid = 1, scan_grid = 1;
 
-// Builds the executable graph  WHILE(cond) { k_push ; k_scan }.  The first
-// body pass pushes an empty frontier (the control block starts with zero
-// counts) and k_scan builds the first one; k_scan's last block sets cond.
-template <class Op>
-static void loop_grids(const maiter_graph* g, const Tuning& tu, int* push_grid, int* scan_grid) {
-  *push_grid = grid_for(reinterpret_cast<const void*>(&k_push<Op, kBlock>), kBlock, g->num_sms,
-                        tu.push_blocks_per_sm);
-  int sg = g->num_sms * tu.scan_blocks_per_sm;
-  const int need = static_cast<int>((g->n + kBlock - 1) / kBlock);
-  if (need < sg) sg = need > 0 ? need : 1;
-  *scan_grid = sg;
-}
-
-template <class Op>
-static maiter_status build_loop(const maiter_graph* g, maiter_result* r, const void* coef,
-                                double damping, const Tuning& tu) {
-  if (r->exec) { cudaGraphExecDestroy(r->exec); r->exec = nullptr; }
-  if (r->graph) { cudaGraphDestroy(r->graph); r->graph = nullptr; }
-  KArgs<Op> a = make_args<Op>(g, r, coef, damping, tu);
-  int push_grid, scan_grid;
-  loop_grids<Op>(g, tu, &push_grid, &scan_grid);
-
-  MAITER_CUDA(cudaGraphCreate(&r->graph, 0));
-  cudaGraphConditionalHandle cond;
-  MAITER_CUDA(cudaGraphConditionalHandleCreate(&cond, r->graph, 1, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams np{};
-  np.type = cudaGraphNodeTypeConditional;
-  np.conditional.handle = cond;
-  np.conditional.type = cudaGraphCondTypeWhile;
-  np.conditional.size = 1;
-  cudaGraphNode_t node;
-  MAITER_CUDA(cudaGraphAddNode(&node, r->graph, nullptr, nullptr, 0, &np));
-  cudaGraph_t body = np.conditional.phGraph_out[0];
-
-  cudaStream_t cap;
-  MAITER_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-  cudaError_t e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0,
-                                                cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    k_push<Op, kBlock><<<push_grid, kBlock, 0, cap>>>(a);
-    k_scan<Op, kBlock><<<scan_grid, kBlock, 0, cap>>>(a, cond, 1);
-    cudaGraph_t captured = nullptr;
-    e = cudaStreamEndCapture(cap, &captured);
+  void setup(const maiter_graph* g, maiter_result* r, void* delta, const void* coef,
+             double damping, const Tuning& tu) {
+    a.n = static_cast<int>(g->n);
+    a.rp = g->rp;
+    a.edges.col = g->col;
+    a.edges.w = g->w;
+    a.coef = static_cast<const typename Op::C*>(coef);
+    a.damping = damping;
+    a.v = static_cast<typename Op::V*>(r->v);
+    a.delta = static_cast<typename Op::D*>(delta);
+    for (int b = 0; b < 2; ++b) a.list[b] = r->list[b];
+    a.large = r->large;
+    a.large_d = static_cast<typename Op::D*>(r->large_d);
+    a.large_cap = r->large_cap;
+    a.ctl = r->ctl;
+    a.cut_warp = tu.cut_warp;
+    a.cut_cta = tu.cut_cta;
+    push_grid = grid_for(reinterpret_cast<const void*>(&k_push<Op, kBlock>), kBlock, g->num_sms,
+                         tu.push_blocks_per_sm);
+    scan_grid = g->num_sms * tu.scan_blocks_per_sm;
+    const int need = static_cast<int>((g->n + kBlock - 1) / kBlock);
+    if (need < scan_grid) scan_grid = need > 0 ? need : 1;
   }
-  cudaStreamDestroy(cap);
-  MAITER_CUDA(e);
-  MAITER_CUDA(cudaGraphInstantiate(&r->exec, r->graph, 0));
-  return MAITER_OK;
-}
 
-template <class Op>
-static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
-                              maiter_result* r, cudaStream_t st) {
-  const Tuning tu{};
-  const void* coef = p->coef ? r->coef : nullptr;
-  // The executable graph bakes in the kernel arguments; rebuild it only when
-  // one of them changes.
-  uint64_t key = 1469598103934665603ull;
-  auto mix = [&](uint64_t x) { key = (key ^ x) * 1099511628211ull; };
-  uint64_t dbits;
-  std::memcpy(&dbits, &p->damping, sizeof(dbits));
-  mix(static_cast<uint64_t>(p->op));
-  mix(coef ? 1 : 0);
-  mix(dbits);
-  mix(static_cast<uint64_t>(tu.cut_warp));
-  mix(static_cast<uint64_t>(tu.cut_cta));
-  if (!r->exec || r->exec_key != key) {
-    maiter_status s = build_loop<Op>(g, r, coef, p->damping, tu);
-    if (s != MAITER_OK) return s;
-    r->exec_key = key;
+  void launch_round(cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) const {
+    k_push<Op, kBlock><<<push_grid, kBlock, 0, s>>>(a);
+    k_scan<Op, kBlock><<<scan_grid, kBlock, 0, s>>>(a, h, use_cond);
   }
-  DevCtl c{};
-  c.tau = (p->sched == MAITER_SCHED_THRESHOLD) ? p->threshold : 0.0;
-  c.eps = p->eps;
-  c.max_rounds = p->max_rounds > 0 ? p->max_rounds : 1000000;
-  c.sched = p->sched;
-  *r->h_ctl = c;
-  MAITER_CUDA(cudaMemcpyAsync(r->ctl, r->h_ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, st));
-  maiter_stats& s = r->stats;
-  s = maiter_stats{};
-  float ms = 0.f;
-  if (p->flags & MAITER_FLAG_PROFILE_KERNELS) {
-    // Host-driven loop: the same kernels and launch shapes as the graph body,
-    // each bracketed by events on the launching stream.
-    KArgs<Op> a = make_args<Op>(g, r, coef, p->damping, tu);
-    int push_grid, scan_grid;
-    loop_grids<Op>(g, tu, &push_grid, &scan_grid);
-    cudaEvent_t e[3];
-    for (auto& x : e) MAITER_CUDA(cudaEventCreate(&x));
-    MAITER_CUDA(cudaEventRecord(r->ev0, st));
+
+  // Adds WHILE(h) { k_push ; k_scan } after `deps` (graph mode).
+  maiter_status add_to(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps,
+                       cudaGraphConditionalHandle h, cudaGraphNode_t* node) const {
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    MAITER_CUDA(cudaGraphAddNode(node, graph, deps, nullptr, ndeps, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    cudaStream_t cap;
+    MAITER_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      launch_round(cap, h, 1);
+      cudaGraph_t captured = nullptr;
+      e = cudaStreamEndCapture(cap, &captured);
+    }
+    cudaStreamDestroy(cap);
+    MAITER_CUDA(e);
+    return MAITER_OK;
+  }
+
+  // Host-driven rounds with events around each launch (profiling mode).
+  maiter_status host_loop(maiter_result* r, cudaStream_t st, cudaEvent_t* e,
+                          maiter_stats& s) const {
     for (;;) {
       MAITER_CUDA(cudaEventRecord(e[0], st));
       k_push<Op, kBlock><<<push_grid, kBlock, 0, st>>>(a);
       MAITER_CUDA(cudaEventRecord(e[1], st));
       k_scan<Op, kBlock><<<scan_grid, kBlock, 0, st>>>(a, cudaGraphConditionalHandle{}, 0);
       MAITER_CUDA(cudaEventRecord(e[2], st));
+      MAITER_CUDA(cudaGetLastError());
       MAITER_CUDA(cudaMemcpyAsync(r->h_ctl, r->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
       MAITER_CUDA(cudaStreamSynchronize(st));
       float t1 = 0.f, t2 = 0.f;
@@ -354,11 +318,142 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
       s.scan_ms += t2;
       s.push_launches++;
       s.scan_launches++;
-      if (r->h_ctl->status != 0) break;
+      if (r->h_ctl->status != 0) return MAITER_OK;
+    }
+  }
+};
+
+// The mixed-precision run is two phases: FP64 deltas until the residual has
+// fallen to mixed_switch x its first value, one rounding of every delta to
+// FP32, then FP32 deltas to the end.  Both phases keep v and the residual
+// reduction in FP64.
+struct RunPlan {
+  bool mixed = false;
+  Phase<OpSumF64> f64;
+  Phase<OpSumWarm> warm;
+  Phase<OpSumMixed> f32;
+  Phase<OpMinU32> umin;
+};
+
+static maiter_status setup_plan(const maiter_graph* g, const maiter_run_params* p,
+                                maiter_result* r, const Tuning& tu, RunPlan* plan) {
+  const void* coef = p->coef ? r->coef : nullptr;
+  switch (p->op) {
+    case MAITER_OP_SUM_F64: plan->f64.setup(g, r, r->delta, coef, p->damping, tu); break;
+    case MAITER_OP_SUM_MIXED:
+      plan->mixed = true;
+      plan->warm.setup(g, r, r->delta_wide, coef, p->damping, tu);
+      plan->f32.setup(g, r, r->delta, coef, p->damping, tu);
+      break;
+    default: plan->umin.setup(g, r, r->delta, nullptr, 0.0, tu); break;
+  }
+  return MAITER_OK;
+}
+
+static int conversion_grid(const maiter_graph* g) { return g->num_sms * 4; }
+
+// Builds the executable graph of a run: WHILE{round} for one phase, or
+// WHILE{round FP64} -> k_to_f32 -> WHILE{round FP32} for mixed precision.
+// The first body pass of a phase pushes an empty frontier (its counts start
+// at zero) and its scan builds the first frontier.
+static maiter_status build_graph(const maiter_graph* g, maiter_result* r, int op,
+                                 const RunPlan& plan) {
+  if (r->exec) { cudaGraphExecDestroy(r->exec); r->exec = nullptr; }
+  if (r->graph) { cudaGraphDestroy(r->graph); r->graph = nullptr; }
+  MAITER_CUDA(cudaGraphCreate(&r->graph, 0));
+  cudaGraphConditionalHandle h1;
+  MAITER_CUDA(cudaGraphConditionalHandleCreate(&h1, r->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNode_t n1;
+  maiter_status s;
+  if (op == MAITER_OP_SUM_F64) s = plan.f64.add_to(r->graph, nullptr, 0, h1, &n1);
+  else if (op == MAITER_OP_SUM_MIXED) s = plan.warm.add_to(r->graph, nullptr, 0, h1, &n1);
+  else s = plan.umin.add_to(r->graph, nullptr, 0, h1, &n1);
+  if (s != MAITER_OK) return s;
+  if (op == MAITER_OP_SUM_MIXED) {
+    cudaGraphConditionalHandle h2;
+    MAITER_CUDA(cudaGraphConditionalHandleCreate(&h2, r->graph, 0, 0));
+    const double* d64 = static_cast<const double*>(r->delta_wide);
+    float* d32 = static_cast<float*>(r->delta);
+    int64_t n = g->n;
+    DevCtl* ctl = r->ctl;
+    int use_cond = 1;
+    void* args[] = {&d64, &d32, &n, &ctl, &h2, &use_cond};
+    cudaKernelNodeParams kp{};
+    kp.func = reinterpret_cast<void*>(&k_to_f32);
+    kp.gridDim = dim3(conversion_grid(g));
+    kp.blockDim = dim3(256);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    cudaGraphNode_t kn, n3;
+    MAITER_CUDA(cudaGraphAddKernelNode(&kn, r->graph, &n1, 1, &kp));
+    s = plan.f32.add_to(r->graph, &kn, 1, h2, &n3);
+    if (s != MAITER_OK) return s;
+  }
+  MAITER_CUDA(cudaGraphInstantiate(&r->exec, r->graph, 0));
+  return MAITER_OK;
+}
+
+static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
+                              maiter_result* r, cudaStream_t st) {
+  const Tuning tu{};
+  RunPlan plan;
+  setup_plan(g, p, r, tu, &plan);
+  // The executable graph bakes in the kernel arguments; rebuild it only when
+  // one of them changes.
+  uint64_t key = 1469598103934665603ull;
+  auto mix = [&](uint64_t x) { key = (key ^ x) * 1099511628211ull; };
+  uint64_t dbits;
+  std::memcpy(&dbits, &p->damping, sizeof(dbits));
+  mix(static_cast<uint64_t>(p->op));
+  mix(p->coef ? 1 : 0);
+  mix(dbits);
+  mix(static_cast<uint64_t>(tu.cut_warp));
+  mix(static_cast<uint64_t>(tu.cut_cta));
+  const bool profile = (p->flags & MAITER_FLAG_PROFILE_KERNELS) != 0;
+  if (!profile && (!r->exec || r->exec_key != key)) {
+    maiter_status s = build_graph(g, r, p->op, plan);
+    if (s != MAITER_OK) return s;
+    r->exec_key = key;
+  }
+  DevCtl c{};
+  c.tau = (p->sched == MAITER_SCHED_THRESHOLD) ? p->threshold : 0.0;
+  c.eps = p->eps;
+  c.eps_eff = p->eps;
+  c.switch_frac = plan.mixed ? p->mixed_switch : 0.0;
+  c.max_rounds = p->max_rounds > 0 ? p->max_rounds : 1000000;
+  c.sched = p->sched;
+  *r->h_ctl = c;
+  MAITER_CUDA(cudaMemcpyAsync(r->ctl, r->h_ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, st));
+  maiter_stats& s = r->stats;
+  s = maiter_stats{};
+  float ms = 0.f;
+  if (profile) {
+    // Host-driven loop: the same kernels and launch shapes as the graph body,
+    // each bracketed by events on the launching stream.
+    cudaEvent_t e[3];
+    for (auto& x : e) MAITER_CUDA(cudaEventCreate(&x));
+    MAITER_CUDA(cudaEventRecord(r->ev0, st));
+    maiter_status ls;
+    if (p->op == MAITER_OP_SUM_F64) {
+      ls = plan.f64.host_loop(r, st, e, s);
+    } else if (p->op == MAITER_OP_SUM_MIXED) {
+      ls = plan.warm.host_loop(r, st, e, s);
+      if (ls == MAITER_OK) {
+        k_to_f32<<<conversion_grid(g), 256, 0, st>>>(static_cast<const double*>(r->delta_wide),
+                                                     static_cast<float*>(r->delta), g->n,
+                                                     r->ctl, cudaGraphConditionalHandle{}, 0);
+        MAITER_CUDA(cudaGetLastError());
+        MAITER_CUDA(cudaMemcpyAsync(r->h_ctl, r->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+        MAITER_CUDA(cudaStreamSynchronize(st));
+        if (r->h_ctl->status == 0) ls = plan.f32.host_loop(r, st, e, s);
+      }
+    } else {
+      ls = plan.umin.host_loop(r, st, e, s);
     }
     MAITER_CUDA(cudaEventRecord(r->ev1, st));
     MAITER_CUDA(cudaStreamSynchronize(st));
     for (auto& x : e) cudaEventDestroy(x);
+    if (ls != MAITER_OK) return ls;
   } else {
     MAITER_CUDA(cudaEventRecord(r->ev0, st));
     MAITER_CUDA(cudaGraphLaunch(r->exec, st));
@@ -374,7 +469,9 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   s.residual = h.residual;
   s.elapsed_ms = ms;
   s.converged = h.status == 1;
-  s.kernel_launches += 2 * static_cast<int64_t>(h.rounds + 1);
+  // every phase that ran ends with one scan that did not continue
+  const int64_t phases = 1 + (h.phase > 0 ? 1 : 0);
+  s.kernel_launches += 2 * (static_cast<int64_t>(h.rounds) + phases) + (plan.mixed ? 1 : 0);
   s.status = h.status == 1 ? MAITER_OK : MAITER_ERR_NOT_CONVERGED;
   if (h.status != 1) {
     set_error("round cap of %lld reached before the termination test held (residual %g)",
@@ -384,26 +481,23 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
 }
 
 // Initial v and Delta: copies when given, else the defaults of Table 1.
-template <class Op>
-static maiter_status init_state(const maiter_graph* g, const maiter_run_params* p,
-                                maiter_result* r, cudaStream_t st, int* launches) {
-  *launches = 0;
-  using V = typename Op::V;
-  using D = typename Op::D;
+template <class V, class D>
+static maiter_status init_state(const maiter_graph* g, const maiter_run_params* p, void* vbuf,
+                                void* dbuf, bool is_sum, cudaStream_t st, int* launches) {
   const int64_t n = g->n;
   if (n == 0) return MAITER_OK;
   const int blocks = g->num_sms * 4;
-  V* v = static_cast<V*>(r->v);
-  D* d = static_cast<D*>(r->delta);
+  V* v = static_cast<V*>(vbuf);
+  D* d = static_cast<D*>(dbuf);
   if (p->v0) {
     MAITER_CUDA(cudaMemcpyAsync(v, p->v0, sizeof(V) * n, cudaMemcpyDefault, st));
   } else {
-    k_fill<V><<<blocks, 256, 0, st>>>(v, n, Op::kIsSum ? V(0) : V(kInfU32));
+    k_fill<V><<<blocks, 256, 0, st>>>(v, n, is_sum ? V(0) : V(kInfU32));
     ++*launches;
   }
   if (p->delta0) {
     MAITER_CUDA(cudaMemcpyAsync(d, p->delta0, sizeof(D) * n, cudaMemcpyDefault, st));
-  } else if (Op::kIsSum) {
+  } else if (is_sum) {
     k_fill<D><<<blocks, 256, 0, st>>>(d, n, static_cast<D>(1.0 - p->damping));
     ++*launches;
   } else {
@@ -411,27 +505,37 @@ static maiter_status init_state(const maiter_graph* g, const maiter_run_params* 
     k_fill<D><<<1, 32, 0, st>>>(d + p->source, 1, D(0));
     *launches += 2;
   }
-  if (p->coef) {
-    if (!r->coef) MAITER_CUDA(cudaMalloc(&r->coef, coef_bytes(r->op) * n));
-    MAITER_CUDA(cudaMemcpyAsync(r->coef, p->coef, coef_bytes(r->op) * n, cudaMemcpyDefault, st));
-  }
   MAITER_CUDA(cudaGetLastError());
   return MAITER_OK;
 }
 
-template <class Op>
 static maiter_status run_op(const maiter_graph* g, const maiter_run_params* p, maiter_result* r,
                             cudaStream_t st) {
   int init_launches = 0;
-  maiter_status s = init_state<Op>(g, p, r, st, &init_launches);
+  maiter_status s;
+  switch (p->op) {
+    case MAITER_OP_SUM_F64:
+      s = init_state<double, double>(g, p, r->v, r->delta, true, st, &init_launches);
+      break;
+    case MAITER_OP_SUM_MIXED:
+      s = init_state<double, double>(g, p, r->v, r->delta_wide, true, st, &init_launches);
+      break;
+    default:
+      s = init_state<uint32_t, uint32_t>(g, p, r->v, r->delta, false, st, &init_launches);
+      break;
+  }
   if (s != MAITER_OK) return s;
+  if (p->coef && g->n > 0) {
+    if (!r->coef) MAITER_CUDA(cudaMalloc(&r->coef, coef_bytes(r->op) * g->n));
+    MAITER_CUDA(cudaMemcpyAsync(r->coef, p->coef, coef_bytes(r->op) * g->n, cudaMemcpyDefault, st));
+  }
   if (g->n == 0) {
     r->stats = maiter_stats{};
     r->stats.converged = 1;
     r->stats.kernel_launches = init_launches;
     return MAITER_OK;
   }
-  s = run_sync<Op>(g, p, r, st);
+  s = run_sync(g, p, r, st);
   r->stats.kernel_launches += init_launches;
   return s;
 }
@@ -455,6 +559,8 @@ maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p, mait
     MAITER_REQUIRE(p->coef || std::isfinite(p->damping),
                    "damping must be finite when coef is NULL");
     MAITER_REQUIRE(std::isfinite(p->eps) && p->eps >= 0.0, "eps must be finite and >= 0");
+    MAITER_REQUIRE(p->op != MAITER_OP_SUM_MIXED || (p->mixed_switch >= 0.0 && p->mixed_switch <= 1.0),
+                   "mixed_switch must lie in [0, 1]");
     MAITER_REQUIRE(p->sched != MAITER_SCHED_THRESHOLD ||
                        (std::isfinite(p->threshold) && p->threshold >= 0.0),
                    "threshold must be finite and >= 0");
@@ -482,9 +588,7 @@ maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p, mait
   cudaStream_t st = static_cast<cudaStream_t>(p->stream);
   maiter_status s;
   switch (p->op) {
-    case MAITER_OP_SUM_F64: s = run_op<OpSumF64>(g, p, r, st); break;
-    case MAITER_OP_SUM_MIXED: s = run_op<OpSumMixed>(g, p, r, st); break;
-    default: s = run_op<OpMinU32>(g, p, r, st); break;
+    default: s = run_op(g, p, r, st); break;
   }
   if (s == MAITER_OK || s == MAITER_ERR_NOT_CONVERGED) {
     *out = r;

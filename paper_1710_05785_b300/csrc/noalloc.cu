@@ -25,7 +25,8 @@ namespace {
 
 constexpr int64_t kNoallocMaxN = int64_t(1) << 20;   // vertices
 constexpr size_t kCtlBytes = 256;
-constexpr size_t kScratchBytes = kCtlBytes + sizeof(int) * kBuckets * size_t(kNoallocMaxN);
+constexpr int kNoallocLists = 3;   // small and medium lists, plus one spare list slot
+constexpr size_t kScratchBytes = kCtlBytes + sizeof(int) * kNoallocLists * size_t(kNoallocMaxN);
 // slot layout: [DevCtl | ... | validation flag (last 4 bytes)]
 static_assert(sizeof(DevCtl) + sizeof(unsigned) <= kCtlBytes, "control block must fit its slot");
 
@@ -168,10 +169,15 @@ extern "C" maiter_status maiter_sssp_noalloc(int64_t n, int64_t m, const int32_t
   a.damping = 0.0;
   a.v = v_out;
   a.delta = delta_out;
-  for (int b = 0; b < kBuckets; ++b) a.list[b] = lists + size_t(b) * kNoallocMaxN;
+  for (int b = 0; b < 2; ++b) a.list[b] = lists + size_t(b) * kNoallocMaxN;
+  // No chunked large-vertex path here: its entry count grows with m, which a
+  // fixed array cannot bound, so every vertex of degree >= 32 takes the warp path.
+  a.large = nullptr;
+  a.large_d = nullptr;
+  a.large_cap = 0;
   a.ctl = ctl;
   a.cut_warp = 32;
-  a.cut_cta = 2048;
+  a.cut_cta = 1 << 30;
 
   DevCtl h{};
   for (;;) {

@@ -73,6 +73,7 @@ int main(void) {
   F(maiter_stats, residual); F(maiter_stats, elapsed_ms); F(maiter_stats, status);
   F(maiter_stats, converged); F(maiter_stats, kernel_launches); F(maiter_stats, push_ms);
   F(maiter_stats, scan_launches); F(maiter_run_params, flags);
+  F(maiter_run_params, mixed_switch);
   return 0;
 }
 ''')
