@@ -293,6 +293,7 @@ def main():
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "push_launches": push_launches,
                      "push_ms_per_launch": push_ms / max(push_launches, 1),
+                     "scan_ms_per_launch": sum(p["scan_ms"] for p in prof) / max(push_launches, 1),
                      "alg_bytes_per_launch": alg_bytes / max(push_launches, 1)},
         "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

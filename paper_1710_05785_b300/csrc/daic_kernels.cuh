@@ -30,6 +30,7 @@ namespace maiter {
 constexpr int kBuckets = 3;
 constexpr int kChunk = 1024;   // edges per large-vertex work item (one CTA, 4 per thread)
 constexpr int kUnroll = 4;
+constexpr int kScanItems = 4;  // vertices per thread per k_scan tile
 
 // Device-resident control block of one run.  Everything the round loop needs
 // to decide on its own lives here, so the loop never returns to the host.
@@ -107,68 +108,99 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
   const unsigned ws = ctl->wset;
   const double tau = ctl->tau;
   const int lane = threadIdx.x & 31;
-  const unsigned lt_mask = (1u << lane) - 1u;
+  const int wid = threadIdx.x >> 5;
+  constexpr int kWarps = BLOCK / 32;
+  constexpr int kItems = kScanItems;         // vertices per thread per tile
+  constexpr int kTile = BLOCK * kItems;
 
   double rsum = 0.0;
   unsigned long long nact = 0, npush = 0, npend = 0;
+  __shared__ int s_woff[3][kWarps];          // per-warp exclusive offsets, per bucket
+  __shared__ unsigned s_base[3];             // the tile's base position, per bucket
 
-  // Warps walk 32 consecutive vertices at a time: coalesced loads, and each
-  // ballot covers one aligned group so compaction needs one atomic per bucket.
-  const int stride = gridDim.x * BLOCK;
-  for (int base = blockIdx.x * BLOCK + (threadIdx.x & ~31); base < a.n; base += stride) {
-    const int j = base + lane;
-    bool sel = false;
-    int deg = 0;
-    if (j < a.n) {
-      const D d = a.delta[j];
-      const typename Op::V vv = Op::kIsSum ? typename Op::V(0) : a.v[j];
-      const bool pend = Op::pending(d, vv);
-      npend += pend;
-      if (Op::kIsSum) {
-        const double p = Op::priority(d, vv);
-        rsum += p;
-        sel = pend && p > tau;
-      } else {
-        sel = pend;
-      }
-      if (sel) deg = __ldg(a.rp + j + 1) - __ldg(a.rp + j);
-    }
-    const int bucket = !sel ? -1 : (deg < a.cut_warp ? 0 : (deg < a.cut_cta ? 1 : 2));
+  // Each block walks tiles of kTile consecutive vertices (item u of thread t
+  // is vertex tile + u*BLOCK + t: coalesced).  A tile's selections are
+  // counted, prefix-summed across the block, and reserved with one atomic
+  // per bucket, then written: compaction costs three atomics per tile.
+  for (int tile = blockIdx.x * kTile; tile < a.n; tile += gridDim.x * kTile) {
+    int bkt[kItems], dg[kItems];
+    int cnt[3] = {0, 0, 0};
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const bool mine = bucket == b;
-      const unsigned mask = __ballot_sync(0xffffffffu, mine);
-      if (mask) {
-        const int leader = __ffs(mask) - 1;
-        unsigned pos = 0;
-        if (lane == leader) pos = atomicAdd(&ctl->cnt[ws][b], static_cast<unsigned>(__popc(mask)));
-        pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (mine) a.list[b][pos + __popc(mask & lt_mask)] = j;
+    for (int u = 0; u < kItems; ++u) {
+      const int j = tile + u * BLOCK + static_cast<int>(threadIdx.x);
+      bkt[u] = -1;
+      dg[u] = 0;
+      if (j < a.n) {
+        const D d = a.delta[j];
+        const typename Op::V vv = Op::kIsSum ? typename Op::V(0) : a.v[j];
+        const bool pend = Op::pending(d, vv);
+        npend += pend;
+        bool sel;
+        if (Op::kIsSum) {
+          const double p = Op::priority(d, vv);
+          rsum += p;
+          sel = pend && p > tau;
+        } else {
+          sel = pend;
+        }
+        if (sel) {
+          const int deg = __ldg(a.rp + j + 1) - __ldg(a.rp + j);
+          const int b = deg < a.cut_warp ? 0 : (deg < a.cut_cta ? 1 : 2);
+          bkt[u] = b;
+          dg[u] = deg;
+          cnt[0] += (b == 0);
+          cnt[1] += (b == 1);
+          cnt[2] += (b == 2) ? (deg + kChunk - 1) / kChunk : 0;
+          ++nact;
+          npush += static_cast<unsigned long long>(deg);
+        }
       }
     }
-    // Large vertices: one entry per chunk; their delta is taken here.
-    const int chunks = (bucket == 2) ? (deg + kChunk - 1) / kChunk : 0;
-    if (__ballot_sync(0xffffffffu, chunks > 0)) {
-      const int incl = warp_incl_scan(chunks, lane);
-      const int total = __shfl_sync(0xffffffffu, incl, 31);
-      unsigned base_pos = 0;
-      if (lane == 31) base_pos = atomicAdd(&ctl->cnt[ws][2], static_cast<unsigned>(total));
-      base_pos = __shfl_sync(0xffffffffu, base_pos, 31);
-      if (chunks > 0) {
-        const unsigned p0 = base_pos + static_cast<unsigned>(incl - chunks);
-        if (p0 + static_cast<unsigned>(chunks) <= a.large_cap) {
+    int incl[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      incl[b] = warp_incl_scan(cnt[b], lane);
+      if (lane == 31) s_woff[b][wid] = incl[b];
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      const int b = threadIdx.x;
+      int run = 0;
+      for (int w = 0; w < kWarps; ++w) {
+        const int t = s_woff[b][w];
+        s_woff[b][w] = run;
+        run += t;
+      }
+      s_base[b] = run ? atomicAdd(&ctl->cnt[ws][b], static_cast<unsigned>(run)) : 0u;
+    }
+    __syncthreads();
+    unsigned pos[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      pos[b] = s_base[b] + static_cast<unsigned>(s_woff[b][wid] + incl[b] - cnt[b]);
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+      const int j = tile + u * BLOCK + static_cast<int>(threadIdx.x);
+      if (bkt[u] == 0) {
+        a.list[0][pos[0]++] = j;
+      } else if (bkt[u] == 1) {
+        a.list[1][pos[1]++] = j;
+      } else if (bkt[u] == 2) {
+        // Large vertex: one entry per chunk; its delta is taken here.
+        const int chunks = (dg[u] + kChunk - 1) / kChunk;
+        if (pos[2] + static_cast<unsigned>(chunks) <= a.large_cap) {
           const D d = Op::take(j, a.delta, a.v);
           for (int q = 0; q < chunks; ++q) {
-            a.large[p0 + q] = make_int2(j, q);
-            a.large_d[p0 + q] = d;
+            a.large[pos[2] + q] = make_int2(j, q);
+            a.large_d[pos[2] + q] = d;
           }
         } else {
           atomicOr(&ctl->overflow, 1u);
         }
+        pos[2] += static_cast<unsigned>(chunks);
       }
     }
-    nact += sel;
-    npush += static_cast<unsigned long long>(deg);
+    __syncthreads();   // s_woff / s_base are reused by the next tile
   }
 
   // Block reduction, one atomic per block per counter.
@@ -180,7 +212,6 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
   nact = warp_sum(nact);
   npush = warp_sum(npush);
   npend = warp_sum(npend);
-  const int wid = threadIdx.x >> 5;
   if (lane == 0) { s_r[wid] = rsum; s_a[wid] = nact; s_p[wid] = npush; s_q[wid] = npend; }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -286,7 +317,7 @@ __device__ __forceinline__ void scatter_range(const EdgeCtx& g, int e, int end,
 }
 
 template <class Op, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_push(KArgs<Op> a) {
+__global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a) {
   using Msg = typename Op::Msg;
   const DevCtl* ctl = a.ctl;
   const unsigned rs = ctl->rset;
