@@ -88,18 +88,31 @@ typedef enum {
 } maiter_sched;
 
 typedef enum {
-  MAITER_ENGINE_SYNC = 0      /* round loop: frontier, then push; the loop and its
+  MAITER_ENGINE_SYNC = 0,     /* round loop: frontier, then push; the loop and its
                                  termination test run on the device (CUDA graph
                                  with a conditional node), no host round trip */
+  MAITER_ENGINE_ASYNC = 1     /* persistent kernel over a device work queue: warps
+                                 take queued vertices, update them and re-queue
+                                 receivers whose delta crosses the threshold (ALL:
+                                 eps / (2n)), with no barrier between CTAs (Eq. 5,
+                                 Section 3.2).  Between launches an exact device
+                                 reduction tests termination and re-seeds the queue
+                                 (the periodic check of Section 5.1).  SUM_F64 and
+                                 MIN_U32; schedules ALL and THRESHOLD. */
 } maiter_engine;
 
 /* Run flags (bit set). */
 typedef enum {
-  MAITER_FLAG_PROFILE_KERNELS = 1  /* drive the round loop from the host, one
+  MAITER_FLAG_PROFILE_KERNELS = 1, /* drive the round loop from the host, one
                                       launch per kernel with CUDA events around
                                       each, and report per-kernel device time in
                                       maiter_stats (same kernels and launch
                                       shapes; one host sync per round) */
+  MAITER_FLAG_INJECT_STALL = 2     /* ASYNC, for testing the bounded waits: the
+                                      first queue launch gets a phantom pending
+                                      item that nothing completes, so its idle
+                                      warps wait timeout_ms and the run returns
+                                      MAITER_ERR_TIMEOUT (no fault, no hang) */
 } maiter_flags;
 
 typedef struct maiter_run_params {
@@ -133,7 +146,9 @@ typedef struct maiter_run_params {
                           vertex of in-degree k, which is why the large early
                           deltas are accumulated in FP64. */
   int64_t max_rounds;  /* round cap; <= 0 means 1,000,000 */
-  int64_t timeout_ms;  /* reserved for bounded device waits; 0 = default */
+  int64_t timeout_ms;  /* ASYNC: budget of every bounded device wait per launch
+                          (0 = 10,000 ms); when it runs out the run returns
+                          MAITER_ERR_TIMEOUT with a valid, resumable state */
   void* stream;        /* cudaStream_t to run on; NULL = the default stream */
 } maiter_run_params;
 
@@ -170,9 +185,12 @@ void maiter_graph_destroy(maiter_graph* g);
 /* Runs a DAIC to termination (Eq. 5 updates, Section 3.5 schedules).
  * If *out is NULL a new result is allocated; otherwise *out must be a result
  * earlier returned for this graph and is reused without allocation (its
- * previous state is overwritten).  The result is left readable on every
- * return except INVALID_ARG/OOM, including NOT_CONVERGED.
- * Errors: INVALID_ARG, OOM, CUDA, NOT_CONVERGED, UNSUPPORTED. */
+ * previous state is overwritten).  On OK, NOT_CONVERGED and TIMEOUT, *out
+ * holds a readable result whose (v, Delta) is a valid DAIC state (it can be
+ * passed back as v0/delta0 to resume); on other errors a freshly allocated
+ * result is freed and *out is left as it was.  A result may be destroyed
+ * before or after its graph; a graph must outlive every run on it.
+ * Errors: INVALID_ARG, OOM, CUDA, NOT_CONVERGED, TIMEOUT, UNSUPPORTED. */
 maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p,
                          maiter_result** out);
 

@@ -33,8 +33,8 @@ _STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CON
 OP_SUM_F64, OP_SUM_MIXED, OP_MIN_U32 = 0, 1, 2
 G_SCALE_BY_SRC, G_ADD_EDGE = 0, 1
 SCHED_ALL, SCHED_THRESHOLD, SCHED_TOPFRAC = 0, 1, 2
-ENGINE_SYNC = 0
-FLAG_PROFILE_KERNELS = 1
+ENGINE_SYNC, ENGINE_ASYNC = 0, 1
+FLAG_PROFILE_KERNELS, FLAG_INJECT_STALL = 1, 2
 
 INF32 = 0xFFFFFFFF
 
@@ -267,7 +267,8 @@ def run(graph: Graph, op: int = OP_SUM_F64, *, coef=None, damping: float = 0.8, 
     p.max_rounds, p.timeout_ms = max_rounds, timeout_ms
     p.stream = stream
     h = ctypes.c_void_p(result.handle.value if result is not None else None)
-    allow = (OK, ERR_NOT_CONVERGED) if allow_not_converged else (OK,)
+    # both leave a readable, resumable state
+    allow = (OK, ERR_NOT_CONVERGED, ERR_TIMEOUT) if allow_not_converged else (OK,)
     st = lib().maiter_run(graph.handle, ctypes.byref(p), ctypes.byref(h))
     if result is None and h.value:
         result = Result(h, graph, op)

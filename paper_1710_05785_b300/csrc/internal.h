@@ -8,6 +8,7 @@
 
 #include "../../include/maiter.h"
 #include "daic_kernels.cuh"
+#include "async_kernels.cuh"
 
 namespace maiter {
 
@@ -86,5 +87,21 @@ struct maiter_result {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   uint64_t exec_key = 0;
+  // asynchronous engine (allocated on its first use)
+  int* aqueue = nullptr;               // ring of vertex ids, acap slots
+  unsigned long long acap = 0;
+  unsigned int* inq = nullptr;         // n in-queue flags
+  maiter::AsyncCtl* actl = nullptr;
+  maiter::AsyncCtl* h_actl = nullptr;  // pinned mirror
+  cudaGraph_t agraph = nullptr;
+  cudaGraphExec_t aexec = nullptr;
+  uint64_t aexec_key = 0;
   maiter_stats stats{};
 };
+
+namespace maiter {
+// Persistent asynchronous engine (async_engine.cu); v and Delta are initialised.
+maiter_status run_async(const maiter_graph* g, const maiter_run_params* p, maiter_result* r,
+                        cudaStream_t st);
+void free_async(maiter_result* r);
+}  // namespace maiter

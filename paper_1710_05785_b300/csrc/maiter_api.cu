@@ -184,6 +184,7 @@ void maiter_result_destroy(maiter_result* r) {
   cudaFree(r->large);
   cudaFree(r->large_d);
   cudaFree(r->ctl);
+  free_async(r);
   if (r->h_ctl) cudaFreeHost(r->h_ctl);
   if (r->ev0) cudaEventDestroy(r->ev0);
   if (r->ev1) cudaEventDestroy(r->ev1);
@@ -536,7 +537,7 @@ static maiter_status run_op(const maiter_graph* g, const maiter_run_params* p, m
     r->stats.kernel_launches = init_launches;
     return MAITER_OK;
   }
-  s = run_sync(g, p, r, st);
+  s = (p->engine == MAITER_ENGINE_ASYNC) ? run_async(g, p, r, st) : run_sync(g, p, r, st);
   r->stats.kernel_launches += init_launches;
   return s;
 }
@@ -552,8 +553,15 @@ maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p, mait
   const bool is_sum = p->op != MAITER_OP_MIN_U32;
   MAITER_REQUIRE(p->sched >= MAITER_SCHED_ALL && p->sched <= MAITER_SCHED_TOPFRAC,
                  "unknown sched %d", p->sched);
-  MAITER_REQUIRE(p->engine == MAITER_ENGINE_SYNC, "unknown engine %d", p->engine);
-  MAITER_REQUIRE((p->flags & ~MAITER_FLAG_PROFILE_KERNELS) == 0 && p->reserved0 == 0,
+  MAITER_REQUIRE(p->engine == MAITER_ENGINE_SYNC || p->engine == MAITER_ENGINE_ASYNC,
+                 "unknown engine %d", p->engine);
+  MAITER_REQUIRE(p->timeout_ms >= 0, "timeout_ms must be >= 0");
+  if (p->engine == MAITER_ENGINE_ASYNC && p->sched == MAITER_SCHED_TOPFRAC) {
+    set_error("the asynchronous engine schedules by threshold; use the sync engine for TOPFRAC");
+    return MAITER_ERR_UNSUPPORTED;
+  }
+  MAITER_REQUIRE((p->flags & ~(MAITER_FLAG_PROFILE_KERNELS | MAITER_FLAG_INJECT_STALL)) == 0 &&
+                     p->reserved0 == 0,
                  "unknown flags 0x%x", p->flags);
   if (is_sum) {
     MAITER_REQUIRE(p->g == MAITER_G_SCALE_BY_SRC, "sum ops take g = MAITER_G_SCALE_BY_SRC");
@@ -591,7 +599,7 @@ maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p, mait
   switch (p->op) {
     default: s = run_op(g, p, r, st); break;
   }
-  if (s == MAITER_OK || s == MAITER_ERR_NOT_CONVERGED) {
+  if (s == MAITER_OK || s == MAITER_ERR_NOT_CONVERGED || s == MAITER_ERR_TIMEOUT) {
     *out = r;
   } else if (fresh) {
     maiter_result_destroy(r);
