@@ -60,6 +60,32 @@ struct DevCtl {
   unsigned int pad;
 };
 
+// Top-fraction selection state (see topq_kernels.cuh).
+constexpr int kHistBins = 2048;
+struct TopqCtl {
+  unsigned int hist[3][kHistBins];  // one histogram per radix pass (zeroed after use)
+  unsigned int ticket[3];
+  unsigned int prefix;              // key bits fixed by the passes so far
+  unsigned int kth;                 // rank still to find within the prefix bucket
+  unsigned int key_thr;             // result: the k-th largest key (0xFFFFFFFF: none)
+  unsigned long long pend;          // pending vertices with a non-zero key
+  double frac;                      // q
+};
+
+// Priority key (Section 3.5, |v (+) Delta - v|) rounded to FP32: |Delta_j| for
+// +; v_j - Delta_j for min, with v_j = infinity mapped to +inf.  Positive
+// floats order like their bit patterns; 0 means "not pending".
+template <class Op>
+__device__ __forceinline__ unsigned priority_key(typename Op::D d, typename Op::V v) {
+  if constexpr (Op::kIsSum) {
+    return __float_as_uint(fabsf(static_cast<float>(d)));
+  } else {
+    if (!(d < v)) return 0u;
+    if (v == kInfU32) return 0x7F800000u;
+    return __float_as_uint(static_cast<float>(v - d));
+  }
+}
+
 template <class Op>
 struct KArgs {
   int n;
@@ -74,6 +100,7 @@ struct KArgs {
   typename Op::D* large_d;       // large: the delta taken by the scan, per entry
   unsigned int large_cap;        // capacity of large / large_d
   DevCtl* ctl;
+  const TopqCtl* topq;           // non-null: select key >= topq->key_thr (TOPFRAC)
   int cut_warp;                  // deg <  cut_warp : small bucket
   int cut_cta;                   // deg >= cut_cta  : large bucket (chunked)
 };
@@ -107,6 +134,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
   DevCtl* ctl = a.ctl;
   const unsigned ws = ctl->wset;
   const double tau = ctl->tau;
+  const unsigned key_thr = a.topq ? a.topq->key_thr : 0u;
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   constexpr int kWarps = BLOCK / 32;
@@ -143,6 +171,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
         } else {
           sel = pend;
         }
+        if (a.topq) sel = pend && priority_key<Op>(d, vv) >= key_thr;
         if (sel) {
           const int deg = __ldg(a.rp + j + 1) - __ldg(a.rp + j);
           const int b = deg < a.cut_warp ? 0 : (deg < a.cut_cta ? 1 : 2);

@@ -9,6 +9,7 @@
 #include "../../include/maiter.h"
 #include "daic_kernels.cuh"
 #include "async_kernels.cuh"
+#include "topq_kernels.cuh"
 
 namespace maiter {
 
@@ -81,6 +82,7 @@ struct maiter_result {
   void* large_d = nullptr;             // their taken deltas (8 bytes per entry)
   unsigned large_cap = 0;              // n + m / kChunk + 1 entries
   maiter::DevCtl* ctl = nullptr;
+  maiter::TopqCtl* topq = nullptr;     // top-fraction selection (allocated on first use)
   maiter::DevCtl* h_ctl = nullptr;   // pinned mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // cached executable graph of the round loop

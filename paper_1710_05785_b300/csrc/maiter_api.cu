@@ -184,6 +184,7 @@ void maiter_result_destroy(maiter_result* r) {
   cudaFree(r->large);
   cudaFree(r->large_d);
   cudaFree(r->ctl);
+  cudaFree(r->topq);
   free_async(r);
   if (r->h_ctl) cudaFreeHost(r->h_ctl);
   if (r->ev0) cudaEventDestroy(r->ev0);
@@ -245,10 +246,10 @@ constexpr int kBlock = 256;
 template <class Op>
 struct Phase {
   KArgs<Op> a{};
-  int push_grid = 1, scan_grid = 1;
+  int push_grid = 1, scan_grid = 1, hist_grid = 1;
 
   void setup(const maiter_graph* g, maiter_result* r, void* delta, const void* coef,
-             double damping, const Tuning& tu) {
+             double damping, const Tuning& tu, bool topq) {
     a.n = static_cast<int>(g->n);
     a.rp = g->rp;
     a.edges.col = g->col;
@@ -262,6 +263,8 @@ struct Phase {
     a.large_d = static_cast<typename Op::D*>(r->large_d);
     a.large_cap = r->large_cap;
     a.ctl = r->ctl;
+    a.topq = topq ? r->topq : nullptr;
+    hist_grid = g->num_sms * 4;
     a.cut_warp = tu.cut_warp;
     a.cut_cta = tu.cut_cta;
     push_grid = grid_for(reinterpret_cast<const void*>(&k_push<Op, kBlock>), kBlock, g->num_sms,
@@ -272,8 +275,18 @@ struct Phase {
     if (need < scan_grid) scan_grid = need > 0 ? need : 1;
   }
 
+  // TOPFRAC: the three radix-select passes that fix the round's key threshold.
+  void launch_select(cudaStream_t s) const {
+    if (!a.topq) return;
+    TopqCtl* tq = const_cast<TopqCtl*>(a.topq);
+    k_topq_hist<Op, kBlock, 0><<<hist_grid, kBlock, 0, s>>>(a, tq);
+    k_topq_hist<Op, kBlock, 1><<<hist_grid, kBlock, 0, s>>>(a, tq);
+    k_topq_hist<Op, kBlock, 2><<<hist_grid, kBlock, 0, s>>>(a, tq);
+  }
+
   void launch_round(cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) const {
     k_push<Op, kBlock><<<push_grid, kBlock, 0, s>>>(a);
+    launch_select(s);
     k_scan<Op, kBlock><<<scan_grid, kBlock, 0, s>>>(a, h, use_cond);
   }
 
@@ -308,6 +321,7 @@ struct Phase {
       MAITER_CUDA(cudaEventRecord(e[0], st));
       k_push<Op, kBlock><<<push_grid, kBlock, 0, st>>>(a);
       MAITER_CUDA(cudaEventRecord(e[1], st));
+      launch_select(st);
       k_scan<Op, kBlock><<<scan_grid, kBlock, 0, st>>>(a, cudaGraphConditionalHandle{}, 0);
       MAITER_CUDA(cudaEventRecord(e[2], st));
       MAITER_CUDA(cudaGetLastError());
@@ -340,14 +354,19 @@ struct RunPlan {
 static maiter_status setup_plan(const maiter_graph* g, const maiter_run_params* p,
                                 maiter_result* r, const Tuning& tu, RunPlan* plan) {
   const void* coef = p->coef ? r->coef : nullptr;
+  const bool topq = p->sched == MAITER_SCHED_TOPFRAC;
+  if (topq && !r->topq) {
+    MAITER_CUDA(cudaMalloc(&r->topq, sizeof(TopqCtl)));
+    MAITER_CUDA(cudaMemset(r->topq, 0, sizeof(TopqCtl)));
+  }
   switch (p->op) {
-    case MAITER_OP_SUM_F64: plan->f64.setup(g, r, r->delta, coef, p->damping, tu); break;
+    case MAITER_OP_SUM_F64: plan->f64.setup(g, r, r->delta, coef, p->damping, tu, topq); break;
     case MAITER_OP_SUM_MIXED:
       plan->mixed = true;
-      plan->warm.setup(g, r, r->delta_wide, coef, p->damping, tu);
-      plan->f32.setup(g, r, r->delta, coef, p->damping, tu);
+      plan->warm.setup(g, r, r->delta_wide, coef, p->damping, tu, topq);
+      plan->f32.setup(g, r, r->delta, coef, p->damping, tu, topq);
       break;
-    default: plan->umin.setup(g, r, r->delta, nullptr, 0.0, tu); break;
+    default: plan->umin.setup(g, r, r->delta, nullptr, 0.0, tu, topq); break;
   }
   return MAITER_OK;
 }
@@ -399,7 +418,10 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
                               maiter_result* r, cudaStream_t st) {
   const Tuning tu{};
   RunPlan plan;
-  setup_plan(g, p, r, tu, &plan);
+  {
+    maiter_status ps = setup_plan(g, p, r, tu, &plan);
+    if (ps != MAITER_OK) return ps;
+  }
   // The executable graph bakes in the kernel arguments; rebuild it only when
   // one of them changes.
   uint64_t key = 1469598103934665603ull;
@@ -411,6 +433,7 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   mix(dbits);
   mix(static_cast<uint64_t>(tu.cut_warp));
   mix(static_cast<uint64_t>(tu.cut_cta));
+  mix(p->sched == MAITER_SCHED_TOPFRAC ? 1 : 0);
   const bool profile = (p->flags & MAITER_FLAG_PROFILE_KERNELS) != 0;
   if (!profile && (!r->exec || r->exec_key != key)) {
     maiter_status s = build_graph(g, r, p->op, plan);
@@ -425,6 +448,12 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   c.max_rounds = p->max_rounds > 0 ? p->max_rounds : 1000000;
   c.sched = p->sched;
   *r->h_ctl = c;
+  if (r->topq && p->sched == MAITER_SCHED_TOPFRAC) {
+    // histograms and tickets start at zero; q for this run
+    MAITER_CUDA(cudaMemsetAsync(r->topq, 0, sizeof(TopqCtl), st));
+    MAITER_CUDA(cudaMemcpyAsync(&r->topq->frac, &p->top_frac, sizeof(double),
+                                cudaMemcpyHostToDevice, st));
+  }
   MAITER_CUDA(cudaMemcpyAsync(r->ctl, r->h_ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, st));
   maiter_stats& s = r->stats;
   s = maiter_stats{};
@@ -473,7 +502,9 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   s.converged = h.status == 1;
   // every phase that ran ends with one scan that did not continue
   const int64_t phases = 1 + (h.phase > 0 ? 1 : 0);
-  s.kernel_launches += 2 * (static_cast<int64_t>(h.rounds) + phases) + (plan.mixed ? 1 : 0);
+  const int per_round = (p->sched == MAITER_SCHED_TOPFRAC) ? 5 : 2;   // + 3 radix passes
+  s.kernel_launches +=
+      per_round * (static_cast<int64_t>(h.rounds) + phases) + (plan.mixed ? 1 : 0);
   s.status = h.status == 1 ? MAITER_OK : MAITER_ERR_NOT_CONVERGED;
   if (h.status != 1) {
     set_error("round cap of %lld reached before the termination test held (residual %g)",
@@ -579,10 +610,8 @@ maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p, mait
     MAITER_REQUIRE(p->delta0 || (p->source >= 0 && p->source < g->n),
                    "min without delta0 needs a source in [0, n)");
   }
-  if (p->sched == MAITER_SCHED_TOPFRAC) {
-    set_error("MAITER_SCHED_TOPFRAC is not available in this build");
-    return MAITER_ERR_UNSUPPORTED;
-  }
+  MAITER_REQUIRE(p->sched != MAITER_SCHED_TOPFRAC || (p->top_frac > 0.0 && p->top_frac <= 1.0),
+                 "top_frac must lie in (0, 1]");
   DeviceGuard guard(g->device);
   maiter_result* r = *out;
   bool fresh = false;
