@@ -155,6 +155,117 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+PR_WORKLOADS = {
+    # configuration 1: FP64 PageRank to sum |Delta| < 1e-8
+    "pagerank-rmat13": dict(scale=13, ef=8, op="f64", eps=1e-8),
+    # configuration 3: FP32 deltas / FP64 state and residual, scale 24; eps = 4e-8
+    # bounds the per-entry relative error by 25 * eps = 1e-6 (v* >= 1 - d)
+    "pagerank-mixed-rmat24": dict(scale=24, ef=16, op="mixed", eps=4e-8),
+}
+# algorithmic bytes of the PageRank push kernel (RMW = read + write):
+#   FP64:  4 B target + 16 B Delta_k RMW = 20 B per edge;
+#          8 B offsets + 16 B Delta_j exchange + 16 B v_j RMW = 40 B per vertex
+#   FP32 deltas: 4 + 8 = 12 B per edge; 8 + 8 + 16 = 32 B per vertex
+PR_BYTES = {"f64": (20, 40), "f32": (12, 32)}
+D_PR = 0.8
+
+
+def run_pagerank(args, wl):
+    """PageRank workloads: one step = one run from v0 = 0, Delta1 = 1 - d to the
+    tolerance; value = m / time-to-tolerance (GTEPS per solution)."""
+    import torch
+    import paper_1710_05785_b300 as mt
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    cfg = PR_WORKLOADS[wl]
+    g = graphgen.rmat(cfg["scale"], cfg["ef"])
+    G = mt.Graph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev), device=local)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    eps = cfg["eps"]
+    variants = {
+        "plain_f64_sync": dict(op=mt.OP_SUM_F64),
+        "mixed_sync": dict(op=mt.OP_SUM_MIXED),
+        "f64_async": dict(op=mt.OP_SUM_F64, engine=mt.ENGINE_ASYNC),
+        "f64_topq10_sync": dict(op=mt.OP_SUM_F64, sched=mt.SCHED_TOPFRAC, top_frac=0.1),
+    }
+    head = "plain_f64_sync" if cfg["op"] == "f64" else "mixed_sync"
+    results = {}
+    res = {}
+
+    def one(name, kw):
+        flush.fill_(1)
+        r = mt.run(G, eps=eps, damping=D_PR, stream=stream, result=res.get(name), **kw)
+        res[name] = r
+        return r.stats()
+
+    for name, kw in variants.items():
+        reps = args.steps if name == head else max(1, min(args.steps, 2))
+        for _ in range(max(args.warmup, 1) if name == head else 1):
+            one(name, kw)
+        torch.cuda.synchronize()
+        st = [one(name, kw) for _ in range(reps)]
+        t = min(s["elapsed_ms"] for s in st) if name != head else float(np.mean([s["elapsed_ms"] for s in st]))
+        results[name] = dict(time_to_tolerance_ms=t, rounds=st[-1]["rounds"],
+                             edge_pushes=st[-1]["edge_pushes"], residual=st[-1]["residual"],
+                             kernel_launches=st[-1]["kernel_launches"], stats=st[-1])
+    plain_t = results["plain_f64_sync"]["time_to_tolerance_ms"]
+    hs = results[head]
+    ms = hs["time_to_tolerance_ms"]
+    prof = mt.run(G, eps=eps, damping=D_PR, stream=stream, flags=mt.FLAG_PROFILE_KERNELS,
+                  **variants[head]).stats()
+    if cfg["op"] == "f64":
+        alg = PR_BYTES["f64"][0] * prof["edge_pushes"] + PR_BYTES["f64"][1] * prof["activations"]
+    else:
+        w_e, w_v = prof["warm_edge_pushes"], prof["warm_activations"]
+        alg = (PR_BYTES["f64"][0] * w_e + PR_BYTES["f64"][1] * w_v
+               + PR_BYTES["f32"][0] * (prof["edge_pushes"] - w_e)
+               + PR_BYTES["f32"][1] * (prof["activations"] - w_v))
+    peaks, peak_kind = measured_peaks()
+    achieved = alg / (prof["push_ms"] * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": g.m / (ms * 1e-3) / 1e9, "unit": "GTEPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if cfg["op"] == "f64" else "f32/f64", "data": "synthetic",
+        "config": {"workload": f"{wl}: PageRank d=0.8, R-MAT scale {cfg['scale']} ef {cfg['ef']}",
+                   "n": g.n, "m": g.m, "eps": eps, "headline": head,
+                   "l2": f"{L2_FLUSH_BYTES >> 20} MiB write before every run"},
+        "time_to_tolerance_ms": ms,
+        "vs_plain_form": plain_t / ms,
+        "variants": {k: {kk: vv for kk, vv in v.items() if kk != "stats"} for k, v in results.items()},
+        "gteps_work": hs["edge_pushes"] / (ms * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "kernel": "k_push<OpSum>", "achieved": achieved,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                     "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "push_launches": prof["push_launches"],
+                     "push_ms_per_launch": prof["push_ms"] / max(prof["push_launches"], 1),
+                     "scan_ms_per_launch": prof["scan_ms"] / max(prof["scan_launches"], 1),
+                     "alg_bytes_per_launch": alg / max(prof["push_launches"], 1)},
+        "gpu_launches": int(sum(v["kernel_launches"] for v in results.values())),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        coef = oracle.pagerank_coef(g, D_PR)
+        c = oracle.pagerank_c(g.n, D_PR)
+        t0 = time.perf_counter()
+        it = 0
+        while time.perf_counter() - t0 < 15.0 and it < 200:
+            oracle.linear_power(g, coef, c, tol=0.0, max_iter=1)
+            it += 1
+        per_iter = (time.perf_counter() - t0) / it
+        rounds = results["plain_f64_sync"]["rounds"]
+        line["cpu_baseline"] = {
+            "value": g.m / (per_iter * rounds) / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{it} synchronous iterations of the oracle over the full graph "
+                      f"({per_iter * 1e3:.0f} ms each), projected to the {rounds} rounds the "
+                      f"plain GPU form needed"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -163,9 +274,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--workload", default="sssp-rmat20",
+                    choices=["sssp-rmat20"] + sorted(PR_WORKLOADS),
+                    help="sssp-rmat20 (default; configuration 2) or a PageRank configuration")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload in PR_WORKLOADS:
+        run_pagerank(args, args.workload)
         return
 
     import torch
@@ -249,6 +366,31 @@ def main():
     except (OSError, ValueError):
         pass
 
+    # the other schedules and the asynchronous engine on the same 8 sources
+    # (one warm pass, then the best of two timed passes)
+    variant_kw = {
+        "async": dict(engine=mt.ENGINE_ASYNC),
+        "topq05_sync": dict(sched=mt.SCHED_TOPFRAC, top_frac=0.05),
+    }
+    variants = {"plain_sync": {"ms_per_8_sources": ms_per_step,
+                               "edge_pushes": int(sum(s["edge_pushes"] for s in stats) / args.steps)}}
+    for name, kw in variant_kw.items():
+        rv = None
+        best, pushes = None, 0
+        for rep in range(3):
+            t0 = time.perf_counter()
+            tot, pushes = 0.0, 0
+            for s in sources:
+                rv = mt.run(G, mt.OP_MIN_U32, source=s, result=rv, stream=stream.cuda_stream, **kw)
+                st = rv.stats()
+                tot += st["elapsed_ms"]
+                pushes += st["edge_pushes"]
+            if rep > 0:
+                best = tot if best is None else min(best, tot)
+        rv.close()
+        variants[name] = {"ms_per_8_sources": best, "edge_pushes": int(pushes),
+                          "vs_plain": ms_per_step / best}
+
     # end to end through the C ABI from pinned host buffers, per step:
     # upload the CSR, run the 8 sources, read every distance vector back
     rp_h = torch.from_numpy(g.row_ptr).pin_memory()
@@ -297,6 +439,7 @@ def main():
                      "alg_bytes_per_launch": alg_bytes / max(push_launches, 1)},
         "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
+        "variants": variants,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "wall_s_timed": t_wall,

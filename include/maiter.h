@@ -166,6 +166,11 @@ typedef struct maiter_stats {
   double scan_ms;        /* summed device time of the frontier/termination kernel */
   int64_t push_launches;
   int64_t scan_launches;
+  /* SUM_MIXED: the part of rounds / activations / edge_pushes spent in the
+     FP64-delta warm-up phase (0 for other ops) */
+  int64_t warm_rounds;
+  int64_t warm_activations;
+  int64_t warm_edge_pushes;
 } maiter_stats;
 
 /* Fills *p with defaults: PageRank-style sum in FP64, d = 0.8, sched ALL,

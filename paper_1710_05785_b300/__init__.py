@@ -68,6 +68,8 @@ class Stats(ctypes.Structure):
         ("converged", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
         ("push_ms", ctypes.c_double), ("scan_ms", ctypes.c_double),
         ("push_launches", ctypes.c_int64), ("scan_launches", ctypes.c_int64),
+        ("warm_rounds", ctypes.c_int64), ("warm_activations", ctypes.c_int64),
+        ("warm_edge_pushes", ctypes.c_int64),
     ]
 
     def as_dict(self):

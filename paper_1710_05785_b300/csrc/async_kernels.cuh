@@ -29,11 +29,13 @@
 
 namespace maiter {
 
+// The three hot counters sit on cache lines of their own: idle warps poll
+// them and every claim and enqueue hits them.
 struct AsyncCtl {
-  unsigned long long head;       // next queue index to claim
-  unsigned long long tail;       // next queue index to reserve
-  long long pending;             // reserved + in-flight vertices
-  unsigned int ticket;           // last-block election in k_async_seed
+  alignas(128) unsigned long long head;   // next queue index to claim
+  alignas(128) unsigned long long tail;   // next queue index to reserve
+  alignas(128) long long pending;         // reserved + in-flight vertices
+  alignas(128) unsigned int ticket;       // last-block election in k_async_seed
   int status;                    // 0 running, 1 converged, 2 epoch cap, 4 timeout, 5 queue full
   double resid_acc;
   unsigned long long pend_acc;
@@ -103,8 +105,10 @@ __device__ __forceinline__ void enqueue_warp(const AArgs<Op>& a, bool want, int 
   }
 }
 
-// Claims up to 32 queued indices for the calling warp: returns the first index
-// and the count (0 when nothing is claimable right now).
+// Claims up to kClaim queued indices for the calling warp (processed 32 at a
+// time): returns the first index and the count (0 when nothing is claimable
+// right now).  Large claims keep the rate of compare-and-swap on head low.
+constexpr int kClaim = 128;
 __device__ __forceinline__ int claim_warp(AsyncCtl* ctl, unsigned long long* first, int lane) {
   int got = 0;
   unsigned long long h = 0;
@@ -114,11 +118,13 @@ __device__ __forceinline__ int claim_warp(AsyncCtl* ctl, unsigned long long* fir
       h = vc->head;
       const unsigned long long t = vc->tail;
       if (h >= t) break;
-      const unsigned long long take = (t - h) < 32ull ? (t - h) : 32ull;
+      const unsigned long long take =
+          (t - h) < static_cast<unsigned long long>(kClaim) ? (t - h) : kClaim;
       if (atomicCAS(&ctl->head, h, h + take) == h) {
         got = static_cast<int>(take);
         break;
       }
+      __nanosleep(32 + (tries & 7) * 16);
     }
   }
   got = __shfl_sync(0xffffffffu, got, 0);
@@ -139,6 +145,7 @@ __global__ void __launch_bounds__(BLOCK) k_async(AArgs<Op> a) {
   // idle-wait bookkeeping (lane 0): the wait restarts whenever work moves
   unsigned long long idle_since = 0, seen_head = ~0ull;
   long long seen_pending = -1;
+  unsigned backoff = 128;          // idle poll interval (ns), doubled up to 8 us
 
   for (;;) {
     if (vc->status >= 4) break;
@@ -163,17 +170,24 @@ __global__ void __launch_bounds__(BLOCK) k_async(AArgs<Op> a) {
             atomicMax(&ctl->status, 4);
             quit = 1;
           }
-          if (!quit) __nanosleep(256);
+          if (!quit) {
+            __nanosleep(backoff);
+            backoff = backoff < 8192u ? backoff * 2u : 8192u;
+          }
         }
       }
       if (__shfl_sync(0xffffffffu, quit, 0)) break;
       continue;
     }
     seen_pending = -1;
+    backoff = 128;
+    for (int sub = 0; sub < got; sub += 32) {
+    const int cnt = got - sub < 32 ? got - sub : 32;
+    const unsigned long long fsub = first + static_cast<unsigned long long>(sub);
     // Read the claimed ids (a slot may still be in the middle of being written).
     int j = -1;
-    if (lane < got) {
-      volatile int* slot = a.queue + ((first + lane) % a.cap);
+    if (lane < cnt) {
+      volatile int* slot = a.queue + ((fsub + lane) % a.cap);
       int x = *slot;
       if (x == -1) {
         const unsigned long long t0 = global_ns();
@@ -258,6 +272,7 @@ __global__ void __launch_bounds__(BLOCK) k_async(AArgs<Op> a) {
       }
       enqueue_warp(a, want, k, lane);
     }
+    }  // sub-batches
     // The batch is done: its pushes (and the enqueues they caused) are visible.
     __threadfence();
     if (lane == 0) {

@@ -58,6 +58,9 @@ struct DevCtl {
   int phase;                     // 1 once the FP32 phase of a mixed run has started
   unsigned int overflow;         // a list reservation would have run past its capacity
   unsigned int pad;
+  unsigned long long warm_rounds;      // mixed precision: counters at the FP32 switch
+  unsigned long long warm_activations;
+  unsigned long long warm_pushes;
 };
 
 // Top-fraction selection state (see topq_kernels.cuh).
@@ -444,6 +447,9 @@ static __global__ void k_to_f32(const double* __restrict__ d64, float* __restric
     const int st = ctl->status;
     ctl->status = (st == 1) ? 0 : st;
     ctl->phase = (st == 1) ? 1 : 0;
+    ctl->warm_rounds = ctl->rounds;
+    ctl->warm_activations = ctl->activations;
+    ctl->warm_pushes = ctl->pushes;
     ctl->eps_eff = ctl->eps;
     ctl->switch_frac = 0.0;
     for (int s = 0; s < 2; ++s)

@@ -497,6 +497,13 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   s.rounds = static_cast<int64_t>(h.rounds);
   s.activations = static_cast<int64_t>(h.activations);
   s.edge_pushes = static_cast<int64_t>(h.pushes);
+  if (plan.mixed) {
+    // the warm-up phase is the whole run if it never switched to FP32
+    const bool switched = h.phase > 0;
+    s.warm_rounds = static_cast<int64_t>(switched ? h.warm_rounds : h.rounds);
+    s.warm_activations = static_cast<int64_t>(switched ? h.warm_activations : h.activations);
+    s.warm_edge_pushes = static_cast<int64_t>(switched ? h.warm_pushes : h.pushes);
+  }
   s.residual = h.residual;
   s.elapsed_ms = ms;
   s.converged = h.status == 1;
