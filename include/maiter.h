@@ -245,6 +245,64 @@ maiter_status maiter_sssp_noalloc(int64_t n, int64_t m, const int32_t* row_ptr,
                                   uint32_t* v_out, uint32_t* delta_out, int64_t max_rounds,
                                   int device, void* stream, int64_t* rounds_out);
 
+/* ------------------------------------------------------------------ batch
+ * Many queries - personalised PageRank (+, g = d x / outdeg) and SSSP (min,
+ * g = x + w) - over several graphs of uneven size, advanced together round by
+ * round in ONE CUDA-graph launch (a WHILE node; no host round trip between
+ * rounds).  Each query has its own v and Delta (query-major layout); a round
+ * updates every (query, vertex) item of a sparse frontier and appends the
+ * receivers whose delta crosses the query's threshold eps_q / n (sum) or whose
+ * distance improves (min).  A sum query ends when its frontier is empty, which
+ * proves sum |Delta| <= eps_q (every vertex is at or below eps_q / n); a min
+ * query ends when no distance can improve (exact).  Personalised PageRank is
+ * PageRank (Section 4.2) with Delta1 = (1 - d) / |S| on the seed set S and 0
+ * elsewhere (the Rooted PageRank row of Table 1 with damping). */
+typedef struct maiter_batch maiter_batch;   /* opaque: query-major state + frontiers */
+
+typedef struct maiter_query {
+  int32_t graph;        /* index into the graphs array */
+  int32_t op;           /* MAITER_OP_SUM_F64 (PPR) or MAITER_OP_MIN_U32 (SSSP) */
+  const int32_t* seeds; /* host array of num_seeds distinct vertex ids */
+  int32_t num_seeds;
+  int32_t reserved;     /* must be 0 */
+  double damping;       /* PPR: d in [0, 1) */
+  double eps;           /* PPR: bound on sum_j |Delta_j| at termination (> 0) */
+} maiter_query;
+
+typedef struct maiter_batch_params {
+  int64_t max_rounds;      /* <= 0 means 1,000,000 */
+  void* stream;            /* cudaStream_t; NULL = default stream */
+  int32_t cut_large;       /* out-degree from which an item is split into chunks
+                              processed by separate CTAs (0 = 1024) */
+  int32_t chunk;           /* edges per chunk (0 = 1024, else >= 32) */
+  int32_t push_blocks_per_sm;  /* cap on resident push CTAs per SM (0 = occupancy) */
+  int32_t flags;           /* MAITER_FLAG_PROFILE_KERNELS or 0 */
+} maiter_batch_params;
+
+void maiter_batch_params_default(maiter_batch_params* p);
+
+/* Runs every query to termination.  All graphs must live on one device.  If
+ * *out is non-NULL and was returned for the same graphs, query graphs/ops and
+ * tuning, it is reused without allocation; otherwise it is (re)built.
+ * Errors: INVALID_ARG, OOM (also when a frontier outgrows its bounded
+ * capacity), CUDA, NOT_CONVERGED (state readable). */
+maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_graphs,
+                               const maiter_query* queries, int32_t num_queries,
+                               const maiter_batch_params* p, maiter_batch** out);
+
+/* Copies query `query`'s states (double for PPR, uint32 for SSSP; count = n
+ * of its graph) into `out` (host or device). */
+maiter_status maiter_batch_get_state(const maiter_batch* b, int32_t query, void* out,
+                                     int64_t count);
+
+/* Aggregate statistics of the last run (rounds, updates, pushes, time). */
+maiter_status maiter_batch_get_stats(const maiter_batch* b, maiter_stats* out);
+
+/* Per query: the last round in which it still had frontier items. */
+maiter_status maiter_batch_query_rounds(const maiter_batch* b, int32_t* out, int32_t count);
+
+void maiter_batch_destroy(maiter_batch* b);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* maiter_last_error(void);
 

@@ -109,6 +109,18 @@ def lib():
         L.maiter_params_default.argtypes = [ctypes.POINTER(RunParams)]
         L.maiter_last_error.restype = ctypes.c_char_p
         L.maiter_version.restype = ctypes.c_char_p
+        L.maiter_batch_params_default.argtypes = [ctypes.POINTER(BatchParams)]
+        L.maiter_run_batch.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32,
+                                       ctypes.POINTER(QuerySpec), i32,
+                                       ctypes.POINTER(BatchParams), ctypes.POINTER(ctypes.c_void_p)]
+        L.maiter_run_batch.restype = i32
+        L.maiter_batch_get_state.argtypes = [P, i32, P, i64]
+        L.maiter_batch_get_state.restype = i32
+        L.maiter_batch_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+        L.maiter_batch_get_stats.restype = i32
+        L.maiter_batch_query_rounds.argtypes = [P, P, i32]
+        L.maiter_batch_query_rounds.restype = i32
+        L.maiter_batch_destroy.argtypes = [P]
         _lib = L
     return _lib
 
@@ -276,6 +288,87 @@ def run(graph: Graph, op: int = OP_SUM_F64, *, coef=None, damping: float = 0.8, 
         result = Result(h, graph, op)
     _check(st, allow)
     return result
+
+
+class QuerySpec(ctypes.Structure):
+    """Mirror of ``maiter_query``."""
+    _fields_ = [("graph", ctypes.c_int32), ("op", ctypes.c_int32), ("seeds", ctypes.c_void_p),
+                ("num_seeds", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("damping", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class BatchParams(ctypes.Structure):
+    """Mirror of ``maiter_batch_params``."""
+    _fields_ = [("max_rounds", ctypes.c_int64), ("stream", ctypes.c_void_p),
+                ("cut_large", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("push_blocks_per_sm", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class Batch:
+    """``maiter_batch``: the query-major states of a batched run."""
+
+    def __init__(self, handle, graphs, queries):
+        self.handle = handle
+        self.graphs = graphs
+        self.queries = queries
+
+    def state(self, q: int, out=None):
+        op, g = self.queries[q][0], self.graphs[self.queries[q][1]]
+        if out is None:
+            out = np.empty(g.n, dtype=np.uint32 if op == OP_MIN_U32 else np.float64)
+        _check(lib().maiter_batch_get_state(self.handle, q, _addr(out), g.n))
+        return out
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().maiter_batch_get_stats(self.handle, ctypes.byref(s)))
+        return s.as_dict()
+
+    def query_rounds(self) -> np.ndarray:
+        out = np.empty(len(self.queries), dtype=np.int32)
+        _check(lib().maiter_batch_query_rounds(self.handle, _addr(out), len(self.queries)))
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().maiter_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def run_batch(graphs, queries, *, max_rounds: int = 1000000, stream=None, cut_large: int = 0,
+              chunk: int = 0, push_blocks_per_sm: int = 0, flags: int = 0,
+              batch: Batch | None = None) -> Batch:
+    """``maiter_run_batch``.  ``queries`` is a list of dicts with keys op
+    (OP_SUM_F64 or OP_MIN_U32), graph (index), seeds (ids), and for PageRank
+    damping and eps."""
+    G = (ctypes.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+    Q = (QuerySpec * len(queries))()
+    keep = []
+    for i, q in enumerate(queries):
+        seeds = np.ascontiguousarray(q["seeds"], dtype=np.int32)
+        keep.append(seeds)
+        Q[i].graph, Q[i].op = int(q["graph"]), int(q["op"])
+        Q[i].seeds, Q[i].num_seeds = seeds.ctypes.data, int(seeds.shape[0])
+        Q[i].damping = float(q.get("damping", 0.8))
+        Q[i].eps = float(q.get("eps", 1e-6))
+    p = BatchParams()
+    lib().maiter_batch_params_default(ctypes.byref(p))
+    p.max_rounds, p.stream = max_rounds, stream
+    p.cut_large, p.chunk, p.push_blocks_per_sm, p.flags = cut_large, chunk, push_blocks_per_sm, flags
+    h = ctypes.c_void_p(batch.handle.value if batch is not None else None)
+    st = lib().maiter_run_batch(G, len(graphs), Q, len(queries), ctypes.byref(p), ctypes.byref(h))
+    if batch is None and h.value:
+        batch = Batch(h, list(graphs), [(int(q["op"]), int(q["graph"])) for q in queries])
+    elif batch is not None:
+        batch.queries = [(int(q["op"]), int(q["graph"])) for q in queries]
+    _check(st)
+    return batch
 
 
 def version() -> str:

@@ -1,0 +1,469 @@
+// Host side of the batched engine: query tables, query-major state, sparse
+// frontiers, and the CUDA graph WHILE(cond) { k_b_take ; k_b_push } that
+// advances every query of the batch in one launch.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "batch_kernels.cuh"
+
+struct maiter_batch {
+  int device = 0;
+  int nq = 0, ng = 0;
+  std::vector<const maiter_graph*> graphs;
+  std::vector<maiter::BQuery> hq;
+  std::vector<int64_t> qn;                  // vertices of each query's graph
+  std::vector<maiter::BItem> hseeds;
+  int cut_large = 0, chunk = 0;
+  maiter::BGraph* d_graphs = nullptr;
+  maiter::BQuery* d_queries = nullptr;
+  maiter::BItem* d_seeds = nullptr;
+  double* v_sum = nullptr;
+  double* d_sum = nullptr;
+  uint32_t* v_min = nullptr;
+  uint32_t* d_min = nullptr;
+  unsigned* stamp = nullptr;
+  maiter::BItem* items[2][maiter::kBOps][2] = {};
+  unsigned cap[maiter::kBOps][2] = {};
+  maiter::BChunk* chunks = nullptr;
+  unsigned chunk_cap = 0;
+  unsigned* qlast = nullptr;
+  maiter::BCtl* ctl = nullptr;
+  maiter::BCtl* h_ctl = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int exec_grid = 0;
+  int64_t n_sum = 0, n_min = 0;
+  maiter_stats stats{};
+};
+
+namespace maiter {
+
+constexpr int kBBlock = 256;
+
+// Number of vertices of out-degree >= cut (sizes the large-item lists).
+__global__ void k_count_large(const int* __restrict__ rp, int n, int cut, unsigned* out) {
+  unsigned c = 0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    c += (rp[j + 1] - rp[j]) >= cut;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+static void free_batch_buffers(maiter_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  cudaFree(b->d_graphs);
+  cudaFree(b->d_queries);
+  cudaFree(b->d_seeds);
+  cudaFree(b->v_sum);
+  cudaFree(b->d_sum);
+  cudaFree(b->v_min);
+  cudaFree(b->d_min);
+  cudaFree(b->stamp);
+  for (auto& s : b->items)
+    for (auto& o : s)
+      for (auto& l : o) { cudaFree(l); l = nullptr; }
+  cudaFree(b->chunks);
+  cudaFree(b->qlast);
+  cudaFree(b->ctl);
+  if (b->h_ctl) cudaFreeHost(b->h_ctl);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  b->d_graphs = nullptr; b->d_queries = nullptr; b->d_seeds = nullptr;
+  b->v_sum = b->d_sum = nullptr; b->v_min = b->d_min = nullptr; b->stamp = nullptr;
+  b->chunks = nullptr; b->qlast = nullptr; b->ctl = nullptr; b->h_ctl = nullptr;
+  b->ev0 = b->ev1 = nullptr;
+}
+
+static BArgs batch_args(const maiter_batch* b) {
+  BArgs a{};
+  a.graphs = b->d_graphs;
+  a.queries = b->d_queries;
+  a.v_sum = b->v_sum;
+  a.d_sum = b->d_sum;
+  a.v_min = b->v_min;
+  a.d_min = b->d_min;
+  a.stamp = b->stamp;
+  for (int s = 0; s < 2; ++s)
+    for (int o = 0; o < kBOps; ++o)
+      for (int l = 0; l < 2; ++l) a.items[s][o][l] = b->items[s][o][l];
+  for (int o = 0; o < kBOps; ++o)
+    for (int l = 0; l < 2; ++l) a.cap[o][l] = b->cap[o][l];
+  a.chunks = b->chunks;
+  a.chunk_cap = b->chunk_cap;
+  a.qlast = b->qlast;
+  a.ctl = b->ctl;
+  a.cut_large = b->cut_large;
+  a.chunk = b->chunk;
+  return a;
+}
+
+// Validates the queries and builds the host tables; allocates device memory.
+static maiter_status batch_setup(maiter_batch* b, const maiter_graph* const* graphs, int ng,
+                                 const maiter_query* qs, int nq, const maiter_batch_params* p) {
+  b->device = graphs[0]->device;
+  b->ng = ng;
+  b->nq = nq;
+  b->graphs.assign(graphs, graphs + ng);
+  b->cut_large = p->cut_large > 0 ? p->cut_large : 1024;
+  b->chunk = p->chunk > 0 ? p->chunk : 1024;
+  b->hq.resize(nq);
+  b->qn.resize(nq);
+  b->hseeds.clear();
+  int64_t off[2] = {0, 0};
+  int64_t m_op[2] = {0, 0};
+  for (int q = 0; q < nq; ++q) {
+    const maiter_query& Q = qs[q];
+    const maiter_graph* g = graphs[Q.graph];
+    const int op = Q.op == MAITER_OP_MIN_U32 ? 1 : 0;
+    BQuery& bq = b->hq[q];
+    bq.graph = Q.graph;
+    bq.op = op;
+    bq.off = off[op];
+    bq.damping = Q.damping;
+    bq.tau = op == 0 ? Q.eps / static_cast<double>(g->n) : 0.0;
+    bq.init = op == 0 ? (1.0 - Q.damping) / static_cast<double>(Q.num_seeds) : 0.0;
+    b->qn[q] = g->n;
+    off[op] += g->n;
+    m_op[op] += g->m;
+    for (int s = 0; s < Q.num_seeds; ++s)
+      b->hseeds.push_back(BItem{static_cast<unsigned>(q), Q.seeds[s]});
+  }
+  b->n_sum = off[0];
+  b->n_min = off[1];
+  // large-vertex counts per graph at this cut-off
+  std::vector<unsigned> nlarge(ng, 0);
+  {
+    unsigned* d_cnt = nullptr;
+    MAITER_CUDA(cudaMalloc(&d_cnt, sizeof(unsigned) * ng));
+    MAITER_CUDA(cudaMemset(d_cnt, 0, sizeof(unsigned) * ng));
+    for (int i = 0; i < ng; ++i)
+      k_count_large<<<graphs[i]->num_sms * 2, 256>>>(graphs[i]->rp, static_cast<int>(graphs[i]->n),
+                                                     b->cut_large, d_cnt + i);
+    cudaError_t e = cudaMemcpy(nlarge.data(), d_cnt, sizeof(unsigned) * ng, cudaMemcpyDeviceToHost);
+    cudaFree(d_cnt);
+    MAITER_CUDA(e);
+  }
+  int64_t large_op[2] = {0, 0};
+  for (int q = 0; q < nq; ++q) large_op[b->hq[q].op] += nlarge[b->hq[q].graph];
+  // Capacities: each (query, vertex) sits at most once in a min frontier (round
+  // stamps) and at most twice in a sum frontier (it can cross the threshold
+  // again after its own update); overflow is detected and reported.
+  for (int o = 0; o < kBOps; ++o) {
+    const int64_t n_op = o == 0 ? off[0] : off[1];
+    const int64_t mult = o == 0 ? 2 : 1;
+    const int64_t c0 = n_op * mult + 1024, c1 = large_op[o] * mult + 64;
+    MAITER_REQUIRE(c0 < (int64_t(1) << 32) && c1 < (int64_t(1) << 32),
+                   "batch too large: %lld (query, vertex) states", (long long)n_op);
+    b->cap[o][0] = static_cast<unsigned>(c0);
+    b->cap[o][1] = static_cast<unsigned>(c1);
+  }
+  const int64_t ccap = (large_op[0] * 2 + large_op[1]) + (m_op[0] * 2 + m_op[1]) / b->chunk + 64;
+  MAITER_REQUIRE(ccap < (int64_t(1) << 32), "batch too large for the chunk list");
+  b->chunk_cap = static_cast<unsigned>(ccap);
+
+  std::vector<BGraph> hg(ng);
+  for (int i = 0; i < ng; ++i)
+    hg[i] = BGraph{graphs[i]->rp, graphs[i]->col, graphs[i]->w, static_cast<int>(graphs[i]->n), 0};
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes > 0 ? bytes : 1);
+  };
+  A(reinterpret_cast<void**>(&b->d_graphs), sizeof(BGraph) * ng);
+  A(reinterpret_cast<void**>(&b->d_queries), sizeof(BQuery) * nq);
+  A(reinterpret_cast<void**>(&b->d_seeds), sizeof(BItem) * b->hseeds.size());
+  A(reinterpret_cast<void**>(&b->v_sum), sizeof(double) * b->n_sum);
+  A(reinterpret_cast<void**>(&b->d_sum), sizeof(double) * b->n_sum);
+  A(reinterpret_cast<void**>(&b->v_min), sizeof(uint32_t) * b->n_min);
+  A(reinterpret_cast<void**>(&b->d_min), sizeof(uint32_t) * b->n_min);
+  A(reinterpret_cast<void**>(&b->stamp), sizeof(unsigned) * b->n_min);
+  for (int s = 0; s < 2; ++s)
+    for (int o = 0; o < kBOps; ++o)
+      for (int l = 0; l < 2; ++l)
+        A(reinterpret_cast<void**>(&b->items[s][o][l]), sizeof(BItem) * b->cap[o][l]);
+  A(reinterpret_cast<void**>(&b->chunks), sizeof(BChunk) * b->chunk_cap);
+  A(reinterpret_cast<void**>(&b->qlast), sizeof(unsigned) * nq);
+  A(reinterpret_cast<void**>(&b->ctl), sizeof(BCtl));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_ctl, sizeof(BCtl));
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_graphs, hg.data(), sizeof(BGraph) * ng, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_queries, b->hq.data(), sizeof(BQuery) * nq, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !b->hseeds.empty())
+    e = cudaMemcpy(b->d_seeds, b->hseeds.data(), sizeof(BItem) * b->hseeds.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    set_error("batch allocation failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MAITER_ERR_OOM : MAITER_ERR_CUDA;
+  }
+  return MAITER_OK;
+}
+
+static int batch_grid(const maiter_batch* b, const maiter_batch_params* p) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, reinterpret_cast<const void*>(&k_b_push<kBBlock>), kBBlock, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  if (p->push_blocks_per_sm > 0 && per_sm > p->push_blocks_per_sm) per_sm = p->push_blocks_per_sm;
+  return b->graphs[0]->num_sms * per_sm;
+}
+
+static maiter_status batch_build_graph(maiter_batch* b, int grid) {
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  const BArgs a = batch_args(b);
+  MAITER_CUDA(cudaGraphCreate(&b->graph, 0));
+  cudaGraphConditionalHandle h;
+  MAITER_CUDA(cudaGraphConditionalHandleCreate(&h, b->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  MAITER_CUDA(cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t cap;
+  MAITER_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    k_b_take<kBBlock><<<grid, kBBlock, 0, cap>>>(a);
+    k_b_push<kBBlock><<<grid, kBBlock, 0, cap>>>(a, h, 1);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cap, &captured);
+  }
+  cudaStreamDestroy(cap);
+  MAITER_CUDA(e);
+  MAITER_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  b->exec_grid = grid;
+  return MAITER_OK;
+}
+
+static maiter_status batch_run(maiter_batch* b, const maiter_batch_params* p) {
+  DeviceGuard guard(b->device);
+  cudaStream_t st = static_cast<cudaStream_t>(p->stream);
+  const int grid = batch_grid(b, p);
+  const bool profile = (p->flags & MAITER_FLAG_PROFILE_KERNELS) != 0;
+  if (!profile && (!b->exec || b->exec_grid != grid)) {
+    maiter_status s = batch_build_graph(b, grid);
+    if (s != MAITER_OK) return s;
+  }
+  // identities everywhere (0 for +, infinity for min), then the seeds
+  MAITER_CUDA(cudaMemsetAsync(b->v_sum, 0, sizeof(double) * b->n_sum, st));
+  MAITER_CUDA(cudaMemsetAsync(b->d_sum, 0, sizeof(double) * b->n_sum, st));
+  MAITER_CUDA(cudaMemsetAsync(b->v_min, 0xFF, sizeof(uint32_t) * b->n_min, st));
+  MAITER_CUDA(cudaMemsetAsync(b->d_min, 0xFF, sizeof(uint32_t) * b->n_min, st));
+  MAITER_CUDA(cudaMemsetAsync(b->stamp, 0, sizeof(unsigned) * b->n_min, st));
+  MAITER_CUDA(cudaMemsetAsync(b->qlast, 0, sizeof(unsigned) * b->nq, st));
+  BCtl c{};
+  c.rset = 0;
+  c.wset = 1;
+  c.max_rounds = p->max_rounds > 0 ? p->max_rounds : 1000000;
+  *b->h_ctl = c;
+  MAITER_CUDA(cudaMemcpyAsync(b->ctl, b->h_ctl, sizeof(BCtl), cudaMemcpyHostToDevice, st));
+  const BArgs a = batch_args(b);
+  const int nseeds = static_cast<int>(b->hseeds.size());
+  MAITER_CUDA(cudaEventRecord(b->ev0, st));
+  if (nseeds > 0)
+    k_b_seed<<<(nseeds + 255) / 256, 256, 0, st>>>(a, b->d_seeds, nseeds);
+  MAITER_CUDA(cudaGetLastError());
+  maiter_stats& s = b->stats;
+  s = maiter_stats{};
+  if (profile) {
+    cudaEvent_t e[3];
+    for (auto& x : e) MAITER_CUDA(cudaEventCreate(&x));
+    for (;;) {
+      MAITER_CUDA(cudaEventRecord(e[0], st));
+      k_b_take<kBBlock><<<grid, kBBlock, 0, st>>>(a);
+      MAITER_CUDA(cudaEventRecord(e[1], st));
+      k_b_push<kBBlock><<<grid, kBBlock, 0, st>>>(a, cudaGraphConditionalHandle{}, 0);
+      MAITER_CUDA(cudaEventRecord(e[2], st));
+      MAITER_CUDA(cudaGetLastError());
+      MAITER_CUDA(cudaMemcpyAsync(b->h_ctl, b->ctl, sizeof(BCtl), cudaMemcpyDeviceToHost, st));
+      MAITER_CUDA(cudaStreamSynchronize(st));
+      float t1 = 0.f, t2 = 0.f;
+      cudaEventElapsedTime(&t1, e[0], e[1]);
+      cudaEventElapsedTime(&t2, e[1], e[2]);
+      s.scan_ms += t1;   // the take/expand kernel
+      s.push_ms += t2;
+      s.scan_launches++;
+      s.push_launches++;
+      if (b->h_ctl->status != 0) break;
+    }
+    for (auto& x : e) cudaEventDestroy(x);
+  } else if (nseeds > 0) {
+    MAITER_CUDA(cudaGraphLaunch(b->exec, st));
+  }
+  MAITER_CUDA(cudaEventRecord(b->ev1, st));
+  MAITER_CUDA(cudaMemcpyAsync(b->h_ctl, b->ctl, sizeof(BCtl), cudaMemcpyDeviceToHost, st));
+  MAITER_CUDA(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+  const BCtl& h = *b->h_ctl;
+  s.rounds = static_cast<int64_t>(h.rounds);
+  s.activations = static_cast<int64_t>(h.updates);
+  s.edge_pushes = static_cast<int64_t>(h.pushes);
+  s.residual = 0.0;
+  s.elapsed_ms = ms;
+  const int status = nseeds == 0 ? 1 : h.status;
+  s.converged = status == 1;
+  s.kernel_launches = (nseeds > 0 ? 1 : 0) + 2 * static_cast<int64_t>(h.rounds);
+  if (status == 1) {
+    s.status = MAITER_OK;
+  } else if (status == 2) {
+    s.status = MAITER_ERR_NOT_CONVERGED;
+    set_error("round cap reached before every query converged");
+  } else {
+    s.status = MAITER_ERR_OOM;
+    set_error("a batch frontier outgrew its capacity");
+  }
+  return static_cast<maiter_status>(s.status);
+}
+
+}  // namespace maiter
+
+using namespace maiter;
+
+extern "C" {
+
+void maiter_batch_params_default(maiter_batch_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->max_rounds = 1000000;
+  p->cut_large = 1024;
+  p->chunk = 1024;
+  p->push_blocks_per_sm = 0;
+}
+
+void maiter_batch_destroy(maiter_batch* b) {
+  if (!b) return;
+  DeviceGuard guard(b->device);
+  free_batch_buffers(b);
+  delete b;
+}
+
+maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_graphs,
+                               const maiter_query* queries, int32_t num_queries,
+                               const maiter_batch_params* p, maiter_batch** out) {
+  set_error("%s", "");
+  cudaGetLastError();
+  MAITER_REQUIRE(graphs && queries && p && out, "maiter_run_batch: NULL argument");
+  MAITER_REQUIRE(num_graphs >= 1 && num_queries >= 1, "need at least one graph and one query");
+  for (int i = 0; i < num_graphs; ++i) {
+    MAITER_REQUIRE(graphs[i], "graph %d is NULL", i);
+    MAITER_REQUIRE(graphs[i]->device == graphs[0]->device, "all graphs must be on one device");
+  }
+  MAITER_REQUIRE(p->cut_large >= 0 && p->chunk >= 0 && (p->chunk == 0 || p->chunk >= 32),
+                 "cut_large >= 0 and chunk = 0 or >= 32");
+  MAITER_REQUIRE((p->flags & ~MAITER_FLAG_PROFILE_KERNELS) == 0, "unknown flags 0x%x", p->flags);
+  for (int q = 0; q < num_queries; ++q) {
+    const maiter_query& Q = queries[q];
+    MAITER_REQUIRE(Q.graph >= 0 && Q.graph < num_graphs, "query %d: graph %d out of range", q, Q.graph);
+    MAITER_REQUIRE(Q.op == MAITER_OP_SUM_F64 || Q.op == MAITER_OP_MIN_U32,
+                   "query %d: op must be SUM_F64 (personalised PageRank) or MIN_U32 (SSSP)", q);
+    MAITER_REQUIRE(Q.num_seeds >= 1 && Q.seeds, "query %d: needs at least one seed", q);
+    const maiter_graph* g = graphs[Q.graph];
+    for (int s = 0; s < Q.num_seeds; ++s)
+      MAITER_REQUIRE(Q.seeds[s] >= 0 && Q.seeds[s] < g->n, "query %d: seed out of range", q);
+    if (Q.op == MAITER_OP_SUM_F64) {
+      MAITER_REQUIRE(std::isfinite(Q.damping) && Q.damping >= 0.0 && Q.damping < 1.0,
+                     "query %d: damping must lie in [0, 1)", q);
+      MAITER_REQUIRE(std::isfinite(Q.eps) && Q.eps > 0.0, "query %d: eps must be > 0", q);
+    } else {
+      MAITER_REQUIRE(g->w || g->m == 0, "query %d: SSSP needs edge weights", q);
+    }
+  }
+  DeviceGuard guard(graphs[0]->device);
+  maiter_batch* b = *out;
+  bool fresh = false;
+  // Reuse when the batch has the same shape; rebuild otherwise.
+  bool same = b && b->nq == num_queries && b->ng == num_graphs &&
+              b->cut_large == (p->cut_large > 0 ? p->cut_large : 1024) &&
+              b->chunk == (p->chunk > 0 ? p->chunk : 1024);
+  if (same) {
+    for (int i = 0; i < num_graphs && same; ++i) same = b->graphs[i] == graphs[i];
+    for (int q = 0; q < num_queries && same; ++q) {
+      const maiter_query& Q = queries[q];
+      same = b->hq[q].graph == Q.graph && b->hq[q].op == (Q.op == MAITER_OP_MIN_U32 ? 1 : 0);
+    }
+  }
+  if (!same) {
+    if (!b) {
+      b = new (std::nothrow) maiter_batch();
+      MAITER_REQUIRE(b, "host allocation failed");
+      fresh = true;
+    } else {
+      free_batch_buffers(b);
+    }
+    maiter_status s = batch_setup(b, graphs, num_graphs, queries, num_queries, p);
+    if (s != MAITER_OK) {
+      if (fresh) maiter_batch_destroy(b);
+      return s;
+    }
+  } else {
+    // same shape: refresh thresholds, seeds and damping
+    b->hseeds.clear();
+    for (int q = 0; q < num_queries; ++q) {
+      const maiter_query& Q = queries[q];
+      BQuery& bq = b->hq[q];
+      bq.damping = Q.damping;
+      bq.tau = bq.op == 0 ? Q.eps / static_cast<double>(b->qn[q]) : 0.0;
+      bq.init = bq.op == 0 ? (1.0 - Q.damping) / static_cast<double>(Q.num_seeds) : 0.0;
+      for (int s = 0; s < Q.num_seeds; ++s)
+        b->hseeds.push_back(BItem{static_cast<unsigned>(q), Q.seeds[s]});
+    }
+    cudaFree(b->d_seeds);
+    b->d_seeds = nullptr;
+    MAITER_CUDA(cudaMalloc(&b->d_seeds, sizeof(BItem) * (b->hseeds.empty() ? 1 : b->hseeds.size())));
+    MAITER_CUDA(cudaMemcpy(b->d_seeds, b->hseeds.data(), sizeof(BItem) * b->hseeds.size(),
+                           cudaMemcpyHostToDevice));
+    MAITER_CUDA(cudaMemcpy(b->d_queries, b->hq.data(), sizeof(BQuery) * num_queries,
+                           cudaMemcpyHostToDevice));
+  }
+  maiter_status s = batch_run(b, p);
+  if (s == MAITER_OK || s == MAITER_ERR_NOT_CONVERGED) {
+    *out = b;
+  } else if (fresh) {
+    maiter_batch_destroy(b);
+  }
+  return s;
+}
+
+maiter_status maiter_batch_get_state(const maiter_batch* b, int32_t query, void* out, int64_t count) {
+  set_error("%s", "");
+  MAITER_REQUIRE(b && out, "NULL argument");
+  MAITER_REQUIRE(query >= 0 && query < b->nq, "query %d out of range", query);
+  MAITER_REQUIRE(count == b->qn[query], "count %lld != n %lld of the query's graph",
+                 (long long)count, (long long)b->qn[query]);
+  DeviceGuard guard(b->device);
+  const BQuery& q = b->hq[query];
+  if (q.op == 0)
+    MAITER_CUDA(cudaMemcpy(out, b->v_sum + q.off, sizeof(double) * count, cudaMemcpyDefault));
+  else
+    MAITER_CUDA(cudaMemcpy(out, b->v_min + q.off, sizeof(uint32_t) * count, cudaMemcpyDefault));
+  return MAITER_OK;
+}
+
+maiter_status maiter_batch_get_stats(const maiter_batch* b, maiter_stats* out) {
+  set_error("%s", "");
+  MAITER_REQUIRE(b && out, "NULL argument");
+  *out = b->stats;
+  return MAITER_OK;
+}
+
+maiter_status maiter_batch_query_rounds(const maiter_batch* b, int32_t* out, int32_t count) {
+  set_error("%s", "");
+  MAITER_REQUIRE(b && out && count == b->nq, "need num_queries entries");
+  DeviceGuard guard(b->device);
+  MAITER_CUDA(cudaMemcpy(out, b->qlast, sizeof(int32_t) * count, cudaMemcpyDeviceToHost));
+  return MAITER_OK;
+}
+
+}  // extern "C"

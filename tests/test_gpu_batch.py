@@ -1,0 +1,107 @@
+"""Batched engine: personalised PageRank and SSSP queries over graphs of uneven
+size in one CUDA-graph launch, each query checked against the oracle.
+
+PPR tolerance: the batch stops a query when no vertex has |Delta| > eps_q / n,
+so sum |Delta| <= eps_q and ||v - v*||_1 <= eps_q / (1 - d).  With
+eps_q = 1e-6 (1 - d)^2 / |S| and v* >= (1 - d) / |S| at the seeds, the
+norm-wise relative error is at most 1e-6 (the bound asserted below)."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+D = 0.8
+
+
+@pytest.fixture(scope="module")
+def mt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1710_05785_b300 as m
+    m.lib()
+    return m
+
+
+def make_batch(scales, n_ppr, n_sssp, seed=7):
+    graphs = [graphgen.rmat(s, 8, weights=True, seed=1000 + s + i) for i, s in enumerate(scales)]
+    queries = []
+    for gi, g in enumerate(graphs):
+        for q, S in enumerate(graphgen.ppr_seed_sets(g.n, n_ppr, seed=seed + gi, max_size=16)):
+            eps = 1e-6 * (1 - D) ** 2 / len(S)
+            queries.append(dict(op=0, graph=gi, seeds=S, damping=D, eps=eps))
+        for s in graphgen.sssp_sources(g, n_sssp, seed=seed + 100 + gi):
+            queries.append(dict(op=2, graph=gi, seeds=[int(s)]))
+    return graphs, queries
+
+
+def check(mt, graphs, queries, b):
+    for qi, q in enumerate(queries):
+        g = graphs[q["graph"]]
+        v = b.state(qi)
+        if q["op"] == 2:
+            expect = oracle.dijkstra(g, int(q["seeds"][0]))
+            np.testing.assert_array_equal(v, expect, err_msg=f"query {qi}")
+        else:
+            vstar = oracle.pagerank(g, D, seeds=q["seeds"])
+            assert oracle.relative_error(v, vstar) <= 1e-6, qi
+
+
+def test_batch_mixed_queries_uneven_graphs(mt):
+    graphs, queries = make_batch([8, 10, 11, 12], n_ppr=6, n_sssp=3)
+    G = [mt.Graph.from_csr(g) for g in graphs]
+    b = mt.run_batch(G, queries)
+    check(mt, graphs, queries, b)
+    st = b.stats()
+    assert st["converged"] == 1 and st["rounds"] >= 1
+    qr = b.query_rounds()
+    # 0 for a query whose seeds send nothing (all of them dangling)
+    assert (qr >= 0).all() and qr.max() <= st["rounds"] and (qr > 0).sum() > len(queries) // 2
+
+
+def test_batch_reuse_gives_the_same_answer(mt):
+    graphs, queries = make_batch([9, 11], n_ppr=4, n_sssp=2, seed=3)
+    G = [mt.Graph.from_csr(g) for g in graphs]
+    b = mt.run_batch(G, queries)
+    first = [b.state(i).copy() for i in range(len(queries))]
+    b2 = mt.run_batch(G, queries, batch=b)
+    assert b2 is b
+    for i, q in enumerate(queries):
+        if q["op"] == 2:
+            np.testing.assert_array_equal(first[i], b.state(i))
+        else:
+            assert oracle.relative_error(b.state(i), first[i]) <= 1e-6
+
+
+def test_batch_multi_source_sssp_and_hub_chunks(mt):
+    # a star hub (chunked path) plus an R-MAT graph; a two-seed SSSP query
+    n = 6000
+    src = np.concatenate([np.zeros(n - 1, np.int64), np.arange(1, n - 1)])
+    dst = np.concatenate([np.arange(1, n), np.arange(2, n)])
+    w = (np.arange(src.size) % 7 + 1).astype(np.uint32)
+    star = graphgen.csr_from_edges(n, src, dst, w)
+    r = graphgen.rmat(11, 8, weights=True)
+    G = [mt.Graph.from_csr(star), mt.Graph.from_csr(r)]
+    s2 = graphgen.sssp_sources(r, 2)
+    queries = [dict(op=2, graph=0, seeds=[0]), dict(op=0, graph=0, seeds=[0, 5], damping=D,
+                                                    eps=1e-6 * (1 - D) ** 2 / 2),
+               dict(op=2, graph=1, seeds=[int(s2[0]), int(s2[1])])]
+    b = mt.run_batch(G, queries, cut_large=256, chunk=512)
+    np.testing.assert_array_equal(b.state(0), oracle.dijkstra(star, 0))
+    assert oracle.relative_error(b.state(1), oracle.pagerank(star, D, seeds=[0, 5])) <= 1e-6
+    expect = np.minimum(oracle.dijkstra(r, int(s2[0])), oracle.dijkstra(r, int(s2[1])))
+    np.testing.assert_array_equal(b.state(2), expect)
+
+
+def test_batch_rejects_bad_queries(mt):
+    g = graphgen.rmat(6, 4, weights=True)
+    G = [mt.Graph.from_csr(g)]
+    with pytest.raises(mt.MaiterError):
+        mt.run_batch(G, [dict(op=2, graph=0, seeds=[g.n])])
+    with pytest.raises(mt.MaiterError):
+        mt.run_batch(G, [dict(op=1, graph=0, seeds=[0])])
+    with pytest.raises(mt.MaiterError):
+        mt.run_batch(G, [dict(op=0, graph=1, seeds=[0], eps=1e-6)])
