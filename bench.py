@@ -266,6 +266,92 @@ def run_pagerank(args, wl):
         print(json.dumps(line), flush=True)
 
 
+BATCH_SCALES = [16, 17, 18, 19, 20, 21, 22, 22]   # the last scale-22 graph on a second seed
+
+
+def batch_workload(scales=BATCH_SCALES, ppr_per_graph=64, sssp_per_graph=16, ef=16, d=0.8):
+    """Configuration 4: 512 personalised-PageRank queries (seed sets of 1-64
+    vertices, sizes log-uniform) and 128 SSSP sources over 8 R-MAT graphs."""
+    graphs, queries = [], []
+    for gi, s in enumerate(scales):
+        seed = graphgen.DEFAULT_SEED_BASE + s + (1000 if gi == len(scales) - 1 else 0)
+        g = graphgen.rmat(s, ef, seed=seed, weights=True)
+        graphs.append(g)
+        for S in graphgen.ppr_seed_sets(g.n, ppr_per_graph, seed=seed + 7):
+            queries.append(dict(op=0, graph=gi, seeds=S, damping=d, eps=1e-6 * (1 - d) ** 2 / len(S)))
+        for src in graphgen.sssp_sources(g, sssp_per_graph, seed=seed + 11):
+            queries.append(dict(op=2, graph=gi, seeds=[int(src)]))
+    return graphs, queries
+
+
+def run_batch_bench(args):
+    """One step = every query of configuration 4 to its own termination, in
+    one CUDA-graph launch; value = sum over queries of m / step time."""
+    import torch
+    import paper_1710_05785_b300 as mt
+    from paper_1710_05785_b300 import autotune
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    graphs, queries = batch_workload()
+    G = [mt.Graph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
+                  torch.from_numpy(g.w.view(np.int32)).to(dev), device=local) for g in graphs]
+    tuned = autotune.tune_batch(mt, graphs, G, queries, cache=autotune.Cache(None), sample=48)
+    untuned = dict(cut_large=1024, chunk=1024, push_blocks_per_sm=0)
+    edges = float(sum(graphs[q["graph"]].m for q in queries))
+    out = {}
+    for name, cfg in [("tuned", tuned), ("default", untuned)]:
+        b = None
+        for _ in range(max(args.warmup, 1) if name == "tuned" else 1):
+            b = mt.run_batch(G, queries, batch=b, stream=stream, **cfg)
+        reps = args.steps if name == "tuned" else 1
+        times = []
+        for _ in range(reps):
+            b = mt.run_batch(G, queries, batch=b, stream=stream, **cfg)
+            times.append(b.stats()["elapsed_ms"])
+        st = b.stats()
+        qr = b.query_rounds()
+        out[name] = dict(ms=float(np.mean(times)), stats=st, qrounds=qr, cfg=cfg)
+        if name == "tuned":
+            prof = mt.run_batch(G, queries, batch=b, stream=stream,
+                                flags=mt.FLAG_PROFILE_KERNELS, **cfg).stats()
+        b.close()
+    ms = out["tuned"]["ms"]
+    st = out["tuned"]["stats"]
+    peaks, peak_kind = measured_peaks()
+    # PPR pushes dominate: 20 B per edge (FP64), 40 B per update
+    alg = 20 * prof["edge_pushes"] + 40 * prof["activations"]
+    achieved = alg / (prof["push_ms"] * 1e-3) / 1e9
+    qr = out["tuned"]["qrounds"]
+    line = {
+        "metric": METRIC, "value": edges / (ms * 1e-3) / 1e9, "unit": "GTEPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64/u32", "data": "synthetic",
+        "config": {"workload": "batch: 512 PPR (seed sets 1-64, log-uniform) + 128 SSSP over 8 "
+                               "R-MAT graphs, scales 16-22 (22 twice), edge factor 16",
+                   "queries": len(queries), "graphs": len(graphs),
+                   "ppr_eps": "1e-6 (1-d)^2 / |S| per query", "launch": "one CUDA graph per batch",
+                   "tuned": tuned},
+        "queries_per_s": len(queries) / (ms * 1e-3),
+        "rounds": st["rounds"], "query_rounds": {"min": int(qr.min()), "median": float(np.median(qr)),
+                                                 "max": int(qr.max())},
+        "edge_pushes": st["edge_pushes"],
+        "vs_untuned": out["default"]["ms"] / ms,
+        "untuned_ms": out["default"]["ms"],
+        "roofline": {"bound": "hbm", "kernel": "k_b_push", "achieved": achieved,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                     "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "push_launches": prof["push_launches"],
+                     "push_ms_per_launch": prof["push_ms"] / max(prof["push_launches"], 1)},
+        "gpu_launches": int(st["kernel_launches"]) * (args.steps + 1),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -275,7 +361,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--workload", default="sssp-rmat20",
-                    choices=["sssp-rmat20"] + sorted(PR_WORKLOADS),
+                    choices=["sssp-rmat20", "batch"] + sorted(PR_WORKLOADS),
                     help="sssp-rmat20 (default; configuration 2) or a PageRank configuration")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -283,6 +369,9 @@ def main():
         return
     if args.workload in PR_WORKLOADS:
         run_pagerank(args, args.workload)
+        return
+    if args.workload == "batch":
+        run_batch_bench(args)
         return
 
     import torch

@@ -150,6 +150,13 @@ typedef struct maiter_run_params {
                           (0 = 10,000 ms); when it runs out the run returns
                           MAITER_ERR_TIMEOUT with a valid, resumable state */
   void* stream;        /* cudaStream_t to run on; NULL = the default stream */
+  /* Tuning (0 = built-in default), e.g. from the autotuner: */
+  int32_t cut_warp;    /* out-degree below which a vertex takes the warp-gathered
+                          path (default 32) */
+  int32_t cut_cta;     /* out-degree from which a vertex is split into 1024-edge
+                          chunks, one CTA each (default 512) */
+  int32_t push_blocks_per_sm;  /* cap on resident push CTAs per SM (default: occupancy) */
+  int32_t reserved1;   /* must be 0 */
 } maiter_run_params;
 
 typedef struct maiter_stats {
@@ -308,6 +315,10 @@ const char* maiter_last_error(void);
 
 /* Library version string. */
 const char* maiter_version(void);
+
+/* Name (NUL-terminated, truncated to len) and SM count of a device; used to
+ * key tuning caches.  Errors: INVALID_ARG, CUDA. */
+maiter_status maiter_device_info(int device, char* name, int32_t len, int32_t* num_sms);
 
 #ifdef __cplusplus
 }

@@ -56,6 +56,8 @@ class RunParams(ctypes.Structure):
         ("mixed_switch", ctypes.c_double),
         ("max_rounds", ctypes.c_int64), ("timeout_ms", ctypes.c_int64),
         ("stream", ctypes.c_void_p),
+        ("cut_warp", ctypes.c_int32), ("cut_cta", ctypes.c_int32),
+        ("push_blocks_per_sm", ctypes.c_int32), ("reserved1", ctypes.c_int32),
     ]
 
 
@@ -121,6 +123,8 @@ def lib():
         L.maiter_batch_query_rounds.argtypes = [P, P, i32]
         L.maiter_batch_query_rounds.restype = i32
         L.maiter_batch_destroy.argtypes = [P]
+        L.maiter_device_info.argtypes = [ctypes.c_int, ctypes.c_char_p, i32, ctypes.POINTER(i32)]
+        L.maiter_device_info.restype = i32
         _lib = L
     return _lib
 
@@ -253,6 +257,7 @@ def run(graph: Graph, op: int = OP_SUM_F64, *, coef=None, damping: float = 0.8, 
         top_frac: float = 0.01, eps: float = 1e-8, mixed_switch: float = 0.01,
         max_rounds: int = 1000000,
         timeout_ms: int = 0, stream=None, engine: int = ENGINE_SYNC, flags: int = 0,
+        cut_warp: int = 0, cut_cta: int = 0, push_blocks_per_sm: int = 0,
         result: Result | None = None, allow_not_converged: bool = False) -> Result:
     """``maiter_run``: one DAIC run to termination.  ``stream`` is a raw
     cudaStream_t handle (e.g. ``torch.cuda.current_stream().cuda_stream``)."""
@@ -278,6 +283,7 @@ def run(graph: Graph, op: int = OP_SUM_F64, *, coef=None, damping: float = 0.8, 
     p.source = source
     p.threshold, p.top_frac, p.eps = threshold, top_frac, eps
     p.mixed_switch = mixed_switch
+    p.cut_warp, p.cut_cta, p.push_blocks_per_sm = cut_warp, cut_cta, push_blocks_per_sm
     p.max_rounds, p.timeout_ms = max_rounds, timeout_ms
     p.stream = stream
     h = ctypes.c_void_p(result.handle.value if result is not None else None)
@@ -369,6 +375,14 @@ def run_batch(graphs, queries, *, max_rounds: int = 1000000, stream=None, cut_la
         batch.queries = [(int(q["op"]), int(q["graph"])) for q in queries]
     _check(st)
     return batch
+
+
+def device_info(device: int = 0) -> tuple[str, int]:
+    """(name, SM count) of a CUDA device, from ``maiter_device_info``."""
+    buf = ctypes.create_string_buffer(256)
+    sms = ctypes.c_int32(0)
+    _check(lib().maiter_device_info(device, buf, 256, ctypes.byref(sms)))
+    return buf.value.decode(), sms.value
 
 
 def version() -> str:

@@ -73,6 +73,19 @@ const char* maiter_last_error(void) { return g_err; }
 
 const char* maiter_version(void) { return "maiter-b300 0.1 (sm_103a)"; }
 
+maiter_status maiter_device_info(int device, char* name, int32_t len, int32_t* num_sms) {
+  begin_call();
+  MAITER_REQUIRE(name && len > 0 && num_sms, "NULL argument");
+  int ndev = 0;
+  MAITER_CUDA(cudaGetDeviceCount(&ndev));
+  MAITER_REQUIRE(device >= 0 && device < ndev, "device %d out of range", device);
+  cudaDeviceProp prop{};
+  MAITER_CUDA(cudaGetDeviceProperties(&prop, device));
+  std::snprintf(name, static_cast<size_t>(len), "%s", prop.name);
+  *num_sms = prop.multiProcessorCount;
+  return MAITER_OK;
+}
+
 void maiter_params_default(maiter_run_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));
@@ -416,7 +429,10 @@ static maiter_status build_graph(const maiter_graph* g, maiter_result* r, int op
 
 static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
                               maiter_result* r, cudaStream_t st) {
-  const Tuning tu{};
+  Tuning tu{};
+  if (p->cut_warp > 0) tu.cut_warp = p->cut_warp;
+  if (p->cut_cta > 0) tu.cut_cta = p->cut_cta;
+  if (p->push_blocks_per_sm > 0) tu.push_blocks_per_sm = p->push_blocks_per_sm;
   RunPlan plan;
   {
     maiter_status ps = setup_plan(g, p, r, tu, &plan);
@@ -434,6 +450,7 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   mix(static_cast<uint64_t>(tu.cut_warp));
   mix(static_cast<uint64_t>(tu.cut_cta));
   mix(p->sched == MAITER_SCHED_TOPFRAC ? 1 : 0);
+  mix(static_cast<uint64_t>(tu.push_blocks_per_sm));
   const bool profile = (p->flags & MAITER_FLAG_PROFILE_KERNELS) != 0;
   if (!profile && (!r->exec || r->exec_key != key)) {
     maiter_status s = build_graph(g, r, p->op, plan);
@@ -594,6 +611,11 @@ maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p, mait
   MAITER_REQUIRE(p->engine == MAITER_ENGINE_SYNC || p->engine == MAITER_ENGINE_ASYNC,
                  "unknown engine %d", p->engine);
   MAITER_REQUIRE(p->timeout_ms >= 0, "timeout_ms must be >= 0");
+  MAITER_REQUIRE(p->cut_warp >= 0 && p->cut_cta >= 0 && p->push_blocks_per_sm >= 0 &&
+                     p->reserved1 == 0,
+                 "tuning fields must be >= 0 (0 = default)");
+  MAITER_REQUIRE(p->cut_warp == 0 || p->cut_cta == 0 || p->cut_warp <= p->cut_cta,
+                 "cut_warp must not exceed cut_cta");
   if (p->engine == MAITER_ENGINE_ASYNC && p->sched == MAITER_SCHED_TOPFRAC) {
     set_error("the asynchronous engine schedules by threshold; use the sync engine for TOPFRAC");
     return MAITER_ERR_UNSUPPORTED;

@@ -96,6 +96,25 @@ def test_batch_multi_source_sssp_and_hub_chunks(mt):
     np.testing.assert_array_equal(b.state(2), expect)
 
 
+def test_autotuned_configs_keep_results_exact(mt, tmp_path):
+    from paper_1710_05785_b300 import autotune
+    graphs, queries = make_batch([9, 11], n_ppr=3, n_sssp=2, seed=5)
+    G = [mt.Graph.from_csr(g) for g in graphs]
+    cache = autotune.Cache(str(tmp_path / "t.json"))
+    best = autotune.tune_batch(mt, graphs, G, queries, cache=cache, sample=8)
+    assert set(best) == {"cut_large", "chunk", "push_blocks_per_sm"}
+    assert autotune.tune_batch(mt, graphs, G, queries, cache=cache, sample=8) == best  # cached
+    b = mt.run_batch(G, queries, **best)
+    check(mt, graphs, queries, b)
+    # single-run tuning: SSSP on one graph, then an exact run with the tuned cut-offs
+    g = graphs[1]
+    Gs = G[1]
+    s = int(queries[-1]["seeds"][0])
+    cfg = autotune.tune_run(mt, g, Gs, dict(op=mt.OP_MIN_U32, source=s), cache=cache)
+    r = mt.run(Gs, mt.OP_MIN_U32, source=s, **cfg)
+    np.testing.assert_array_equal(r.state(), oracle.dijkstra(g, s))
+
+
 def test_batch_rejects_bad_queries(mt):
     g = graphgen.rmat(6, 4, weights=True)
     G = [mt.Graph.from_csr(g)]
