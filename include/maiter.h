@@ -82,10 +82,17 @@ typedef enum {
   MAITER_SCHED_ALL = 0,       /* every vertex with a pending delta
                                  (Delta_j != 0 for +, Delta_j < v_j for min) */
   MAITER_SCHED_THRESHOLD = 1, /* +: |Delta_j| > threshold; min: as ALL */
-  MAITER_SCHED_TOPFRAC = 2    /* the top_frac fraction of pending vertices by
+  MAITER_SCHED_TOPFRAC = 2,   /* the top_frac fraction of pending vertices by
                                  priority, ties included (priority queue of
                                  Section 5.1) */
+  MAITER_SCHED_LEARNED = 3    /* the top_frac fraction of pending vertices by the
+                                 score of a learned network (params.scorer, a
+                                 maiter_mlp); every 8th round activates every
+                                 pending vertex, so none can starve (Theorem 3
+                                 needs every vertex updated again eventually) */
 } maiter_sched;
+
+typedef struct maiter_mlp maiter_mlp;       /* opaque: learned priority scorer */
 
 typedef enum {
   MAITER_ENGINE_SYNC = 0,     /* round loop: frontier, then push; the loop and its
@@ -157,6 +164,7 @@ typedef struct maiter_run_params {
                           chunks, one CTA each (default 512) */
   int32_t push_blocks_per_sm;  /* cap on resident push CTAs per SM (default: occupancy) */
   int32_t reserved1;   /* must be 0 */
+  const maiter_mlp* scorer;    /* LEARNED: the network (same device as the graph) */
 } maiter_run_params;
 
 typedef struct maiter_stats {
@@ -251,6 +259,51 @@ maiter_status maiter_sssp_noalloc(int64_t n, int64_t m, const int32_t* row_ptr,
                                   const int32_t* col, const uint32_t* w, int64_t source,
                                   uint32_t* v_out, uint32_t* delta_out, int64_t max_rounds,
                                   int device, void* stream, int64_t* rounds_out);
+
+/* -------------------------------------------------------- learned scorer
+ * A 2-layer network 8 -> 64 (ReLU) -> 1 scores pending vertices for
+ * MAITER_SCHED_LEARNED.  Weights are BF16 on the device (an FP32 master copy
+ * is kept for training); inputs are rounded to BF16; every product is
+ * accumulated in FP32.  Parameters, FP32, in this order: W1[64][8] (row-major),
+ * b1[64], w2[64], b2 (641 values).  Features of vertex j (8 values, the
+ * library computes them itself when scheduling; maiter_trace records them):
+ *   sum ops: log1p(|Delta_j| n), log1p(v_j), log1p(indeg_j), log1p(outdeg_j),
+ *            log1p(rounds since j's last update), 1,
+ *            log1p(|Delta_j| n / (outdeg_j + 1)), 0
+ *   min:     log1p(Delta_j) or 0 if infinite, log1p(v_j) or 0 if infinite,
+ *            log1p(indeg_j), log1p(outdeg_j), log1p(rounds since last update),
+ *            [Delta_j finite], [v_j finite], 0 */
+#define MAITER_MLP_INPUTS 8
+#define MAITER_MLP_HIDDEN 64
+#define MAITER_MLP_PARAMS 641
+
+/* Creates a network on `device` with seeded He-style random weights. */
+maiter_status maiter_mlp_create(int device, uint64_t seed, maiter_mlp** out);
+maiter_status maiter_mlp_set_params(maiter_mlp* m, const float* params);   /* 641 FP32 */
+maiter_status maiter_mlp_get_params(const maiter_mlp* m, float* params);
+/* out[i] = network(x[i*8 .. i*8+8)) for i < n (x, out: host or device FP32). */
+maiter_status maiter_mlp_forward(const maiter_mlp* m, const float* x, int64_t n, float* out);
+/* Gradient of the mean squared error (1/n) sum_i (net(x_i) - y_i)^2 with
+ * respect to the 641 parameters (evaluated at the BF16 weights), and the loss. */
+maiter_status maiter_mlp_gradients(const maiter_mlp* m, const float* x, const float* y, int64_t n,
+                                   float* grad, float* loss);
+/* Adam on the GPU: `epochs` passes over (x, y) in seeded random minibatches
+ * of `batch` rows; *final_loss = mean squared error of the last minibatch. */
+maiter_status maiter_mlp_train(maiter_mlp* m, const float* x, const float* y, int64_t n,
+                               int32_t epochs, int32_t batch, float lr, uint64_t seed,
+                               float* final_loss);
+void maiter_mlp_destroy(maiter_mlp* m);
+
+/* Activation trace of a round-engine run (SUM_F64 or MIN_U32; any schedule
+ * but LEARNED): after every push of the first max_records rounds, records for
+ * each of the num_sample vertices in `sample` its 8 features, Delta, v and the
+ * round of its last update (1-based, 0 = never), into host arrays of
+ * max_records x num_sample rows.  The run continues to termination; *out
+ * receives its result (as maiter_run).  *records = rows written. */
+maiter_status maiter_trace(const maiter_graph* g, const maiter_run_params* p,
+                           const int32_t* sample, int32_t num_sample, int32_t max_records,
+                           float* features, double* delta, double* v, uint32_t* last_update,
+                           int32_t* records, maiter_result** out);
 
 /* ------------------------------------------------------------------ batch
  * Many queries - personalised PageRank (+, g = d x / outdeg) and SSSP (min,

@@ -32,7 +32,8 @@ _STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CON
 # maiter_op / maiter_g / maiter_sched / maiter_engine
 OP_SUM_F64, OP_SUM_MIXED, OP_MIN_U32 = 0, 1, 2
 G_SCALE_BY_SRC, G_ADD_EDGE = 0, 1
-SCHED_ALL, SCHED_THRESHOLD, SCHED_TOPFRAC = 0, 1, 2
+SCHED_ALL, SCHED_THRESHOLD, SCHED_TOPFRAC, SCHED_LEARNED = 0, 1, 2, 3
+MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 8, 64, 641
 ENGINE_SYNC, ENGINE_ASYNC = 0, 1
 FLAG_PROFILE_KERNELS, FLAG_INJECT_STALL = 1, 2
 
@@ -58,6 +59,7 @@ class RunParams(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("cut_warp", ctypes.c_int32), ("cut_cta", ctypes.c_int32),
         ("push_blocks_per_sm", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("scorer", ctypes.c_void_p),
     ]
 
 
@@ -125,6 +127,23 @@ def lib():
         L.maiter_batch_destroy.argtypes = [P]
         L.maiter_device_info.argtypes = [ctypes.c_int, ctypes.c_char_p, i32, ctypes.POINTER(i32)]
         L.maiter_device_info.restype = i32
+        L.maiter_mlp_create.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]
+        L.maiter_mlp_create.restype = i32
+        L.maiter_mlp_set_params.argtypes = [P, P]
+        L.maiter_mlp_set_params.restype = i32
+        L.maiter_mlp_get_params.argtypes = [P, P]
+        L.maiter_mlp_get_params.restype = i32
+        L.maiter_mlp_forward.argtypes = [P, P, i64, P]
+        L.maiter_mlp_forward.restype = i32
+        L.maiter_mlp_gradients.argtypes = [P, P, P, i64, P, ctypes.POINTER(ctypes.c_float)]
+        L.maiter_mlp_gradients.restype = i32
+        L.maiter_mlp_train.argtypes = [P, P, P, i64, i32, i32, ctypes.c_float, ctypes.c_uint64,
+                                       ctypes.POINTER(ctypes.c_float)]
+        L.maiter_mlp_train.restype = i32
+        L.maiter_mlp_destroy.argtypes = [P]
+        L.maiter_trace.argtypes = [P, ctypes.POINTER(RunParams), P, i32, i32, P, P, P, P,
+                                   ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_void_p)]
+        L.maiter_trace.restype = i32
         _lib = L
     return _lib
 
@@ -257,7 +276,7 @@ def run(graph: Graph, op: int = OP_SUM_F64, *, coef=None, damping: float = 0.8, 
         top_frac: float = 0.01, eps: float = 1e-8, mixed_switch: float = 0.01,
         max_rounds: int = 1000000,
         timeout_ms: int = 0, stream=None, engine: int = ENGINE_SYNC, flags: int = 0,
-        cut_warp: int = 0, cut_cta: int = 0, push_blocks_per_sm: int = 0,
+        cut_warp: int = 0, cut_cta: int = 0, push_blocks_per_sm: int = 0, scorer=None,
         result: Result | None = None, allow_not_converged: bool = False) -> Result:
     """``maiter_run``: one DAIC run to termination.  ``stream`` is a raw
     cudaStream_t handle (e.g. ``torch.cuda.current_stream().cuda_stream``)."""
@@ -284,6 +303,7 @@ def run(graph: Graph, op: int = OP_SUM_F64, *, coef=None, damping: float = 0.8, 
     p.threshold, p.top_frac, p.eps = threshold, top_frac, eps
     p.mixed_switch = mixed_switch
     p.cut_warp, p.cut_cta, p.push_blocks_per_sm = cut_warp, cut_cta, push_blocks_per_sm
+    p.scorer = scorer.handle.value if scorer is not None else None
     p.max_rounds, p.timeout_ms = max_rounds, timeout_ms
     p.stream = stream
     h = ctypes.c_void_p(result.handle.value if result is not None else None)
@@ -375,6 +395,89 @@ def run_batch(graphs, queries, *, max_rounds: int = 1000000, stream=None, cut_la
         batch.queries = [(int(q["op"]), int(q["graph"])) for q in queries]
     _check(st)
     return batch
+
+
+class MLP:
+    """``maiter_mlp``: the learned priority scorer (8 -> 64 -> 1, BF16 weights)."""
+
+    def __init__(self, device: int = 0, seed: int = 0, params=None):
+        h = ctypes.c_void_p()
+        _check(lib().maiter_mlp_create(device, seed, ctypes.byref(h)))
+        self.handle = h
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.shape != (MLP_PARAMS,):
+            raise ValueError(f"need {MLP_PARAMS} parameters")
+        _check(lib().maiter_mlp_set_params(self.handle, _addr(p)))
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, dtype=np.float32)
+        _check(lib().maiter_mlp_get_params(self.handle, _addr(out)))
+        return out
+
+    def forward(self, x) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, MLP_INPUTS)
+        out = np.empty(x.shape[0], dtype=np.float32)
+        _check(lib().maiter_mlp_forward(self.handle, _addr(x), x.shape[0], _addr(out)))
+        return out
+
+    def gradients(self, x, y):
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, MLP_INPUTS)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float(0.0)
+        _check(lib().maiter_mlp_gradients(self.handle, _addr(x), _addr(y), x.shape[0], _addr(g),
+                                          ctypes.byref(loss)))
+        return g, loss.value
+
+    def train(self, x, y, epochs: int = 10, batch: int = 1024, lr: float = 1e-3, seed: int = 0):
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, MLP_INPUTS)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        loss = ctypes.c_float(0.0)
+        _check(lib().maiter_mlp_train(self.handle, _addr(x), _addr(y), x.shape[0], epochs, batch,
+                                      lr, seed, ctypes.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if self.handle:
+            lib().maiter_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def trace(graph: Graph, op: int, sample, max_records: int, **run_kwargs):
+    """``maiter_trace``: features, deltas, states and last-update rounds of the
+    sampled vertices after every push of the first ``max_records`` rounds of a
+    round-engine run.  Returns (dict of arrays shaped [records, samples, ...],
+    the run's Result)."""
+    sample = np.ascontiguousarray(sample, dtype=np.int32)
+    ns = sample.shape[0]
+    feat = np.empty((max_records, ns, MLP_INPUTS), dtype=np.float32)
+    dl = np.empty((max_records, ns), dtype=np.float64)
+    vs = np.empty((max_records, ns), dtype=np.float64)
+    la = np.empty((max_records, ns), dtype=np.uint32)
+    p = params_default()
+    p.op = op
+    p.g = G_ADD_EDGE if op == OP_MIN_U32 else G_SCALE_BY_SRC
+    for k, v in run_kwargs.items():
+        setattr(p, k, v)
+    rec = ctypes.c_int32(0)
+    h = ctypes.c_void_p()
+    st = lib().maiter_trace(graph.handle, ctypes.byref(p), _addr(sample), ns, max_records,
+                            _addr(feat), _addr(dl), _addr(vs), _addr(la), ctypes.byref(rec),
+                            ctypes.byref(h))
+    res = Result(h, graph, op) if h.value else None
+    _check(st, (OK, ERR_NOT_CONVERGED))
+    r = rec.value
+    return dict(features=feat[:r], delta=dl[:r], v=vs[:r], last_update=la[:r]), res
 
 
 def device_info(device: int = 0) -> tuple[str, int]:

@@ -103,7 +103,9 @@ struct KArgs {
   typename Op::D* large_d;       // large: the delta taken by the scan, per entry
   unsigned int large_cap;        // capacity of large / large_d
   DevCtl* ctl;
-  const TopqCtl* topq;           // non-null: select key >= topq->key_thr (TOPFRAC)
+  const TopqCtl* topq;           // non-null: select key >= topq->key_thr (TOPFRAC, LEARNED)
+  const unsigned* keys;          // non-null (LEARNED): per-vertex priority keys from the scorer
+  unsigned* last_act;            // non-null: round of each vertex's last update (1-based)
   int cut_warp;                  // deg <  cut_warp : small bucket
   int cut_cta;                   // deg >= cut_cta  : large bucket (chunked)
 };
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
         } else {
           sel = pend;
         }
-        if (a.topq) sel = pend && priority_key<Op>(d, vv) >= key_thr;
+        if (a.topq) sel = pend && (a.keys ? a.keys[j] : priority_key<Op>(d, vv)) >= key_thr;
         if (sel) {
           const int deg = __ldg(a.rp + j + 1) - __ldg(a.rp + j);
           const int b = deg < a.cut_warp ? 0 : (deg < a.cut_cta ? 1 : 2);
@@ -357,6 +359,8 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a) {
   const int cM = static_cast<int>(ctl->cnt[rs][1]);
   const int cL = static_cast<int>(ctl->cnt[rs][2]);
   const int lane = threadIdx.x & 31;
+  // rounds of the updates this launch performs (for the scorer's age feature)
+  const unsigned round = static_cast<unsigned>(ctl->rounds);
 
   // Large vertices: one CTA per chunk of kChunk edges.  The delta was taken
   // by the scan; chunk 0 folds it into v_j.
@@ -366,6 +370,7 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a) {
     const int rb = __ldg(a.rp + j), re = __ldg(a.rp + j + 1);
     const Msg m = Op::finish(j, re - rb, a.large_d[i], a.v, a.coef, a.damping,
                              q == 0 && threadIdx.x == 0);
+    if (a.last_act && q == 0 && threadIdx.x == 0) a.last_act[j] = round;
     if (Op::live(m)) {
       const int beg = rb + q * kChunk;
       const int end = min(re, beg + kChunk);
@@ -385,6 +390,7 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a) {
       beg = __ldg(a.rp + j);
       end = __ldg(a.rp + j + 1);
       m = Op::fold(j, end - beg, a.delta, a.v, a.coef, a.damping);
+      if (a.last_act) a.last_act[j] = round;
     }
     m = __shfl_sync(0xffffffffu, m, 0);
     beg = __shfl_sync(0xffffffffu, beg, 0);
@@ -403,6 +409,7 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a) {
       beg = __ldg(a.rp + j);
       deg = __ldg(a.rp + j + 1) - beg;
       m = Op::fold(j, deg, a.delta, a.v, a.coef, a.damping);
+      if (a.last_act) a.last_act[j] = round;
       if (!Op::live(m)) deg = 0;
     }
     const int incl = warp_incl_scan(deg, lane);

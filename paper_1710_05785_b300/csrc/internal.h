@@ -10,6 +10,7 @@
 #include "daic_kernels.cuh"
 #include "async_kernels.cuh"
 #include "topq_kernels.cuh"
+#include "learned_kernels.cuh"
 
 namespace maiter {
 
@@ -65,6 +66,7 @@ struct maiter_graph {
   int* rp = nullptr;           // n + 1 int32 offsets
   int* col = nullptr;          // m targets
   uint32_t* w = nullptr;       // m weights or null
+  int* indeg = nullptr;        // in-degrees (computed on first use by the learned scorer)
   int num_sms = 0;
 };
 
@@ -83,6 +85,8 @@ struct maiter_result {
   unsigned large_cap = 0;              // n + m / kChunk + 1 entries
   maiter::DevCtl* ctl = nullptr;
   maiter::TopqCtl* topq = nullptr;     // top-fraction selection (allocated on first use)
+  unsigned* keys = nullptr;            // learned scheduling: per-vertex keys
+  unsigned* last_act = nullptr;        // learned scheduling / traces: last update round
   maiter::DevCtl* h_ctl = nullptr;   // pinned mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // cached executable graph of the round loop
@@ -102,6 +106,9 @@ struct maiter_result {
 };
 
 namespace maiter {
+// The learned scorer's BF16 weights on the device, and its device (mlp.cu).
+const MlpWeights* mlp_device_weights(const maiter_mlp* m);
+int mlp_device(const maiter_mlp* m);
 // Persistent asynchronous engine (async_engine.cu); v and Delta are initialised.
 maiter_status run_async(const maiter_graph* g, const maiter_run_params* p, maiter_result* r,
                         cudaStream_t st);

@@ -111,6 +111,7 @@ void maiter_graph_destroy(maiter_graph* g) {
   cudaFree(g->rp);
   cudaFree(g->col);
   cudaFree(g->w);
+  cudaFree(g->indeg);
   delete g;
 }
 
@@ -198,6 +199,8 @@ void maiter_result_destroy(maiter_result* r) {
   cudaFree(r->large_d);
   cudaFree(r->ctl);
   cudaFree(r->topq);
+  cudaFree(r->keys);
+  cudaFree(r->last_act);
   free_async(r);
   if (r->h_ctl) cudaFreeHost(r->h_ctl);
   if (r->ev0) cudaEventDestroy(r->ev0);
@@ -254,15 +257,36 @@ static int grid_for(const void* fn, int block, int num_sms, int per_sm_cap) {
 
 constexpr int kBlock = 256;
 
+// Device buffers that a traced run fills, one row per (record, sampled vertex).
+struct TraceSink {
+  const int* sample = nullptr;
+  int ns = 0;
+  int max_records = 0;
+  int records = 0;
+  float* feat = nullptr;
+  double* dl = nullptr;
+  double* vs = nullptr;
+  unsigned* la = nullptr;
+};
+
 // One phase of the round loop, WHILE(cond) { k_push ; k_scan }, for one
 // operator: its kernel arguments and launch shapes.
 template <class Op>
 struct Phase {
   KArgs<Op> a{};
   int push_grid = 1, scan_grid = 1, hist_grid = 1;
+  const MlpWeights* mlp = nullptr;    // LEARNED: scorer weights
+  const int* indeg = nullptr;         // LEARNED / traces: in-degrees
+  unsigned* keys = nullptr;           // LEARNED: key array written by k_score
 
   void setup(const maiter_graph* g, maiter_result* r, void* delta, const void* coef,
-             double damping, const Tuning& tu, bool topq) {
+             double damping, const Tuning& tu, bool topq, const MlpWeights* scorer = nullptr,
+             bool track = false) {
+    mlp = scorer;
+    indeg = g->indeg;
+    keys = scorer ? r->keys : nullptr;
+    a.keys = keys;
+    a.last_act = (scorer || track) ? r->last_act : nullptr;
     a.n = static_cast<int>(g->n);
     a.rp = g->rp;
     a.edges.col = g->col;
@@ -292,6 +316,7 @@ struct Phase {
   void launch_select(cudaStream_t s) const {
     if (!a.topq) return;
     TopqCtl* tq = const_cast<TopqCtl*>(a.topq);
+    if (mlp) k_score<Op, kBlock><<<hist_grid, kBlock, 0, s>>>(a, mlp, indeg, keys);
     k_topq_hist<Op, kBlock, 0><<<hist_grid, kBlock, 0, s>>>(a, tq);
     k_topq_hist<Op, kBlock, 1><<<hist_grid, kBlock, 0, s>>>(a, tq);
     k_topq_hist<Op, kBlock, 2><<<hist_grid, kBlock, 0, s>>>(a, tq);
@@ -327,13 +352,21 @@ struct Phase {
     return MAITER_OK;
   }
 
-  // Host-driven rounds with events around each launch (profiling mode).
-  maiter_status host_loop(maiter_result* r, cudaStream_t st, cudaEvent_t* e,
-                          maiter_stats& s) const {
+  // Host-driven rounds with events around each launch (profiling mode), and
+  // optionally a trace record of sampled vertices after every push.
+  maiter_status host_loop(maiter_result* r, cudaStream_t st, cudaEvent_t* e, maiter_stats& s,
+                          TraceSink* trace = nullptr) const {
     for (;;) {
       MAITER_CUDA(cudaEventRecord(e[0], st));
       k_push<Op, kBlock><<<push_grid, kBlock, 0, st>>>(a);
       MAITER_CUDA(cudaEventRecord(e[1], st));
+      if (trace && trace->records < trace->max_records) {
+        const int64_t o = static_cast<int64_t>(trace->records) * trace->ns;
+        k_trace<Op><<<(trace->ns + 255) / 256, 256, 0, st>>>(
+            a, indeg, trace->sample, trace->ns, trace->feat + o * kMlpIn, trace->dl + o,
+            trace->vs + o, trace->la + o);
+        ++trace->records;
+      }
       launch_select(st);
       k_scan<Op, kBlock><<<scan_grid, kBlock, 0, st>>>(a, cudaGraphConditionalHandle{}, 0);
       MAITER_CUDA(cudaEventRecord(e[2], st));
@@ -364,22 +397,44 @@ struct RunPlan {
   Phase<OpMinU32> umin;
 };
 
+// In-degrees of a graph (computed once, kept with the graph).
+static maiter_status ensure_indegree(const maiter_graph* g) {
+  if (g->indeg) return MAITER_OK;
+  maiter_graph* mg = const_cast<maiter_graph*>(g);
+  MAITER_CUDA(cudaMalloc(&mg->indeg, sizeof(int) * (g->n > 0 ? g->n : 1)));
+  MAITER_CUDA(cudaMemset(mg->indeg, 0, sizeof(int) * (g->n > 0 ? g->n : 1)));
+  if (g->m > 0) k_indegree<<<g->num_sms * 4, 256>>>(g->col, g->m, mg->indeg);
+  MAITER_CUDA(cudaGetLastError());
+  MAITER_CUDA(cudaDeviceSynchronize());
+  return MAITER_OK;
+}
+
 static maiter_status setup_plan(const maiter_graph* g, const maiter_run_params* p,
-                                maiter_result* r, const Tuning& tu, RunPlan* plan) {
+                                maiter_result* r, const Tuning& tu, RunPlan* plan,
+                                bool track = false) {
   const void* coef = p->coef ? r->coef : nullptr;
-  const bool topq = p->sched == MAITER_SCHED_TOPFRAC;
+  const bool learned = p->sched == MAITER_SCHED_LEARNED;
+  const bool topq = p->sched == MAITER_SCHED_TOPFRAC || learned;
   if (topq && !r->topq) {
     MAITER_CUDA(cudaMalloc(&r->topq, sizeof(TopqCtl)));
     MAITER_CUDA(cudaMemset(r->topq, 0, sizeof(TopqCtl)));
   }
+  if (learned && !r->keys) MAITER_CUDA(cudaMalloc(&r->keys, sizeof(unsigned) * (g->n > 0 ? g->n : 1)));
+  if ((learned || track) && !r->last_act)
+    MAITER_CUDA(cudaMalloc(&r->last_act, sizeof(unsigned) * (g->n > 0 ? g->n : 1)));
+  if (learned || track) {
+    maiter_status s = ensure_indegree(g);
+    if (s != MAITER_OK) return s;
+  }
+  const MlpWeights* W = learned ? mlp_device_weights(p->scorer) : nullptr;
   switch (p->op) {
-    case MAITER_OP_SUM_F64: plan->f64.setup(g, r, r->delta, coef, p->damping, tu, topq); break;
+    case MAITER_OP_SUM_F64: plan->f64.setup(g, r, r->delta, coef, p->damping, tu, topq, W, track); break;
     case MAITER_OP_SUM_MIXED:
       plan->mixed = true;
-      plan->warm.setup(g, r, r->delta_wide, coef, p->damping, tu, topq);
-      plan->f32.setup(g, r, r->delta, coef, p->damping, tu, topq);
+      plan->warm.setup(g, r, r->delta_wide, coef, p->damping, tu, topq, W, track);
+      plan->f32.setup(g, r, r->delta, coef, p->damping, tu, topq, W, track);
       break;
-    default: plan->umin.setup(g, r, r->delta, nullptr, 0.0, tu, topq); break;
+    default: plan->umin.setup(g, r, r->delta, nullptr, 0.0, tu, topq, W, track); break;
   }
   return MAITER_OK;
 }
@@ -428,16 +483,18 @@ static maiter_status build_graph(const maiter_graph* g, maiter_result* r, int op
 }
 
 static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
-                              maiter_result* r, cudaStream_t st) {
+                              maiter_result* r, cudaStream_t st, TraceSink* trace = nullptr) {
   Tuning tu{};
   if (p->cut_warp > 0) tu.cut_warp = p->cut_warp;
   if (p->cut_cta > 0) tu.cut_cta = p->cut_cta;
   if (p->push_blocks_per_sm > 0) tu.push_blocks_per_sm = p->push_blocks_per_sm;
   RunPlan plan;
   {
-    maiter_status ps = setup_plan(g, p, r, tu, &plan);
+    maiter_status ps = setup_plan(g, p, r, tu, &plan, trace != nullptr);
     if (ps != MAITER_OK) return ps;
   }
+  if (r->last_act && (p->sched == MAITER_SCHED_LEARNED || trace))
+    MAITER_CUDA(cudaMemsetAsync(r->last_act, 0, sizeof(unsigned) * g->n, st));
   // The executable graph bakes in the kernel arguments; rebuild it only when
   // one of them changes.
   uint64_t key = 1469598103934665603ull;
@@ -449,9 +506,10 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   mix(dbits);
   mix(static_cast<uint64_t>(tu.cut_warp));
   mix(static_cast<uint64_t>(tu.cut_cta));
-  mix(p->sched == MAITER_SCHED_TOPFRAC ? 1 : 0);
+  mix(static_cast<uint64_t>(p->sched));
+  mix(static_cast<uint64_t>(reinterpret_cast<uintptr_t>(p->scorer)));
   mix(static_cast<uint64_t>(tu.push_blocks_per_sm));
-  const bool profile = (p->flags & MAITER_FLAG_PROFILE_KERNELS) != 0;
+  const bool profile = (p->flags & MAITER_FLAG_PROFILE_KERNELS) != 0 || trace != nullptr;
   if (!profile && (!r->exec || r->exec_key != key)) {
     maiter_status s = build_graph(g, r, p->op, plan);
     if (s != MAITER_OK) return s;
@@ -465,7 +523,7 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   c.max_rounds = p->max_rounds > 0 ? p->max_rounds : 1000000;
   c.sched = p->sched;
   *r->h_ctl = c;
-  if (r->topq && p->sched == MAITER_SCHED_TOPFRAC) {
+  if (r->topq && (p->sched == MAITER_SCHED_TOPFRAC || p->sched == MAITER_SCHED_LEARNED)) {
     // histograms and tickets start at zero; q for this run
     MAITER_CUDA(cudaMemsetAsync(r->topq, 0, sizeof(TopqCtl), st));
     MAITER_CUDA(cudaMemcpyAsync(&r->topq->frac, &p->top_frac, sizeof(double),
@@ -483,7 +541,7 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
     MAITER_CUDA(cudaEventRecord(r->ev0, st));
     maiter_status ls;
     if (p->op == MAITER_OP_SUM_F64) {
-      ls = plan.f64.host_loop(r, st, e, s);
+      ls = plan.f64.host_loop(r, st, e, s, trace);
     } else if (p->op == MAITER_OP_SUM_MIXED) {
       ls = plan.warm.host_loop(r, st, e, s);
       if (ls == MAITER_OK) {
@@ -496,7 +554,7 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
         if (r->h_ctl->status == 0) ls = plan.f32.host_loop(r, st, e, s);
       }
     } else {
-      ls = plan.umin.host_loop(r, st, e, s);
+      ls = plan.umin.host_loop(r, st, e, s, trace);
     }
     MAITER_CUDA(cudaEventRecord(r->ev1, st));
     MAITER_CUDA(cudaStreamSynchronize(st));
@@ -526,7 +584,9 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   s.converged = h.status == 1;
   // every phase that ran ends with one scan that did not continue
   const int64_t phases = 1 + (h.phase > 0 ? 1 : 0);
-  const int per_round = (p->sched == MAITER_SCHED_TOPFRAC) ? 5 : 2;   // + 3 radix passes
+  // + 3 radix passes (TOPFRAC), + the scorer (LEARNED)
+  const int per_round = (p->sched == MAITER_SCHED_TOPFRAC) ? 5
+                        : (p->sched == MAITER_SCHED_LEARNED) ? 6 : 2;
   s.kernel_launches +=
       per_round * (static_cast<int64_t>(h.rounds) + phases) + (plan.mixed ? 1 : 0);
   s.status = h.status == 1 ? MAITER_OK : MAITER_ERR_NOT_CONVERGED;
@@ -567,7 +627,7 @@ static maiter_status init_state(const maiter_graph* g, const maiter_run_params* 
 }
 
 static maiter_status run_op(const maiter_graph* g, const maiter_run_params* p, maiter_result* r,
-                            cudaStream_t st) {
+                            cudaStream_t st, TraceSink* trace = nullptr) {
   int init_launches = 0;
   maiter_status s;
   switch (p->op) {
@@ -592,22 +652,31 @@ static maiter_status run_op(const maiter_graph* g, const maiter_run_params* p, m
     r->stats.kernel_launches = init_launches;
     return MAITER_OK;
   }
-  s = (p->engine == MAITER_ENGINE_ASYNC) ? run_async(g, p, r, st) : run_sync(g, p, r, st);
+  s = (p->engine == MAITER_ENGINE_ASYNC) ? run_async(g, p, r, st) : run_sync(g, p, r, st, trace);
   r->stats.kernel_launches += init_launches;
   return s;
 }
 
 }  // namespace maiter
 
-extern "C" {
+namespace maiter {
 
-maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p, maiter_result** out) {
-  begin_call();
+static maiter_status run_impl(const maiter_graph* g, const maiter_run_params* p, maiter_result** out,
+                              TraceSink* trace) {
   MAITER_REQUIRE(g && p && out, "maiter_run: NULL argument");
   MAITER_REQUIRE(p->op >= MAITER_OP_SUM_F64 && p->op <= MAITER_OP_MIN_U32, "unknown op %d", p->op);
   const bool is_sum = p->op != MAITER_OP_MIN_U32;
-  MAITER_REQUIRE(p->sched >= MAITER_SCHED_ALL && p->sched <= MAITER_SCHED_TOPFRAC,
+  MAITER_REQUIRE(p->sched >= MAITER_SCHED_ALL && p->sched <= MAITER_SCHED_LEARNED,
                  "unknown sched %d", p->sched);
+  if (p->sched == MAITER_SCHED_LEARNED) {
+    MAITER_REQUIRE(p->scorer, "LEARNED scheduling needs params.scorer");
+    MAITER_REQUIRE(mlp_device(p->scorer) == g->device, "the scorer lives on another device");
+    if (p->engine != MAITER_ENGINE_SYNC) {
+      set_error("learned scheduling runs on the round engine");
+      return MAITER_ERR_UNSUPPORTED;
+    }
+    MAITER_REQUIRE(p->top_frac > 0.0 && p->top_frac <= 1.0, "top_frac must lie in (0, 1]");
+  }
   MAITER_REQUIRE(p->engine == MAITER_ENGINE_SYNC || p->engine == MAITER_ENGINE_ASYNC,
                  "unknown engine %d", p->engine);
   MAITER_REQUIRE(p->timeout_ms >= 0, "timeout_ms must be >= 0");
@@ -653,15 +722,76 @@ maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p, mait
     fresh = true;
   }
   cudaStream_t st = static_cast<cudaStream_t>(p->stream);
-  maiter_status s;
-  switch (p->op) {
-    default: s = run_op(g, p, r, st); break;
-  }
+  maiter_status s = run_op(g, p, r, st, trace);
   if (s == MAITER_OK || s == MAITER_ERR_NOT_CONVERGED || s == MAITER_ERR_TIMEOUT) {
     *out = r;
   } else if (fresh) {
     maiter_result_destroy(r);
   }
+  return s;
+}
+
+}  // namespace maiter
+
+extern "C" {
+
+maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p, maiter_result** out) {
+  begin_call();
+  return run_impl(g, p, out, nullptr);
+}
+
+maiter_status maiter_trace(const maiter_graph* g, const maiter_run_params* p,
+                           const int32_t* sample, int32_t num_sample, int32_t max_records,
+                           float* features, double* delta, double* v, uint32_t* last_update,
+                           int32_t* records, maiter_result** out) {
+  begin_call();
+  MAITER_REQUIRE(g && p && sample && features && delta && v && last_update && records && out,
+                 "maiter_trace: NULL argument");
+  MAITER_REQUIRE(num_sample > 0 && max_records > 0, "num_sample and max_records must be > 0");
+  MAITER_REQUIRE(p->op == MAITER_OP_SUM_F64 || p->op == MAITER_OP_MIN_U32,
+                 "traces are recorded for SUM_F64 and MIN_U32 runs");
+  MAITER_REQUIRE(p->engine == MAITER_ENGINE_SYNC && p->sched != MAITER_SCHED_LEARNED,
+                 "traces come from the round engine with a fixed schedule");
+  for (int i = 0; i < num_sample; ++i)
+    MAITER_REQUIRE(sample[i] >= 0 && sample[i] < g->n, "sample id out of range");
+  DeviceGuard guard(g->device);
+  const size_t rows = static_cast<size_t>(num_sample) * static_cast<size_t>(max_records);
+  TraceSink sink;
+  int* d_sample = nullptr;
+  cudaError_t e = cudaMalloc(&d_sample, sizeof(int) * num_sample);
+  if (e == cudaSuccess) e = cudaMalloc(&sink.feat, sizeof(float) * kMlpIn * rows);
+  if (e == cudaSuccess) e = cudaMalloc(&sink.dl, sizeof(double) * rows);
+  if (e == cudaSuccess) e = cudaMalloc(&sink.vs, sizeof(double) * rows);
+  if (e == cudaSuccess) e = cudaMalloc(&sink.la, sizeof(unsigned) * rows);
+  if (e == cudaSuccess) e = cudaMemcpy(d_sample, sample, sizeof(int) * num_sample, cudaMemcpyHostToDevice);
+  maiter_status s = MAITER_ERR_CUDA;
+  if (e == cudaSuccess) {
+    sink.sample = d_sample;
+    sink.ns = num_sample;
+    sink.max_records = max_records;
+    s = run_impl(g, p, out, &sink);
+    const size_t got = static_cast<size_t>(sink.records) * num_sample;
+    if (s == MAITER_OK || s == MAITER_ERR_NOT_CONVERGED) {
+      e = cudaMemcpy(features, sink.feat, sizeof(float) * kMlpIn * got, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(delta, sink.dl, sizeof(double) * got, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(v, sink.vs, sizeof(double) * got, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(last_update, sink.la, sizeof(unsigned) * got, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        set_error("trace copy failed: %s", cudaGetErrorString(e));
+        s = MAITER_ERR_CUDA;
+      }
+      *records = sink.records;
+    }
+  } else {
+    set_error("trace buffers: %s", cudaGetErrorString(e));
+    s = e == cudaErrorMemoryAllocation ? MAITER_ERR_OOM : MAITER_ERR_CUDA;
+  }
+  cudaFree(d_sample);
+  cudaFree(sink.feat);
+  cudaFree(sink.dl);
+  cudaFree(sink.vs);
+  cudaFree(sink.la);
   return s;
 }
 
