@@ -352,6 +352,96 @@ def run_batch_bench(args):
         print(json.dumps(line), flush=True)
 
 
+def run_learned_bench(args):
+    """Configuration 5: scorers trained on traces of scale-20 runs (PageRank
+    with d = 0.8, and SSSP), applied to PageRank at scale 24 and SSSP at scale
+    22 (edge factor 16); messages and time to the same tolerance against the
+    plain form (all pending vertices) and top-q by |Delta|."""
+    import torch
+    import paper_1710_05785_b300 as mt
+    from paper_1710_05785_b300 import learned
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+
+    def upload(g):
+        w = torch.from_numpy(g.w.view(np.int32)).to(dev) if g.w is not None else None
+        return mt.Graph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev), w,
+                        device=local)
+
+    q = 0.1
+    t0 = time.perf_counter()
+    gtp = graphgen.rmat(20, 16, seed=graphgen.DEFAULT_SEED_BASE + 5020)
+    Gtp = upload(gtp)
+    Xp, yp = learned.collect(mt, Gtp, gtp.row_ptr, mt.OP_SUM_F64, samples=8192, records=96,
+                             top_frac=q, eps=1e-8)
+    net_pr, loss_pr = learned.train(mt, Xp, yp, epochs=20, device=local)
+    gts = graphgen.rmat(20, 16, seed=graphgen.DEFAULT_SEED_BASE + 6020, weights=True)
+    Gts = upload(gts)
+    Xs, ys = learned.collect(mt, Gts, gts.row_ptr, mt.OP_MIN_U32, samples=8192, records=96,
+                             top_frac=q, source=int(graphgen.sssp_sources(gts, 1)[0]))
+    net_ss, loss_ss = learned.train(mt, Xs, ys, epochs=20, device=local)
+    train_s = time.perf_counter() - t0
+    del Gtp, Gts
+
+    def measure(G, reps, **kw):
+        r = mt.run(G, stream=stream, **kw)
+        best = None
+        for _ in range(reps):
+            r = mt.run(G, stream=stream, result=r, **kw)
+            st = r.stats()
+            best = st if best is None or st["elapsed_ms"] < best["elapsed_ms"] else best
+        r.close()
+        return {"time_to_tolerance_ms": best["elapsed_ms"], "edge_pushes": best["edge_pushes"],
+                "rounds": best["rounds"], "converged": best["converged"]}
+
+    gp = graphgen.rmat(24, 16)
+    Gp = upload(gp)
+    eps = 4e-8
+    pr = {
+        "plain_f64": measure(Gp, 2, op=mt.OP_SUM_F64, eps=eps),
+        "topq_f64": measure(Gp, 1, op=mt.OP_SUM_F64, eps=eps, sched=mt.SCHED_TOPFRAC, top_frac=q),
+        "learned_f64": measure(Gp, 2, op=mt.OP_SUM_F64, eps=eps, sched=mt.SCHED_LEARNED,
+                               top_frac=q, scorer=net_pr),
+        "mixed": measure(Gp, 2, op=mt.OP_SUM_MIXED, eps=eps),
+        "learned_mixed": measure(Gp, 2, op=mt.OP_SUM_MIXED, eps=eps, sched=mt.SCHED_LEARNED,
+                                 top_frac=q, scorer=net_pr),
+    }
+    del Gp
+    gs = graphgen.rmat(22, 16, weights=True)
+    Gs = upload(gs)
+    srcs = [int(s) for s in graphgen.sssp_sources(gs, 4)]
+    ss = {}
+    for name, kw in [("plain", {}), ("topq", dict(sched=mt.SCHED_TOPFRAC, top_frac=0.05)),
+                     ("learned", dict(sched=mt.SCHED_LEARNED, top_frac=0.05, scorer=net_ss))]:
+        tot = {"time_to_tolerance_ms": 0.0, "edge_pushes": 0, "rounds": 0}
+        for s in srcs:
+            m = measure(Gs, 1, op=mt.OP_MIN_U32, source=s, **kw)
+            for k in tot:
+                tot[k] += m[k]
+        ss[name] = tot
+    head = min(("learned_f64", "learned_mixed"), key=lambda k: pr[k]["time_to_tolerance_ms"])
+    ms = pr[head]["time_to_tolerance_ms"]
+    line = {
+        "metric": METRIC, "value": gp.m / (ms * 1e-3) / 1e9, "unit": "GTEPS",
+        "n_gpus": world, "steps": 2, "warmup": 1, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head == "learned_f64" else "f32/f64", "data": "synthetic",
+        "config": {"workload": "learned scheduling: scorers trained on R-MAT scale-20 traces; "
+                               "PageRank at scale 24 (eps 4e-8), SSSP at scale 22 (4 sources)",
+                   "top_frac": q, "headline": head},
+        "vs_plain_form": pr["plain_f64"]["time_to_tolerance_ms"] / ms,
+        "pagerank_scale24": pr, "sssp_scale22_4_sources": ss,
+        "training": {"seconds": train_s, "pagerank_examples": int(len(yp)),
+                     "pagerank_final_loss": loss_pr, "sssp_examples": int(len(ys)),
+                     "sssp_final_loss": loss_ss},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -361,7 +451,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--workload", default="sssp-rmat20",
-                    choices=["sssp-rmat20", "batch"] + sorted(PR_WORKLOADS),
+                    choices=["sssp-rmat20", "batch", "learned"] + sorted(PR_WORKLOADS),
                     help="sssp-rmat20 (default; configuration 2) or a PageRank configuration")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -372,6 +462,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch_bench(args)
+        return
+    if args.workload == "learned":
+        run_learned_bench(args)
         return
 
     import torch
