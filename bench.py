@@ -299,7 +299,8 @@ def run_batch_bench(args):
     G = [mt.Graph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev),
                   torch.from_numpy(g.w.view(np.int32)).to(dev), device=local) for g in graphs]
     tuned = autotune.tune_batch(mt, graphs, G, queries, cache=autotune.Cache(None), sample=48)
-    untuned = dict(cut_large=1024, chunk=1024, push_blocks_per_sm=0)
+    # the untuned arm: sparse (query, vertex) frontiers with default cut-offs
+    untuned = dict(mode=1, cut_large=1024, chunk=1024, push_blocks_per_sm=0)
     edges = float(sum(graphs[q["graph"]].m for q in queries))
     out = {}
     for name, cfg in [("tuned", tuned), ("default", untuned)]:
@@ -341,7 +342,8 @@ def run_batch_bench(args):
         "edge_pushes": st["edge_pushes"],
         "vs_untuned": out["default"]["ms"] / ms,
         "untuned_ms": out["default"]["ms"],
-        "roofline": {"bound": "hbm", "kernel": "k_b_push", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": "k_push" if tuned.get("mode", 0) == 0 else "k_b_push",
+                     "achieved": achieved,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                      "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
                      "push_launches": prof["push_launches"],

@@ -337,6 +337,13 @@ typedef struct maiter_batch_params {
   int32_t chunk;           /* edges per chunk (0 = 1024, else >= 32) */
   int32_t push_blocks_per_sm;  /* cap on resident push CTAs per SM (0 = occupancy) */
   int32_t flags;           /* MAITER_FLAG_PROFILE_KERNELS or 0 */
+  int32_t mode;            /* 0 = dense (default): every query is a round-engine
+                              run of its own - all pending vertices per round,
+                              exact termination sum |Delta| < eps_q - and one
+                              independent branch of the graph, so queries run
+                              side by side; 1 = sparse frontiers of (query,
+                              vertex) items as described above */
+  int32_t reserved;        /* must be 0 */
 } maiter_batch_params;
 
 void maiter_batch_params_default(maiter_batch_params* p);

@@ -327,7 +327,8 @@ class BatchParams(ctypes.Structure):
     """Mirror of ``maiter_batch_params``."""
     _fields_ = [("max_rounds", ctypes.c_int64), ("stream", ctypes.c_void_p),
                 ("cut_large", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("push_blocks_per_sm", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("push_blocks_per_sm", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Batch:
@@ -368,7 +369,7 @@ class Batch:
 
 
 def run_batch(graphs, queries, *, max_rounds: int = 1000000, stream=None, cut_large: int = 0,
-              chunk: int = 0, push_blocks_per_sm: int = 0, flags: int = 0,
+              chunk: int = 0, push_blocks_per_sm: int = 0, flags: int = 0, mode: int = 0,
               batch: Batch | None = None) -> Batch:
     """``maiter_run_batch``.  ``queries`` is a list of dicts with keys op
     (OP_SUM_F64 or OP_MIN_U32), graph (index), seeds (ids), and for PageRank
@@ -387,6 +388,7 @@ def run_batch(graphs, queries, *, max_rounds: int = 1000000, stream=None, cut_la
     lib().maiter_batch_params_default(ctypes.byref(p))
     p.max_rounds, p.stream = max_rounds, stream
     p.cut_large, p.chunk, p.push_blocks_per_sm, p.flags = cut_large, chunk, push_blocks_per_sm, flags
+    p.mode = mode
     h = ctypes.c_void_p(batch.handle.value if batch is not None else None)
     st = lib().maiter_run_batch(G, len(graphs), Q, len(queries), ctypes.byref(p), ctypes.byref(h))
     if batch is None and h.value:

@@ -22,6 +22,7 @@ RUN_SPACE = {
     "push_blocks_per_sm": [0, 4],
 }
 BATCH_SPACE = {
+    "mode": [0, 1],                 # dense per-query loops / sparse frontiers
     "cut_large": [256, 1024, 4096],
     "chunk": [512, 1024, 2048],
     "push_blocks_per_sm": [0, 4],
@@ -35,6 +36,9 @@ def candidates(space: dict) -> list[dict]:
     for values in itertools.product(*(space[k] for k in keys)):
         c = dict(zip(keys, values))
         if "cut_warp" in c and c["cut_warp"] > c["cut_cta"]:
+            continue
+        # the dense batch mode ignores the sparse mode's chunking parameters
+        if c.get("mode") == 0 and (c.get("cut_large") != 1024 or c.get("chunk") != 1024):
             continue
         out.append(c)
     return out
@@ -128,7 +132,7 @@ def tune_batch(mt, graph_csrs, G, queries, cache: Cache | None = None,
     batches = {}
 
     def measure(c):
-        k = (c["cut_large"], c["chunk"])
+        k = (c.get("mode", 0), c["cut_large"], c["chunk"])
         batches[k] = mt.run_batch(G, qs, batch=batches.get(k), **c)
         return batches[k].stats()["elapsed_ms"]
 

@@ -8,6 +8,7 @@
 
 #include "internal.h"
 #include "batch_kernels.cuh"
+#include "sync_phase.cuh"
 
 struct maiter_batch {
   int device = 0;
@@ -25,8 +26,8 @@ struct maiter_batch {
   uint32_t* v_min = nullptr;
   uint32_t* d_min = nullptr;
   unsigned* stamp = nullptr;
-  maiter::BItem* items[2][maiter::kBOps][2] = {};
-  unsigned cap[maiter::kBOps][2] = {};
+  maiter::BItem* items[2][maiter::kBOps] = {};
+  unsigned cap[maiter::kBOps] = {};
   maiter::BChunk* chunks = nullptr;
   unsigned chunk_cap = 0;
   unsigned* qlast = nullptr;
@@ -37,6 +38,13 @@ struct maiter_batch {
   cudaGraphExec_t exec = nullptr;
   int exec_grid = 0;
   int64_t n_sum = 0, n_min = 0;
+  // dense mode: one round-engine result per query, one WHILE branch each
+  int mode = 0;
+  std::vector<maiter_result*> qres;
+  std::vector<int> seed_off, seed_cnt;
+  int* d_qseeds = nullptr;
+  maiter::DevCtl* h_ctls = nullptr;      // pinned, one per query
+  int dense_grid_cap = 0;
   maiter_stats stats{};
 };
 
@@ -53,7 +61,144 @@ __global__ void k_count_large(const int* __restrict__ rp, int n, int cut, unsign
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// ------------------------------------------------------------- dense mode
+// Every query is its own round-engine run (k_push / k_scan on its own v,
+// Delta, frontier lists and control block) and one branch of a single CUDA
+// graph: init -> seeds -> WHILE(cond_q) { k_push ; k_scan }.  Branches share
+// nothing, so the GPU runs them concurrently, and each ends on its own exact
+// termination test (sum |Delta| < eps_q, or no pending vertex).
+
+template <class V, class D>
+__global__ void k_dense_init(V* __restrict__ v, D* __restrict__ d, int64_t n, V vfill, D dfill,
+                             DevCtl* ctl, DevCtl init) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    v[i] = vfill;
+    d[i] = dfill;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ctl = init;
+}
+
+template <class D>
+__global__ void k_dense_seed(D* __restrict__ d, const int* __restrict__ seeds, int ns, D value) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ns) d[seeds[i]] = value;
+}
+
+static void free_dense(maiter_batch* b) {
+  for (maiter_result* r : b->qres) maiter_result_destroy(r);
+  b->qres.clear();
+  cudaFree(b->d_qseeds);
+  b->d_qseeds = nullptr;
+  if (b->h_ctls) cudaFreeHost(b->h_ctls);
+  b->h_ctls = nullptr;
+}
+
+static maiter_status dense_setup(maiter_batch* b, const maiter_query* qs) {
+  const int nq = b->nq;
+  b->qres.assign(nq, nullptr);
+  b->seed_off.assign(nq, 0);
+  b->seed_cnt.assign(nq, 0);
+  std::vector<int> flat;
+  for (int q = 0; q < nq; ++q) {
+    const maiter_graph* g = b->graphs[qs[q].graph];
+    maiter_status s = alloc_result(g, qs[q].op, &b->qres[q]);
+    if (s != MAITER_OK) return s;
+    b->seed_off[q] = static_cast<int>(flat.size());
+    b->seed_cnt[q] = qs[q].num_seeds;
+    flat.insert(flat.end(), qs[q].seeds, qs[q].seeds + qs[q].num_seeds);
+  }
+  MAITER_CUDA(cudaMalloc(&b->d_qseeds, sizeof(int) * (flat.empty() ? 1 : flat.size())));
+  MAITER_CUDA(cudaMemcpy(b->d_qseeds, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice));
+  MAITER_CUDA(cudaMallocHost(&b->h_ctls, sizeof(DevCtl) * nq));
+  MAITER_CUDA(cudaEventCreate(&b->ev0));
+  MAITER_CUDA(cudaEventCreate(&b->ev1));
+  return MAITER_OK;
+}
+
+template <class Op>
+static Phase<Op> dense_phase(const maiter_batch* b, int q, const maiter_batch_params* p) {
+  const BQuery& Q = b->hq[q];
+  const maiter_graph* g = b->graphs[Q.graph];
+  Tuning tu{};
+  if (p->push_blocks_per_sm > 0) tu.push_blocks_per_sm = p->push_blocks_per_sm;
+  Phase<Op> ph;
+  maiter_result* r = b->qres[q];
+  ph.setup(g, r, r->delta, nullptr, Q.damping, tu, false);
+  // small graphs get small grids, so many queries run side by side
+  const int want = static_cast<int>(std::min<int64_t>(std::max<int64_t>(g->m / 4096, 32), 1 << 30));
+  if (want < ph.push_grid) ph.push_grid = want;
+  return ph;
+}
+
+template <class V, class D>
+static maiter_status dense_add_init(cudaGraph_t graph, const maiter_batch* b, int q, V vfill,
+                                    D dfill, D seedval, const DevCtl& init, cudaGraphNode_t* last) {
+  maiter_result* r = b->qres[q];
+  const maiter_graph* g = b->graphs[b->hq[q].graph];
+  V* v = static_cast<V*>(r->v);
+  D* d = static_cast<D*>(r->delta);
+  int64_t n = g->n;
+  DevCtl* ctl = r->ctl;
+  DevCtl ci = init;
+  void* a1[] = {&v, &d, &n, &vfill, &dfill, &ctl, &ci};
+  cudaKernelNodeParams k1{};
+  k1.func = reinterpret_cast<void*>(&k_dense_init<V, D>);
+  k1.gridDim = dim3(static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, g->num_sms * 2))));
+  k1.blockDim = dim3(256);
+  k1.kernelParams = a1;
+  cudaGraphNode_t n1, n2;
+  MAITER_CUDA(cudaGraphAddKernelNode(&n1, graph, nullptr, 0, &k1));
+  const int* seeds = b->d_qseeds + b->seed_off[q];
+  int ns = b->seed_cnt[q];
+  D sv = seedval;
+  void* a2[] = {&d, &seeds, &ns, &sv};
+  cudaKernelNodeParams k2{};
+  k2.func = reinterpret_cast<void*>(&k_dense_seed<D>);
+  k2.gridDim = dim3((ns + 255) / 256);
+  k2.blockDim = dim3(256);
+  k2.kernelParams = a2;
+  MAITER_CUDA(cudaGraphAddKernelNode(&n2, graph, &n1, 1, &k2));
+  *last = n2;
+  return MAITER_OK;
+}
+
+static DevCtl dense_ctl(const BQuery& Q, const maiter_batch_params* p, double eps) {
+  DevCtl c{};
+  c.eps = Q.op == 0 ? eps : 0.0;
+  c.eps_eff = c.eps;
+  c.max_rounds = p->max_rounds > 0 ? p->max_rounds : 1000000;
+  c.sched = MAITER_SCHED_ALL;
+  return c;
+}
+
+static maiter_status dense_build(maiter_batch* b, const maiter_batch_params* p,
+                                 const std::vector<double>& eps) {
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  MAITER_CUDA(cudaGraphCreate(&b->graph, 0));
+  for (int q = 0; q < b->nq; ++q) {
+    const BQuery& Q = b->hq[q];
+    const DevCtl init = dense_ctl(Q, p, eps[q]);
+    cudaGraphNode_t last, wnode;
+    cudaGraphConditionalHandle h;
+    MAITER_CUDA(cudaGraphConditionalHandleCreate(&h, b->graph, 1, cudaGraphCondAssignDefault));
+    maiter_status s;
+    if (Q.op == 0) {
+      s = dense_add_init<double, double>(b->graph, b, q, 0.0, 0.0, Q.init, init, &last);
+      if (s == MAITER_OK) s = dense_phase<OpSumF64>(b, q, p).add_to(b->graph, &last, 1, h, &wnode);
+    } else {
+      s = dense_add_init<uint32_t, uint32_t>(b->graph, b, q, kInfU32, kInfU32, 0u, init, &last);
+      if (s == MAITER_OK) s = dense_phase<OpMinU32>(b, q, p).add_to(b->graph, &last, 1, h, &wnode);
+    }
+    if (s != MAITER_OK) return s;
+  }
+  MAITER_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return MAITER_OK;
+}
+
 static void free_batch_buffers(maiter_batch* b) {
+  free_dense(b);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
@@ -67,8 +212,7 @@ static void free_batch_buffers(maiter_batch* b) {
   cudaFree(b->d_min);
   cudaFree(b->stamp);
   for (auto& s : b->items)
-    for (auto& o : s)
-      for (auto& l : o) { cudaFree(l); l = nullptr; }
+    for (auto& o : s) { cudaFree(o); o = nullptr; }
   cudaFree(b->chunks);
   cudaFree(b->qlast);
   cudaFree(b->ctl);
@@ -91,10 +235,8 @@ static BArgs batch_args(const maiter_batch* b) {
   a.d_min = b->d_min;
   a.stamp = b->stamp;
   for (int s = 0; s < 2; ++s)
-    for (int o = 0; o < kBOps; ++o)
-      for (int l = 0; l < 2; ++l) a.items[s][o][l] = b->items[s][o][l];
-  for (int o = 0; o < kBOps; ++o)
-    for (int l = 0; l < 2; ++l) a.cap[o][l] = b->cap[o][l];
+    for (int o = 0; o < kBOps; ++o) a.items[s][o] = b->items[s][o];
+  for (int o = 0; o < kBOps; ++o) a.cap[o] = b->cap[o];
   a.chunks = b->chunks;
   a.chunk_cap = b->chunk_cap;
   a.qlast = b->qlast;
@@ -110,6 +252,7 @@ static maiter_status batch_setup(maiter_batch* b, const maiter_graph* const* gra
   b->device = graphs[0]->device;
   b->ng = ng;
   b->nq = nq;
+  b->mode = p->mode;
   b->graphs.assign(graphs, graphs + ng);
   b->cut_large = p->cut_large > 0 ? p->cut_large : 1024;
   b->chunk = p->chunk > 0 ? p->chunk : 1024;
@@ -137,6 +280,7 @@ static maiter_status batch_setup(maiter_batch* b, const maiter_graph* const* gra
   }
   b->n_sum = off[0];
   b->n_min = off[1];
+  if (b->mode == 0) return dense_setup(b, qs);
   // large-vertex counts per graph at this cut-off
   std::vector<unsigned> nlarge(ng, 0);
   {
@@ -158,11 +302,10 @@ static maiter_status batch_setup(maiter_batch* b, const maiter_graph* const* gra
   for (int o = 0; o < kBOps; ++o) {
     const int64_t n_op = o == 0 ? off[0] : off[1];
     const int64_t mult = o == 0 ? 2 : 1;
-    const int64_t c0 = n_op * mult + 1024, c1 = large_op[o] * mult + 64;
-    MAITER_REQUIRE(c0 < (int64_t(1) << 32) && c1 < (int64_t(1) << 32),
+    const int64_t c0 = n_op * mult + 1024;
+    MAITER_REQUIRE(c0 < (int64_t(1) << 32),
                    "batch too large: %lld (query, vertex) states", (long long)n_op);
-    b->cap[o][0] = static_cast<unsigned>(c0);
-    b->cap[o][1] = static_cast<unsigned>(c1);
+    b->cap[o] = static_cast<unsigned>(c0);
   }
   const int64_t ccap = (large_op[0] * 2 + large_op[1]) + (m_op[0] * 2 + m_op[1]) / b->chunk + 64;
   MAITER_REQUIRE(ccap < (int64_t(1) << 32), "batch too large for the chunk list");
@@ -185,8 +328,7 @@ static maiter_status batch_setup(maiter_batch* b, const maiter_graph* const* gra
   A(reinterpret_cast<void**>(&b->stamp), sizeof(unsigned) * b->n_min);
   for (int s = 0; s < 2; ++s)
     for (int o = 0; o < kBOps; ++o)
-      for (int l = 0; l < 2; ++l)
-        A(reinterpret_cast<void**>(&b->items[s][o][l]), sizeof(BItem) * b->cap[o][l]);
+      A(reinterpret_cast<void**>(&b->items[s][o]), sizeof(BItem) * b->cap[o]);
   A(reinterpret_cast<void**>(&b->chunks), sizeof(BChunk) * b->chunk_cap);
   A(reinterpret_cast<void**>(&b->qlast), sizeof(unsigned) * nq);
   A(reinterpret_cast<void**>(&b->ctl), sizeof(BCtl));
@@ -244,6 +386,96 @@ static maiter_status batch_build_graph(maiter_batch* b, int grid) {
   MAITER_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
   b->exec_grid = grid;
   return MAITER_OK;
+}
+
+// Dense mode: rebuild the graph when the queries' parameters change, launch
+// it once, then read every query's control block.
+static maiter_status dense_run(maiter_batch* b, const maiter_batch_params* p,
+                               const maiter_query* qs) {
+  cudaStream_t st = static_cast<cudaStream_t>(p->stream);
+  std::vector<double> eps(b->nq);
+  uint64_t sig = 1469598103934665603ull;
+  auto mix = [&](uint64_t x) { sig = (sig ^ x) * 1099511628211ull; };
+  for (int q = 0; q < b->nq; ++q) {
+    eps[q] = qs[q].eps;
+    uint64_t bits;
+    std::memcpy(&bits, &qs[q].eps, 8);
+    mix(bits);
+    std::memcpy(&bits, &qs[q].damping, 8);
+    mix(bits);
+    for (int s = 0; s < qs[q].num_seeds; ++s) mix(static_cast<uint64_t>(qs[q].seeds[s]));
+  }
+  mix(static_cast<uint64_t>(p->max_rounds));
+  mix(static_cast<uint64_t>(p->push_blocks_per_sm));
+  const bool profile = (p->flags & MAITER_FLAG_PROFILE_KERNELS) != 0;
+  if (!profile && (!b->exec || b->exec_grid != static_cast<int>(sig & 0x7fffffff))) {
+    maiter_status s = dense_build(b, p, eps);
+    if (s != MAITER_OK) return s;
+    b->exec_grid = static_cast<int>(sig & 0x7fffffff);
+  }
+  maiter_stats& s = b->stats;
+  s = maiter_stats{};
+  MAITER_CUDA(cudaEventRecord(b->ev0, st));
+  if (profile) {
+    // queries one after another, each host-driven with events per kernel
+    cudaEvent_t e[3];
+    for (auto& x : e) MAITER_CUDA(cudaEventCreate(&x));
+    for (int q = 0; q < b->nq; ++q) {
+      const BQuery& Q = b->hq[q];
+      maiter_result* r = b->qres[q];
+      const maiter_graph* g = b->graphs[Q.graph];
+      const DevCtl init = dense_ctl(Q, p, eps[q]);
+      const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((g->n + 255) / 256, g->num_sms * 2)));
+      const int ns = b->seed_cnt[q];
+      if (Q.op == 0) {
+        k_dense_init<double, double><<<grid, 256, 0, st>>>(static_cast<double*>(r->v),
+            static_cast<double*>(r->delta), g->n, 0.0, 0.0, r->ctl, init);
+        k_dense_seed<double><<<(ns + 255) / 256, 256, 0, st>>>(static_cast<double*>(r->delta),
+            b->d_qseeds + b->seed_off[q], ns, Q.init);
+        maiter_status ls = dense_phase<OpSumF64>(b, q, p).host_loop(r, st, e, s);
+        if (ls != MAITER_OK) return ls;
+      } else {
+        k_dense_init<uint32_t, uint32_t><<<grid, 256, 0, st>>>(static_cast<uint32_t*>(r->v),
+            static_cast<uint32_t*>(r->delta), g->n, kInfU32, kInfU32, r->ctl, init);
+        k_dense_seed<uint32_t><<<(ns + 255) / 256, 256, 0, st>>>(static_cast<uint32_t*>(r->delta),
+            b->d_qseeds + b->seed_off[q], ns, 0u);
+        maiter_status ls = dense_phase<OpMinU32>(b, q, p).host_loop(r, st, e, s);
+        if (ls != MAITER_OK) return ls;
+      }
+    }
+    for (auto& x : e) cudaEventDestroy(x);
+  } else {
+    MAITER_CUDA(cudaGraphLaunch(b->exec, st));
+  }
+  MAITER_CUDA(cudaEventRecord(b->ev1, st));
+  for (int q = 0; q < b->nq; ++q)
+    MAITER_CUDA(cudaMemcpyAsync(b->h_ctls + q, b->qres[q]->ctl, sizeof(DevCtl),
+                                cudaMemcpyDeviceToHost, st));
+  MAITER_CUDA(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+  s.elapsed_ms = ms;
+  int worst = 1;
+  for (int q = 0; q < b->nq; ++q) {
+    const DevCtl& h = b->h_ctls[q];
+    s.rounds = std::max<int64_t>(s.rounds, static_cast<int64_t>(h.rounds));
+    s.activations += static_cast<int64_t>(h.activations);
+    s.edge_pushes += static_cast<int64_t>(h.pushes);
+    s.residual = std::max(s.residual, h.residual);
+    s.kernel_launches += 2 + 2 * (static_cast<int64_t>(h.rounds) + 1);
+    if (h.status != 1) worst = h.status;
+  }
+  s.converged = worst == 1;
+  if (worst == 1) {
+    s.status = MAITER_OK;
+  } else if (worst == 2) {
+    s.status = MAITER_ERR_NOT_CONVERGED;
+    set_error("round cap reached before every query converged");
+  } else {
+    s.status = MAITER_ERR_OOM;
+    set_error("a frontier outgrew its capacity");
+  }
+  return static_cast<maiter_status>(s.status);
 }
 
 static maiter_status batch_run(maiter_batch* b, const maiter_batch_params* p) {
@@ -363,6 +595,7 @@ maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_gr
   MAITER_REQUIRE(p->cut_large >= 0 && p->chunk >= 0 && (p->chunk == 0 || p->chunk >= 32),
                  "cut_large >= 0 and chunk = 0 or >= 32");
   MAITER_REQUIRE((p->flags & ~MAITER_FLAG_PROFILE_KERNELS) == 0, "unknown flags 0x%x", p->flags);
+  MAITER_REQUIRE((p->mode == 0 || p->mode == 1) && p->reserved == 0, "mode must be 0 or 1");
   for (int q = 0; q < num_queries; ++q) {
     const maiter_query& Q = queries[q];
     MAITER_REQUIRE(Q.graph >= 0 && Q.graph < num_graphs, "query %d: graph %d out of range", q, Q.graph);
@@ -384,7 +617,7 @@ maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_gr
   maiter_batch* b = *out;
   bool fresh = false;
   // Reuse when the batch has the same shape; rebuild otherwise.
-  bool same = b && b->nq == num_queries && b->ng == num_graphs &&
+  bool same = b && b->nq == num_queries && b->ng == num_graphs && b->mode == p->mode &&
               b->cut_large == (p->cut_large > 0 ? p->cut_large : 1024) &&
               b->chunk == (p->chunk > 0 ? p->chunk : 1024);
   if (same) {
@@ -392,6 +625,7 @@ maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_gr
     for (int q = 0; q < num_queries && same; ++q) {
       const maiter_query& Q = queries[q];
       same = b->hq[q].graph == Q.graph && b->hq[q].op == (Q.op == MAITER_OP_MIN_U32 ? 1 : 0);
+      if (same && b->mode == 0) same = b->seed_cnt[q] == Q.num_seeds;
     }
   }
   if (!same) {
@@ -407,6 +641,17 @@ maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_gr
       if (fresh) maiter_batch_destroy(b);
       return s;
     }
+  } else if (b->mode == 0) {
+    // dense, same shape: refresh damping / seed values and the seed ids
+    std::vector<int> flat;
+    for (int q = 0; q < num_queries; ++q) {
+      const maiter_query& Q = queries[q];
+      BQuery& bq = b->hq[q];
+      bq.damping = Q.damping;
+      bq.init = bq.op == 0 ? (1.0 - Q.damping) / static_cast<double>(Q.num_seeds) : 0.0;
+      flat.insert(flat.end(), Q.seeds, Q.seeds + Q.num_seeds);
+    }
+    MAITER_CUDA(cudaMemcpy(b->d_qseeds, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice));
   } else {
     // same shape: refresh thresholds, seeds and damping
     b->hseeds.clear();
@@ -427,7 +672,7 @@ maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_gr
     MAITER_CUDA(cudaMemcpy(b->d_queries, b->hq.data(), sizeof(BQuery) * num_queries,
                            cudaMemcpyHostToDevice));
   }
-  maiter_status s = batch_run(b, p);
+  maiter_status s = b->mode == 0 ? dense_run(b, p, queries) : batch_run(b, p);
   if (s == MAITER_OK || s == MAITER_ERR_NOT_CONVERGED) {
     *out = b;
   } else if (fresh) {
@@ -444,10 +689,13 @@ maiter_status maiter_batch_get_state(const maiter_batch* b, int32_t query, void*
                  (long long)count, (long long)b->qn[query]);
   DeviceGuard guard(b->device);
   const BQuery& q = b->hq[query];
-  if (q.op == 0)
-    MAITER_CUDA(cudaMemcpy(out, b->v_sum + q.off, sizeof(double) * count, cudaMemcpyDefault));
+  const size_t bytes = (q.op == 0 ? sizeof(double) : sizeof(uint32_t)) * count;
+  if (b->mode == 0)
+    MAITER_CUDA(cudaMemcpy(out, b->qres[query]->v, bytes, cudaMemcpyDefault));
+  else if (q.op == 0)
+    MAITER_CUDA(cudaMemcpy(out, b->v_sum + q.off, bytes, cudaMemcpyDefault));
   else
-    MAITER_CUDA(cudaMemcpy(out, b->v_min + q.off, sizeof(uint32_t) * count, cudaMemcpyDefault));
+    MAITER_CUDA(cudaMemcpy(out, b->v_min + q.off, bytes, cudaMemcpyDefault));
   return MAITER_OK;
 }
 
@@ -462,6 +710,11 @@ maiter_status maiter_batch_query_rounds(const maiter_batch* b, int32_t* out, int
   set_error("%s", "");
   MAITER_REQUIRE(b && out && count == b->nq, "need num_queries entries");
   DeviceGuard guard(b->device);
+  if (b->mode == 0) {
+    // dense: the rounds each query's own loop ran (its control block)
+    for (int q = 0; q < count; ++q) out[q] = static_cast<int32_t>(b->h_ctls[q].rounds);
+    return MAITER_OK;
+  }
   MAITER_CUDA(cudaMemcpy(out, b->qlast, sizeof(int32_t) * count, cudaMemcpyDeviceToHost));
   return MAITER_OK;
 }

@@ -3,14 +3,17 @@
 //
 // The unit of work is an item (query, vertex).  Each query owns its own v and
 // Delta arrays (query-major layout, one slice per query).  A round:
-//   k_b_take - for every item of a high-degree vertex: the update of Eq. 5
-//              (take Delta, fold into v, form the message) and its expansion
-//              into chunks of kBChunk edges;
+//   k_b_take - walks the current frontier once: every item of a vertex with at
+//              least cut_large out-edges gets the update of Eq. 5 (take Delta,
+//              fold into v, form the message), is split into chunks of `chunk`
+//              edges for separate CTAs, and is marked done in the list;
 //   k_b_push - the scatter of every item: chunks one CTA each, other items
-//              warp-gathered 32 at a time.  A receiver whose delta crosses its
-//              query's threshold (sum) or whose distance improves (min) is
-//              appended to the next round's frontier, so frontiers stay sparse:
-//              a query touches only the vertices its messages reach.
+//              warp-gathered 32 at a time (the query's and graph's fields are
+//              loaded once per item and shuffled to the lanes of its edges).
+//              A receiver whose delta crosses its query's threshold (sum) or
+//              whose distance improves (min) is appended to the next round's
+//              frontier, so frontiers stay sparse: a query touches only the
+//              vertices its messages reach.
 // The push kernel's last block swaps the frontiers and sets the graph's WHILE
 // condition; the loop ends when no query has an item left.
 //
@@ -46,19 +49,19 @@ struct BQuery {
 
 struct BItem {
   unsigned int q;
-  int u;
+  int u;                          // -1: handled by the chunk path this round
 };
 
 struct BChunk {
   unsigned int q;
   int u;
   int chunk;
-  int pad;
+  int op;
   double msg;                     // sum: message; min: the taken distance (as double)
 };
 
 struct BCtl {
-  unsigned int cnt[2][kBOps][2];  // [set][op][0 general, 1 large]
+  unsigned int cnt[2][kBOps];     // [set][op] frontier sizes
   unsigned int nchunks;           // chunk entries of the current round
   unsigned int rset, wset;        // set the push reads / appends to
   unsigned int ticket;
@@ -76,8 +79,8 @@ struct BArgs {
   uint32_t* v_min;
   uint32_t* d_min;
   unsigned int* stamp;            // min states: round stamp of the last append
-  BItem* items[2][kBOps][2];      // [set][op][general / large]
-  unsigned int cap[kBOps][2];
+  BItem* items[2][kBOps];         // [set][op]
+  unsigned int cap[kBOps];
   BChunk* chunks;
   unsigned int chunk_cap;
   unsigned int* qlast;            // per query: last round it had items
@@ -86,41 +89,34 @@ struct BArgs {
   int chunk;                      // edges per chunk
 };
 
-// Appends the lanes with `want` to the next frontier of op `op`, sorted into
-// general / large by the receiver's out-degree (one atomic per list per warp).
+// Appends the lanes with `want` to the next frontier of op `op` (one atomic
+// per warp).
 __device__ __forceinline__ void b_append(const BArgs& a, unsigned ws, int op, bool want,
-                                         unsigned q, int k, int deg_k, int lane) {
-  const bool big = deg_k >= a.cut_large;
-#pragma unroll
-  for (int l = 0; l < 2; ++l) {
-    const bool mine = want && (big == (l == 1));
-    const unsigned mask = __ballot_sync(0xffffffffu, mine);
-    if (!mask) continue;
-    const int leader = __ffs(mask) - 1;
-    unsigned pos = 0;
-    if (lane == leader) pos = atomicAdd(&a.ctl->cnt[ws][op][l], static_cast<unsigned>(__popc(mask)));
-    pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(mask & ((1u << lane) - 1u));
-    if (mine) {
-      if (pos < a.cap[op][l]) a.items[ws][op][l][pos] = BItem{q, k};
-      else atomicOr(&a.ctl->overflow, 1u);
-    }
+                                         unsigned q, int k, int lane) {
+  const unsigned mask = __ballot_sync(0xffffffffu, want);
+  if (!mask) return;
+  const int leader = __ffs(mask) - 1;
+  unsigned pos = 0;
+  if (lane == leader) pos = atomicAdd(&a.ctl->cnt[ws][op], static_cast<unsigned>(__popc(mask)));
+  pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(mask & ((1u << lane) - 1u));
+  if (want) {
+    if (pos < a.cap[op]) a.items[ws][op][pos] = BItem{q, k};
+    else atomicOr(&a.ctl->overflow, 1u);
   }
 }
 
-// One message over one edge; decides whether the receiver joins the next
-// frontier.
-__device__ __forceinline__ bool b_apply_sum(const BArgs& a, const BQuery& Q, int k, double m) {
-  double* dk = a.d_sum + Q.off + k;
-  const double old = atomicAdd(dk, m);
-  return fabs(old) <= Q.tau && fabs(old + m) > Q.tau;
+// One message over one edge; true if the receiver joins the next frontier.
+__device__ __forceinline__ bool b_apply_sum(double* d_slice, double tau, int k, double m) {
+  const double old = atomicAdd(d_slice + k, m);
+  return fabs(old) <= tau && fabs(old + m) > tau;
 }
-__device__ __forceinline__ bool b_apply_min(const BArgs& a, const BQuery& Q, int k, uint32_t nd,
+__device__ __forceinline__ bool b_apply_min(uint32_t* d_slice, const uint32_t* v_slice,
+                                            unsigned* st_slice, int k, uint32_t nd,
                                             unsigned round_stamp) {
-  uint32_t* dk = a.d_min + Q.off + k;
-  if (!(nd < __ldcg(dk))) return false;
-  const uint32_t old = atomicMin(dk, nd);
-  if (!(nd < old) || !(nd < __ldcg(a.v_min + Q.off + k))) return false;
-  return atomicExch(a.stamp + Q.off + k, round_stamp) != round_stamp;
+  if (!(nd < __ldcg(d_slice + k))) return false;
+  const uint32_t old = atomicMin(d_slice + k, nd);
+  if (!(nd < old) || !(nd < __ldcg(v_slice + k))) return false;
+  return atomicExch(st_slice + k, round_stamp) != round_stamp;
 }
 
 // Update of one item (fold + message).  Returns false if there is nothing to send.
@@ -143,22 +139,26 @@ __device__ __forceinline__ bool b_fold(const BArgs& a, int op, const BQuery& Q, 
   return deg > 0;
 }
 
-// High-degree items: update once, expand into chunks (count in ctl->nchunks).
+// Items of high-degree vertices: update once, expand into chunks, mark done.
 template <int BLOCK>
 static __global__ void __launch_bounds__(BLOCK) k_b_take(BArgs a) {
   BCtl* ctl = a.ctl;
   const unsigned rs = ctl->rset;
+  unsigned long long ups = 0;
   for (int op = 0; op < kBOps; ++op) {
-    const unsigned n = min(ctl->cnt[rs][op][1], a.cap[op][1]);
+    const unsigned n = min(ctl->cnt[rs][op], a.cap[op]);
+    BItem* list = a.items[rs][op];
     for (unsigned i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
-      const BItem it = a.items[rs][op][1][i];
+      const BItem it = list[i];
       const BQuery Q = a.queries[it.q];
-      const BGraph G = a.graphs[Q.graph];
-      const int rb = __ldg(G.rp + it.u), deg = __ldg(G.rp + it.u + 1) - rb;
+      const int* rp = a.graphs[Q.graph].rp;
+      const int rb = __ldg(rp + it.u), deg = __ldg(rp + it.u + 1) - rb;
+      if (deg < a.cut_large) continue;
+      list[i].u = -1;
       double ms = 0.0;
       uint32_t mm = 0;
       if (!b_fold(a, op, Q, it.u, deg, &ms, &mm)) continue;
-      atomicAdd(&ctl->updates, 1ull);
+      ++ups;
       const int nc = (deg + a.chunk - 1) / a.chunk;
       const unsigned p0 = atomicAdd(&ctl->nchunks, static_cast<unsigned>(nc));
       if (p0 + static_cast<unsigned>(nc) > a.chunk_cap) {
@@ -169,11 +169,109 @@ static __global__ void __launch_bounds__(BLOCK) k_b_take(BArgs a) {
         a.chunks[p0 + c] = BChunk{it.q, it.u, c, op, op == 0 ? ms : static_cast<double>(mm)};
     }
   }
+  for (int o = 16; o > 0; o >>= 1) ups += __shfl_xor_sync(0xffffffffu, ups, o);
+  if ((threadIdx.x & 31) == 0 && ups) atomicAdd(&ctl->updates, ups);
+}
+
+__device__ __forceinline__ unsigned long long shfl64(unsigned long long x, int src) {
+  return __shfl_sync(0xffffffffu, x, src);
+}
+
+// Warp-gathered scatter of the general items of one op (OP 0 sum, 1 min).
+template <int OP>
+__device__ __forceinline__ void b_push_items(const BArgs& a, unsigned rs, unsigned ws,
+                                             unsigned stamp, int warp, int nwarps, int lane,
+                                             unsigned long long* my_up,
+                                             unsigned long long* my_push) {
+  const int n = static_cast<int>(min(a.ctl->cnt[rs][OP], a.cap[OP]));
+  const BItem* list = a.items[rs][OP];
+  for (int base = warp * 32; base < n; base += nwarps * 32) {
+    const int i = base + lane;
+    unsigned q = 0;
+    int beg = 0, deg = 0;
+    double ms = 0.0, tau = 0.0;
+    uint32_t mm = 0;
+    unsigned long long off = 0, colp = 0, wp = 0;
+    if (i < n) {
+      const BItem it = list[i];
+      if (it.u >= 0) {
+        q = it.q;
+        const BQuery Q = a.queries[q];
+        const BGraph G = a.graphs[Q.graph];
+        beg = __ldg(G.rp + it.u);
+        deg = __ldg(G.rp + it.u + 1) - beg;
+        off = static_cast<unsigned long long>(Q.off);
+        tau = Q.tau;
+        colp = reinterpret_cast<unsigned long long>(G.col);
+        wp = reinterpret_cast<unsigned long long>(G.w);
+        if (b_fold(a, OP, Q, it.u, deg, &ms, &mm)) ++*my_up;
+        else deg = 0;
+      }
+    }
+    int incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - deg;
+    *my_push += static_cast<unsigned long long>(deg);
+    for (int t0 = 0; t0 < total; t0 += 64) {
+      // two edge steps in flight: owners, fields and edge loads first
+      int k[2];
+      uint32_t wk[2];
+      int own[2];
+      bool ok[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int t = t0 + u * 32 + lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int probe = __shfl_sync(0xffffffffu, incl, owner + step - 1);
+          if (probe <= t) owner += step;
+        }
+        own[u] = owner;
+        ok[u] = t < total;
+        const int ob = __shfl_sync(0xffffffffu, beg, owner);
+        const int oe = __shfl_sync(0xffffffffu, excl, owner);
+        const int* col = reinterpret_cast<const int*>(shfl64(colp, owner));
+        const int e = ob + (t - oe);
+        k[u] = ok[u] ? __ldcs(col + e) : 0;
+        if (OP == 1) {
+          const uint32_t* w = reinterpret_cast<const uint32_t*>(shfl64(wp, owner));
+          wk[u] = ok[u] ? __ldcs(w + e) : 0u;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int owner = own[u];
+        const unsigned oq = __shfl_sync(0xffffffffu, q, owner);
+        const unsigned long long ooff = shfl64(off, owner);
+        bool want = false;
+        if (OP == 0) {
+          const double oms = __shfl_sync(0xffffffffu, ms, owner);
+          const double otau = __shfl_sync(0xffffffffu, tau, owner);
+          if (ok[u]) want = b_apply_sum(a.d_sum + ooff, otau, k[u], oms);
+        } else {
+          const uint32_t omm = __shfl_sync(0xffffffffu, mm, owner);
+          if (ok[u]) {
+            const uint32_t s = omm + wk[u];
+            want = b_apply_min(a.d_min + ooff, a.v_min + ooff, a.stamp + ooff, k[u],
+                               s < omm ? kInfU32 : s, stamp);
+          }
+        }
+        if (want) atomicMax(a.qlast + oq, stamp);
+        b_append(a, ws, OP, want, oq, k[u], lane);
+      }
+    }
+  }
 }
 
 template <int BLOCK>
 static __global__ void __launch_bounds__(BLOCK) k_b_push(BArgs a, cudaGraphConditionalHandle cond,
-                                                  int use_cond) {
+                                                         int use_cond) {
   BCtl* ctl = a.ctl;
   const unsigned rs = ctl->rset, ws = ctl->wset;
   const unsigned stamp = static_cast<unsigned>(ctl->rounds) + 1u;
@@ -188,96 +286,34 @@ static __global__ void __launch_bounds__(BLOCK) k_b_push(BArgs a, cudaGraphCondi
     const BGraph G = a.graphs[Q.graph];
     const int rb = __ldg(G.rp + c.u), re = __ldg(G.rp + c.u + 1);
     const int beg = rb + c.chunk * a.chunk, end = min(re, beg + a.chunk);
-    // the loop runs the same trip count on every warp of the CTA, so the
-    // warp-level append inside stays converged
+    // every warp of the CTA runs the same trip count, so the warp-level
+    // append inside stays converged
     for (int e0 = beg; e0 < end; e0 += BLOCK) {
       const int e = e0 + static_cast<int>(threadIdx.x);
       bool want = false;
-      int k = 0, dk = 0;
+      int k = 0;
       if (e < end) {
         k = __ldcs(G.col + e);
-        if (c.pad == 0) {
-          want = b_apply_sum(a, Q, k, c.msg);
+        if (c.op == 0) {
+          want = b_apply_sum(a.d_sum + Q.off, Q.tau, k, c.msg);
         } else {
           const uint32_t base = static_cast<uint32_t>(c.msg), wk = __ldcs(G.w + e);
           const uint32_t s = base + wk;
-          want = b_apply_min(a, Q, k, s < base ? kInfU32 : s, stamp);
+          want = b_apply_min(a.d_min + Q.off, a.v_min + Q.off, a.stamp + Q.off, k,
+                             s < base ? kInfU32 : s, stamp);
         }
-        if (want) dk = __ldg(G.rp + k + 1) - __ldg(G.rp + k);
         if (want) atomicMax(a.qlast + c.q, stamp);
       }
-      b_append(a, ws, c.pad, want, c.q, k, dk, lane);
+      b_append(a, ws, c.op, want, c.q, k, lane);
     }
     my_push += (threadIdx.x == 0) ? static_cast<unsigned long long>(end - beg) : 0ull;
   }
 
-  // General items, both ops: 32 per warp step, edges gathered across lanes.
+  // General items: 32 per warp step, edges gathered across lanes.
   const int warp = (blockIdx.x * BLOCK + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * BLOCK) >> 5;
-  for (int op = 0; op < kBOps; ++op) {
-    const int n = static_cast<int>(min(ctl->cnt[rs][op][0], a.cap[op][0]));
-    for (int base = warp * 32; base < n; base += nwarps * 32) {
-      const int i = base + lane;
-      unsigned q = 0;
-      int u = 0, beg = 0, deg = 0, g = 0;
-      double ms = 0.0;
-      uint32_t mm = 0;
-      if (i < n) {
-        const BItem it = a.items[rs][op][0][i];
-        q = it.q;
-        u = it.u;
-        const BQuery Q = a.queries[q];
-        g = Q.graph;
-        const BGraph G = a.graphs[g];
-        beg = __ldg(G.rp + u);
-        deg = __ldg(G.rp + u + 1) - beg;
-        if (b_fold(a, op, Q, u, deg, &ms, &mm)) ++my_up;
-        else deg = 0;
-      }
-      int incl = deg;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-      }
-      const int total = __shfl_sync(0xffffffffu, incl, 31);
-      const int excl = incl - deg;
-      my_push += static_cast<unsigned long long>(deg);
-      for (int t0 = 0; t0 < total; t0 += 32) {
-        const int t = t0 + lane;
-        int owner = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int probe = __shfl_sync(0xffffffffu, incl, owner + step - 1);
-          if (probe <= t) owner += step;
-        }
-        const int ob = __shfl_sync(0xffffffffu, beg, owner);
-        const int oe = __shfl_sync(0xffffffffu, excl, owner);
-        const unsigned oq = __shfl_sync(0xffffffffu, q, owner);
-        const double oms = __shfl_sync(0xffffffffu, ms, owner);
-        const uint32_t omm = __shfl_sync(0xffffffffu, mm, owner);
-        bool want = false;
-        int k = 0, dk = 0;
-        if (t < total) {
-          const BQuery Q = a.queries[oq];
-          const BGraph G = a.graphs[Q.graph];
-          const int e = ob + (t - oe);
-          k = __ldcs(G.col + e);
-          if (op == 0) {
-            want = b_apply_sum(a, Q, k, oms);
-          } else {
-            const uint32_t wk = __ldcs(G.w + e), s = omm + wk;
-            want = b_apply_min(a, Q, k, s < omm ? kInfU32 : s, stamp);
-          }
-          if (want) {
-            dk = __ldg(G.rp + k + 1) - __ldg(G.rp + k);
-            atomicMax(a.qlast + oq, stamp);
-          }
-        }
-        b_append(a, ws, op, want, oq, k, dk, lane);
-      }
-    }
-  }
+  b_push_items<0>(a, rs, ws, stamp, warp, nwarps, lane, &my_up, &my_push);
+  b_push_items<1>(a, rs, ws, stamp, warp, nwarps, lane, &my_up, &my_push);
 
   // Counters, then the last block closes the round.
   for (int o = 16; o > 0; o >>= 1) {
@@ -296,9 +332,8 @@ static __global__ void __launch_bounds__(BLOCK) k_b_push(BArgs a, cudaGraphCondi
   if (!s_last || threadIdx.x != 0) return;
   __threadfence();
   volatile BCtl* vc = ctl;
-  // large-item updates happen in k_b_take and count there
   unsigned long long next = 0;
-  for (int op = 0; op < kBOps; ++op) next += vc->cnt[ws][op][0] + vc->cnt[ws][op][1];
+  for (int op = 0; op < kBOps; ++op) next += vc->cnt[ws][op];
   unsigned cont = 0;
   if (vc->overflow) {
     ctl->status = 3;
@@ -311,10 +346,7 @@ static __global__ void __launch_bounds__(BLOCK) k_b_push(BArgs a, cudaGraphCondi
   }
   ctl->rounds = vc->rounds + 1;
   // the lists just read are recycled for the round after next
-  for (int op = 0; op < kBOps; ++op) {
-    ctl->cnt[rs][op][0] = 0;
-    ctl->cnt[rs][op][1] = 0;
-  }
+  for (int op = 0; op < kBOps; ++op) ctl->cnt[rs][op] = 0;
   ctl->rset = ws;
   ctl->wset = rs;
   ctl->nchunks = 0;
@@ -333,20 +365,18 @@ static __global__ void k_b_seed(BArgs a, const BItem* seeds, int nseeds) {
        base += gridDim.x * blockDim.x) {
     const int i = base + lane;
     bool want = false;
-    int op = 0, dk = 0;
+    int op = 0;
     BItem it{0, 0};
     if (i < nseeds) {
       it = seeds[i];
       const BQuery Q = a.queries[it.q];
-      const BGraph G = a.graphs[Q.graph];
       op = Q.op;
       if (op == 0) a.d_sum[Q.off + it.u] = Q.init;
       else a.d_min[Q.off + it.u] = 0u;
-      dk = __ldg(G.rp + it.u + 1) - __ldg(G.rp + it.u);
       want = true;
     }
     // both ops may appear in one warp: append per op
-    for (int o = 0; o < kBOps; ++o) b_append(a, ws, o, want && op == o, it.q, it.u, dk, lane);
+    for (int o = 0; o < kBOps; ++o) b_append(a, ws, o, want && op == o, it.q, it.u, lane);
   }
 }
 

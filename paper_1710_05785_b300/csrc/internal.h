@@ -106,6 +106,8 @@ struct maiter_result {
 };
 
 namespace maiter {
+// A result with its state, frontier lists and control block for op on g.
+maiter_status alloc_result(const maiter_graph* g, int op, maiter_result** out);
 // The learned scorer's BF16 weights on the device, and its device (mlp.cu).
 const MlpWeights* mlp_device_weights(const maiter_mlp* m);
 int mlp_device(const maiter_mlp* m);

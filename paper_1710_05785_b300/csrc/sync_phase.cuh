@@ -1,0 +1,148 @@
+// Host-side pieces of the round engine shared by single runs (maiter_api.cu)
+// and the dense batch (batch_engine.cu): launch shapes, trace sinks, and the
+// Phase that adds / drives WHILE(cond) { k_push ; [select] ; k_scan }.
+#pragma once
+#include "internal.h"
+
+namespace maiter {
+
+inline int grid_for(const void* fn, int block, int num_sms, int per_sm_cap) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  if (per_sm_cap > 0 && per_sm > per_sm_cap) per_sm = per_sm_cap;
+  return num_sms * per_sm;
+}
+
+constexpr int kBlock = 256;
+
+// Device buffers that a traced run fills, one row per (record, sampled vertex).
+struct TraceSink {
+  const int* sample = nullptr;
+  int ns = 0;
+  int max_records = 0;
+  int records = 0;
+  float* feat = nullptr;
+  double* dl = nullptr;
+  double* vs = nullptr;
+  unsigned* la = nullptr;
+};
+
+// One phase of the round loop, WHILE(cond) { k_push ; k_scan }, for one
+// operator: its kernel arguments and launch shapes.
+template <class Op>
+struct Phase {
+  KArgs<Op> a{};
+  int push_grid = 1, scan_grid = 1, hist_grid = 1;
+  const MlpWeights* mlp = nullptr;    // LEARNED: scorer weights
+  const int* indeg = nullptr;         // LEARNED / traces: in-degrees
+  unsigned* keys = nullptr;           // LEARNED: key array written by k_score
+
+  void setup(const maiter_graph* g, maiter_result* r, void* delta, const void* coef,
+             double damping, const Tuning& tu, bool topq, const MlpWeights* scorer = nullptr,
+             bool track = false) {
+    mlp = scorer;
+    indeg = g->indeg;
+    keys = scorer ? r->keys : nullptr;
+    a.keys = keys;
+    a.last_act = (scorer || track) ? r->last_act : nullptr;
+    a.n = static_cast<int>(g->n);
+    a.rp = g->rp;
+    a.edges.col = g->col;
+    a.edges.w = g->w;
+    a.coef = static_cast<const typename Op::C*>(coef);
+    a.damping = damping;
+    a.v = static_cast<typename Op::V*>(r->v);
+    a.delta = static_cast<typename Op::D*>(delta);
+    for (int b = 0; b < 2; ++b) a.list[b] = r->list[b];
+    a.large = r->large;
+    a.large_d = static_cast<typename Op::D*>(r->large_d);
+    a.large_cap = r->large_cap;
+    a.ctl = r->ctl;
+    a.topq = topq ? r->topq : nullptr;
+    hist_grid = g->num_sms * 4;
+    a.cut_warp = tu.cut_warp;
+    a.cut_cta = tu.cut_cta;
+    push_grid = grid_for(reinterpret_cast<const void*>(&k_push<Op, kBlock>), kBlock, g->num_sms,
+                         tu.push_blocks_per_sm);
+    scan_grid = g->num_sms * tu.scan_blocks_per_sm;
+    const int tile = kBlock * kScanItems;
+    const int need = static_cast<int>((g->n + tile - 1) / tile);
+    if (need < scan_grid) scan_grid = need > 0 ? need : 1;
+  }
+
+  // TOPFRAC: the three radix-select passes that fix the round's key threshold.
+  void launch_select(cudaStream_t s) const {
+    if (!a.topq) return;
+    TopqCtl* tq = const_cast<TopqCtl*>(a.topq);
+    if (mlp) k_score<Op, kBlock><<<hist_grid, kBlock, 0, s>>>(a, mlp, indeg, keys);
+    k_topq_hist<Op, kBlock, 0><<<hist_grid, kBlock, 0, s>>>(a, tq);
+    k_topq_hist<Op, kBlock, 1><<<hist_grid, kBlock, 0, s>>>(a, tq);
+    k_topq_hist<Op, kBlock, 2><<<hist_grid, kBlock, 0, s>>>(a, tq);
+  }
+
+  void launch_round(cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) const {
+    k_push<Op, kBlock><<<push_grid, kBlock, 0, s>>>(a);
+    launch_select(s);
+    k_scan<Op, kBlock><<<scan_grid, kBlock, 0, s>>>(a, h, use_cond);
+  }
+
+  // Adds WHILE(h) { k_push ; k_scan } after `deps` (graph mode).
+  maiter_status add_to(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps,
+                       cudaGraphConditionalHandle h, cudaGraphNode_t* node) const {
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    MAITER_CUDA(cudaGraphAddNode(node, graph, deps, nullptr, ndeps, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    cudaStream_t cap;
+    MAITER_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      launch_round(cap, h, 1);
+      cudaGraph_t captured = nullptr;
+      e = cudaStreamEndCapture(cap, &captured);
+    }
+    cudaStreamDestroy(cap);
+    MAITER_CUDA(e);
+    return MAITER_OK;
+  }
+
+  // Host-driven rounds with events around each launch (profiling mode), and
+  // optionally a trace record of sampled vertices after every push.
+  maiter_status host_loop(maiter_result* r, cudaStream_t st, cudaEvent_t* e, maiter_stats& s,
+                          TraceSink* trace = nullptr) const {
+    for (;;) {
+      MAITER_CUDA(cudaEventRecord(e[0], st));
+      k_push<Op, kBlock><<<push_grid, kBlock, 0, st>>>(a);
+      MAITER_CUDA(cudaEventRecord(e[1], st));
+      if (trace && trace->records < trace->max_records) {
+        const int64_t o = static_cast<int64_t>(trace->records) * trace->ns;
+        k_trace<Op><<<(trace->ns + 255) / 256, 256, 0, st>>>(
+            a, indeg, trace->sample, trace->ns, trace->feat + o * kMlpIn, trace->dl + o,
+            trace->vs + o, trace->la + o);
+        ++trace->records;
+      }
+      launch_select(st);
+      k_scan<Op, kBlock><<<scan_grid, kBlock, 0, st>>>(a, cudaGraphConditionalHandle{}, 0);
+      MAITER_CUDA(cudaEventRecord(e[2], st));
+      MAITER_CUDA(cudaGetLastError());
+      MAITER_CUDA(cudaMemcpyAsync(r->h_ctl, r->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
+      MAITER_CUDA(cudaStreamSynchronize(st));
+      float t1 = 0.f, t2 = 0.f;
+      cudaEventElapsedTime(&t1, e[0], e[1]);
+      cudaEventElapsedTime(&t2, e[1], e[2]);
+      s.push_ms += t1;
+      s.scan_ms += t2;
+      s.push_launches++;
+      s.scan_launches++;
+      if (r->h_ctl->status != 0) return MAITER_OK;
+    }
+  }
+};
+
+}  // namespace maiter

@@ -10,7 +10,8 @@ def test_candidates_respect_cut_order():
     cs = autotune.candidates(autotune.RUN_SPACE)
     assert cs and all(c["cut_warp"] <= c["cut_cta"] for c in cs)
     assert len({json.dumps(c, sort_keys=True) for c in cs}) == len(cs)
-    assert len(autotune.candidates(autotune.BATCH_SPACE)) == 3 * 3 * 2
+    # sparse mode: 3 x 3 x 2; dense mode ignores cut_large / chunk: 2
+    assert len(autotune.candidates(autotune.BATCH_SPACE)) == 3 * 3 * 2 + 2
 
 
 def test_search_picks_the_fastest_and_warms_up():
@@ -23,7 +24,7 @@ def test_search_picks_the_fastest_and_warms_up():
             (0 if c["push_blocks_per_sm"] == 4 else 1)
 
     best, timings = autotune.search(autotune.BATCH_SPACE, measure, repeats=2)
-    assert best == {"cut_large": 1024, "chunk": 512, "push_blocks_per_sm": 4}
+    assert best == {"mode": 1, "cut_large": 1024, "chunk": 512, "push_blocks_per_sm": 4}
     assert len(calls) == 3 * len(timings)          # one warm call + two timed per config
     assert timings[0][0] <= timings[-1][0]
 

@@ -50,10 +50,11 @@ def check(mt, graphs, queries, b):
             assert oracle.relative_error(v, vstar) <= 1e-6, qi
 
 
-def test_batch_mixed_queries_uneven_graphs(mt):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_mixed_queries_uneven_graphs(mt, mode):
     graphs, queries = make_batch([8, 10, 11, 12], n_ppr=6, n_sssp=3)
     G = [mt.Graph.from_csr(g) for g in graphs]
-    b = mt.run_batch(G, queries)
+    b = mt.run_batch(G, queries, mode=mode)
     check(mt, graphs, queries, b)
     st = b.stats()
     assert st["converged"] == 1 and st["rounds"] >= 1
@@ -62,12 +63,13 @@ def test_batch_mixed_queries_uneven_graphs(mt):
     assert (qr >= 0).all() and qr.max() <= st["rounds"] and (qr > 0).sum() > len(queries) // 2
 
 
-def test_batch_reuse_gives_the_same_answer(mt):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_reuse_gives_the_same_answer(mt, mode):
     graphs, queries = make_batch([9, 11], n_ppr=4, n_sssp=2, seed=3)
     G = [mt.Graph.from_csr(g) for g in graphs]
-    b = mt.run_batch(G, queries)
+    b = mt.run_batch(G, queries, mode=mode)
     first = [b.state(i).copy() for i in range(len(queries))]
-    b2 = mt.run_batch(G, queries, batch=b)
+    b2 = mt.run_batch(G, queries, batch=b, mode=mode)
     assert b2 is b
     for i, q in enumerate(queries):
         if q["op"] == 2:
@@ -76,7 +78,8 @@ def test_batch_reuse_gives_the_same_answer(mt):
             assert oracle.relative_error(b.state(i), first[i]) <= 1e-6
 
 
-def test_batch_multi_source_sssp_and_hub_chunks(mt):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_multi_source_sssp_and_hub_chunks(mt, mode):
     # a star hub (chunked path) plus an R-MAT graph; a two-seed SSSP query
     n = 6000
     src = np.concatenate([np.zeros(n - 1, np.int64), np.arange(1, n - 1)])
@@ -89,7 +92,7 @@ def test_batch_multi_source_sssp_and_hub_chunks(mt):
     queries = [dict(op=2, graph=0, seeds=[0]), dict(op=0, graph=0, seeds=[0, 5], damping=D,
                                                     eps=1e-6 * (1 - D) ** 2 / 2),
                dict(op=2, graph=1, seeds=[int(s2[0]), int(s2[1])])]
-    b = mt.run_batch(G, queries, cut_large=256, chunk=512)
+    b = mt.run_batch(G, queries, cut_large=256, chunk=512, mode=mode)
     np.testing.assert_array_equal(b.state(0), oracle.dijkstra(star, 0))
     assert oracle.relative_error(b.state(1), oracle.pagerank(star, D, seeds=[0, 5])) <= 1e-6
     expect = np.minimum(oracle.dijkstra(r, int(s2[0])), oracle.dijkstra(r, int(s2[1])))
@@ -102,7 +105,7 @@ def test_autotuned_configs_keep_results_exact(mt, tmp_path):
     G = [mt.Graph.from_csr(g) for g in graphs]
     cache = autotune.Cache(str(tmp_path / "t.json"))
     best = autotune.tune_batch(mt, graphs, G, queries, cache=cache, sample=8)
-    assert set(best) == {"cut_large", "chunk", "push_blocks_per_sm"}
+    assert set(best) == {"mode", "cut_large", "chunk", "push_blocks_per_sm"}
     assert autotune.tune_batch(mt, graphs, G, queries, cache=cache, sample=8) == best  # cached
     b = mt.run_batch(G, queries, **best)
     check(mt, graphs, queries, b)
