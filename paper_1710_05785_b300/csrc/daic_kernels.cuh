@@ -30,7 +30,7 @@ namespace maiter {
 constexpr int kBuckets = 3;
 constexpr int kChunk = 1024;   // edges per large-vertex work item (one CTA, 4 per thread)
 constexpr int kUnroll = 4;
-constexpr int kScanItems = 4;  // vertices per thread per k_scan tile
+constexpr int kScanItems = 8;  // vertices per thread per k_scan tile
 
 // Device-resident control block of one run.  Everything the round loop needs
 // to decide on its own lives here, so the loop never returns to the host.
@@ -158,36 +158,57 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
   for (int tile = blockIdx.x * kTile; tile < a.n; tile += gridDim.x * kTile) {
     int bkt[kItems], dg[kItems];
     int cnt[3] = {0, 0, 0};
+    // Three dependent stages, each with all of the thread's loads in flight
+    // at once: (1) Delta and v of every item, (2) the selection, (3) the row
+    // offsets of the selected items.
+    constexpr D kNone = Op::kIsSum ? D(0) : D(kInfU32);   // "nothing pending"
+    D dd[kItems];
+    typename Op::V vv[kItems];
+    bool sel[kItems];
 #pragma unroll
     for (int u = 0; u < kItems; ++u) {
       const int j = tile + u * BLOCK + static_cast<int>(threadIdx.x);
+      const bool in = j < a.n;
+      dd[u] = in ? a.delta[j] : kNone;
+      vv[u] = Op::kIsSum ? typename Op::V(0) : (in ? a.v[j] : typename Op::V(kInfU32));
+    }
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+      const int j = tile + u * BLOCK + static_cast<int>(threadIdx.x);
+      const bool pend = j < a.n && Op::pending(dd[u], vv[u]);
+      npend += pend;
+      bool s;
+      if (Op::kIsSum) {
+        const double p = Op::priority(dd[u], vv[u]);
+        rsum += p;
+        s = pend && p > tau;
+      } else {
+        s = pend;
+      }
+      if (a.topq) s = pend && (a.keys ? a.keys[j] : priority_key<Op>(dd[u], vv[u])) >= key_thr;
+      sel[u] = s;
+    }
+    int rb[kItems], re[kItems];
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+      const int j = tile + u * BLOCK + static_cast<int>(threadIdx.x);
+      rb[u] = sel[u] ? __ldg(a.rp + j) : 0;
+      re[u] = sel[u] ? __ldg(a.rp + j + 1) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
       bkt[u] = -1;
       dg[u] = 0;
-      if (j < a.n) {
-        const D d = a.delta[j];
-        const typename Op::V vv = Op::kIsSum ? typename Op::V(0) : a.v[j];
-        const bool pend = Op::pending(d, vv);
-        npend += pend;
-        bool sel;
-        if (Op::kIsSum) {
-          const double p = Op::priority(d, vv);
-          rsum += p;
-          sel = pend && p > tau;
-        } else {
-          sel = pend;
-        }
-        if (a.topq) sel = pend && (a.keys ? a.keys[j] : priority_key<Op>(d, vv)) >= key_thr;
-        if (sel) {
-          const int deg = __ldg(a.rp + j + 1) - __ldg(a.rp + j);
-          const int b = deg < a.cut_warp ? 0 : (deg < a.cut_cta ? 1 : 2);
-          bkt[u] = b;
-          dg[u] = deg;
-          cnt[0] += (b == 0);
-          cnt[1] += (b == 1);
-          cnt[2] += (b == 2) ? (deg + kChunk - 1) / kChunk : 0;
-          ++nact;
-          npush += static_cast<unsigned long long>(deg);
-        }
+      if (sel[u]) {
+        const int deg = re[u] - rb[u];
+        const int b = deg < a.cut_warp ? 0 : (deg < a.cut_cta ? 1 : 2);
+        bkt[u] = b;
+        dg[u] = deg;
+        cnt[0] += (b == 0);
+        cnt[1] += (b == 1);
+        cnt[2] += (b == 2) ? (deg + kChunk - 1) / kChunk : 0;
+        ++nact;
+        npush += static_cast<unsigned long long>(deg);
       }
     }
     int incl[3];

@@ -131,7 +131,7 @@ struct OpMinU32 {
   __device__ static __forceinline__ bool live(Msg m) { return m != kInfU32; }
   struct Edge { int k; uint32_t w; };
   __device__ static __forceinline__ Edge load(const EdgeCtx& g, int64_t e) {
-    return Edge{__ldcs(g.col + e), __ldcs(g.w + e)};
+    return Edge{__ldg(g.col + e), __ldg(g.w + e)};
   }
   __device__ static __forceinline__ void apply(Edge ed, Msg m, D* delta) {
     const uint32_t s = m + ed.w;

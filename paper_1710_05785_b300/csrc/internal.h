@@ -55,7 +55,7 @@ struct Tuning {
   int cut_warp = 32;    // out-degree below this: warp-gathered small path
   int cut_cta = 512;    // out-degree at or above this: one CTA per kChunk edges
   int push_blocks_per_sm = 0;   // 0 = occupancy maximum
-  int scan_blocks_per_sm = 4;
+  int scan_blocks_per_sm = 0;   // 0 = occupancy maximum
 };
 
 }  // namespace maiter

@@ -66,7 +66,8 @@ struct Phase {
     a.cut_cta = tu.cut_cta;
     push_grid = grid_for(reinterpret_cast<const void*>(&k_push<Op, kBlock>), kBlock, g->num_sms,
                          tu.push_blocks_per_sm);
-    scan_grid = g->num_sms * tu.scan_blocks_per_sm;
+    scan_grid = grid_for(reinterpret_cast<const void*>(&k_scan<Op, kBlock>), kBlock, g->num_sms,
+                         tu.scan_blocks_per_sm);
     const int tile = kBlock * kScanItems;
     const int need = static_cast<int>((g->n + tile - 1) / tile);
     if (need < scan_grid) scan_grid = need > 0 ? need : 1;
