@@ -288,46 +288,59 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
   // (fence + ticket).  Thread 0 decides; the block then undoes the delta
   // takes of large vertices if no push follows.
   __threadfence();
-  volatile DevCtl* vc = ctl;
+  __shared__ unsigned s_overflow;
   if (threadIdx.x == 0) {
-    const double resid = Op::kIsSum ? vc->resid_acc : static_cast<double>(vc->pend_acc);
-    const unsigned long long act = vc->act_acc;
-    const unsigned long long psh = vc->push_acc;
-    const unsigned long long pend = vc->pend_acc;
+    // Every word the decision needs, loaded at once from L2 (the other CTAs'
+    // atomics land there), then decided without further round trips.
+    const double resid_acc = __ldcg(&ctl->resid_acc);
+    const unsigned long long act = __ldcg(&ctl->act_acc);
+    const unsigned long long psh = __ldcg(&ctl->push_acc);
+    const unsigned long long pend = __ldcg(&ctl->pend_acc);
+    const unsigned long long rounds = __ldcg(&ctl->rounds);
+    const unsigned long long activations = __ldcg(&ctl->activations);
+    const unsigned long long pushes = __ldcg(&ctl->pushes);
+    const long long max_rounds = __ldcg(&ctl->max_rounds);
+    const double eps = __ldcg(&ctl->eps);
+    const double eps_eff = __ldcg(&ctl->eps_eff);
+    const double switch_frac = __ldcg(&ctl->switch_frac);
+    const double tau_now = __ldcg(&ctl->tau);
+    const unsigned overflow = __ldcg(&ctl->overflow);
+    const double resid = Op::kIsSum ? resid_acc : static_cast<double>(pend);
     // A phase that ends early (the FP64 warm-up of the mixed-precision run)
     // stops at switch_frac times the residual its first scan measured.
-    double eps_now = vc->eps_eff;
-    if (vc->rounds == 0) {
-      eps_now = vc->eps;
-      if (vc->switch_frac > 0.0 && vc->switch_frac * resid > eps_now)
-        eps_now = vc->switch_frac * resid;
+    double eps_now = eps_eff;
+    if (rounds == 0) {
+      eps_now = eps;
+      if (switch_frac > 0.0 && switch_frac * resid > eps_now) eps_now = switch_frac * resid;
       ctl->eps_eff = eps_now;
     }
     const bool converged =
-        Op::kIsSum ? (resid < eps_now || pend == 0 || (vc->rounds == 0 && vc->switch_frac >= 1.0))
+        Op::kIsSum ? (resid < eps_now || pend == 0 || (rounds == 0 && switch_frac >= 1.0))
                    : (pend == 0);
     unsigned cont = 0;
     ctl->residual = resid;
-    if (vc->overflow) {
+    if (overflow) {
       ctl->status = 3;
     } else if (converged) {
       ctl->status = 1;
-    } else if (static_cast<long long>(vc->rounds) >= vc->max_rounds) {
+    } else if (static_cast<long long>(rounds) >= max_rounds) {
       ctl->status = 2;
     } else {
       cont = 1;
-      ctl->rounds = vc->rounds + 1;
-      ctl->activations = vc->activations + act;
-      ctl->pushes = vc->pushes + psh;
+      ctl->rounds = rounds + 1;
+      ctl->activations = activations + act;
+      ctl->pushes = pushes + psh;
       // Threshold selected nothing although work remains: lower it (x0.1, to 0)
       // so the run always terminates.
-      if (Op::kIsSum && act == 0) ctl->tau = (vc->tau < 1e-300) ? 0.0 : vc->tau * 0.1;
+      if (Op::kIsSum && act == 0) ctl->tau = (tau_now < 1e-300) ? 0.0 : tau_now * 0.1;
     }
     s_cont = cont;
+    s_overflow = overflow;
   }
   __syncthreads();
   const unsigned cont = s_cont;
-  if (!cont && !vc->overflow) {
+  volatile DevCtl* vc = ctl;
+  if (!cont && !s_overflow) {
     const unsigned nl = vc->cnt[ws][2] < a.large_cap ? vc->cnt[ws][2] : a.large_cap;
     for (unsigned i = threadIdx.x; i < nl; i += BLOCK) {
       const int2 e = a.large[i];
@@ -375,10 +388,13 @@ template <class Op, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a) {
   using Msg = typename Op::Msg;
   const DevCtl* ctl = a.ctl;
+  // both count sets and the selector in one round trip, then pick
+  const uint4 c0 = *reinterpret_cast<const uint4*>(ctl->cnt[0]);
+  const uint4 c1 = *reinterpret_cast<const uint4*>(ctl->cnt[1]);
   const unsigned rs = ctl->rset;
-  const int cS = static_cast<int>(ctl->cnt[rs][0]);
-  const int cM = static_cast<int>(ctl->cnt[rs][1]);
-  const int cL = static_cast<int>(ctl->cnt[rs][2]);
+  const int cS = static_cast<int>(rs ? c1.x : c0.x);
+  const int cM = static_cast<int>(rs ? c1.y : c0.y);
+  const int cL = static_cast<int>(rs ? c1.z : c0.z);
   const int lane = threadIdx.x & 31;
   // rounds of the updates this launch performs (for the scorer's age feature)
   const unsigned round = static_cast<unsigned>(ctl->rounds);
