@@ -62,9 +62,9 @@ __global__ void k_count_large(const int* __restrict__ rp, int n, int cut, unsign
 }
 
 // ------------------------------------------------------------- dense mode
-// Every query is its own round-engine run (k_push / k_scan on its own v,
+// Every query is its own round-engine run (k_scan / k_push on its own v,
 // Delta, frontier lists and control block) and one branch of a single CUDA
-// graph: init -> seeds -> WHILE(cond_q) { k_push ; k_scan }.  Branches share
+// graph: init -> seeds -> WHILE(cond_q) { k_scan ; k_push }.  Branches share
 // nothing, so the GPU runs them concurrently, and each ends on its own exact
 // termination test (sum |Delta| < eps_q, or no pending vertex).
 

@@ -8,10 +8,11 @@
 //                 above a threshold),
 //               * compacts them with warp ballots into lists by out-degree:
 //                 small and medium vertices one entry each, large vertices
-//                 one entry per chunk of kChunk edges,
-//             and whose last block decides, on the device, whether another
-//             round follows (it sets the WHILE condition of the CUDA graph).
-//   k_push  - the update of Eq. 5 for every listed vertex: read-and-reset of
+//                 one entry per chunk of kChunk edges.
+//   k_push  - first the termination decision on the scan's totals (every CTA
+//             decides the same; CTA 0 records it and sets the WHILE condition
+//             of the CUDA graph), then the update of Eq. 5 for every listed
+//             vertex: read-and-reset of
 //             Delta_j, fold into v_j, and the scatter of g_{j,k}(Delta_j) into
 //             every out-neighbour's Delta_k with atomics.  Work granularity by
 //             degree: a CTA per chunk of a large vertex (so a hub is spread
@@ -34,30 +35,35 @@ constexpr int kScanItems = 8;  // vertices per thread per k_scan tile
 
 // Device-resident control block of one run.  Everything the round loop needs
 // to decide on its own lives here, so the loop never returns to the host.
+//
+// A round is k_scan then k_push.  The scan accumulates its counts into the
+// set `scan_set` with fire-and-forget atomics; the push reads that set once
+// the scan has finished (the kernel boundary makes every atomic visible),
+// and every push CTA takes the same termination decision from it.  Push CTA
+// 0 records the decision and clears the other set for the next scan, so no
+// CTA ever waits on another and no word is read while it is being reset.
 struct DevCtl {
-  unsigned int cnt[2][4];        // [set][bucket] frontier sizes (double-buffered);
-                                 // bucket 2 counts large-vertex chunks
-  unsigned int rset;             // set the next push reads
-  unsigned int wset;             // set the next scan writes
-  unsigned int ticket;           // last-block election in k_scan
+  unsigned int cnt[2][4];        // [set][bucket] list sizes; bucket 2 counts large chunks
+  unsigned int scan_set;         // set the next scan writes (flipped by push CTA 0)
+  unsigned int push_set;         // set the next push reads (written by scan CTA 0)
+  unsigned int overflow[2];      // [set] a list reservation would have run past its capacity
+  double resid_acc[2];           // [set] sum |Delta| over the scan (sum ops)
+  unsigned long long act_acc[2];   // [set] selected vertices
+  unsigned long long push_acc[2];  // [set] sum of out-degrees of selected vertices
+  unsigned long long pend_acc[2];  // [set] pending vertices (Delta != 0 / Delta < v)
   int status;                    // 0 running, 1 converged, 2 round cap hit, 3 overflow
-  double resid_acc;              // this scan: sum |Delta| (sum) or pending count (min)
-  unsigned long long act_acc;    // this scan: selected vertices
-  unsigned long long push_acc;   // this scan: sum of out-degrees of selected vertices
-  unsigned long long pend_acc;   // this scan: pending vertices (Delta != 0 / Delta < v)
-  unsigned long long rounds;
+  int sched;                     // maiter_sched
+  unsigned long long rounds;     // pushes performed
   unsigned long long activations;
   unsigned long long pushes;
   double residual;               // last decided residual
   double tau;                    // current activation threshold (sum ops)
   double eps;                    // termination bound (sum ops)
-  double eps_eff;                // bound of the current phase (set by the first scan)
+  double eps_eff;                // bound of the current phase (set by the first decision)
   double switch_frac;            // > 0: this phase ends at switch_frac x first residual
   long long max_rounds;
-  int sched;                     // maiter_sched
   int phase;                     // 1 once the FP32 phase of a mixed run has started
-  unsigned int overflow;         // a list reservation would have run past its capacity
-  unsigned int pad;
+  int pad;
   unsigned long long warm_rounds;      // mixed precision: counters at the FP32 switch
   unsigned long long warm_activations;
   unsigned long long warm_pushes;
@@ -132,12 +138,11 @@ __device__ __forceinline__ int warp_incl_scan(int x, int lane) {
 // ------------------------------------------------------------------ scan
 
 template <class Op, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditionalHandle cond,
-                                                 int use_cond) {
+__global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
   static_assert(BLOCK % 32 == 0 && BLOCK <= 1024, "block");
   using D = typename Op::D;
   DevCtl* ctl = a.ctl;
-  const unsigned ws = ctl->wset;
+  const unsigned ws = ctl->scan_set;
   const double tau = ctl->tau;
   const unsigned key_thr = a.topq ? a.topq->key_thr : 0u;
   const int lane = threadIdx.x & 31;
@@ -250,7 +255,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
             a.large_d[pos[2] + q] = d;
           }
         } else {
-          atomicOr(&ctl->overflow, 1u);
+          atomicOr(&ctl->overflow[ws], 1u);
         }
         pos[2] += static_cast<unsigned>(chunks);
       }
@@ -258,11 +263,10 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
     __syncthreads();   // s_woff / s_base are reused by the next tile
   }
 
-  // Block reduction, one atomic per block per counter.
+  // Block reduction, one fire-and-forget atomic per block per counter; the
+  // push reads the totals after this kernel ends.
   __shared__ double s_r[BLOCK / 32];
   __shared__ unsigned long long s_a[BLOCK / 32], s_p[BLOCK / 32], s_q[BLOCK / 32];
-  __shared__ int s_last;
-  __shared__ unsigned s_cont;
   rsum = warp_sum(rsum);
   nact = warp_sum(nact);
   npush = warp_sum(npush);
@@ -273,97 +277,12 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a, cudaGraphConditiona
     double r = 0.0;
     unsigned long long x = 0, y = 0, z = 0;
     for (int i = 0; i < BLOCK / 32; ++i) { r += s_r[i]; x += s_a[i]; y += s_p[i]; z += s_q[i]; }
-    if (Op::kIsSum && r != 0.0) atomicAdd(&ctl->resid_acc, r);
-    if (x) atomicAdd(&ctl->act_acc, x);
-    if (y) atomicAdd(&ctl->push_acc, y);
-    if (z) atomicAdd(&ctl->pend_acc, z);
-    __threadfence();
-    const unsigned t = atomicAdd(&ctl->ticket, 1u);
-    s_last = (t == gridDim.x - 1);
+    if (Op::kIsSum && r != 0.0) atomicAdd(&ctl->resid_acc[ws], r);
+    if (x) atomicAdd(&ctl->act_acc[ws], x);
+    if (y) atomicAdd(&ctl->push_acc[ws], y);
+    if (z) atomicAdd(&ctl->pend_acc[ws], z);
+    if (blockIdx.x == 0) ctl->push_set = ws;
   }
-  __syncthreads();
-  if (!s_last) return;
-
-  // Last block: every other block's counters and list entries are visible
-  // (fence + ticket).  Thread 0 decides; the block then undoes the delta
-  // takes of large vertices if no push follows.
-  __threadfence();
-  __shared__ unsigned s_overflow;
-  if (threadIdx.x == 0) {
-    // Every word the decision needs, loaded at once from L2 (the other CTAs'
-    // atomics land there), then decided without further round trips.
-    const double resid_acc = __ldcg(&ctl->resid_acc);
-    const unsigned long long act = __ldcg(&ctl->act_acc);
-    const unsigned long long psh = __ldcg(&ctl->push_acc);
-    const unsigned long long pend = __ldcg(&ctl->pend_acc);
-    const unsigned long long rounds = __ldcg(&ctl->rounds);
-    const unsigned long long activations = __ldcg(&ctl->activations);
-    const unsigned long long pushes = __ldcg(&ctl->pushes);
-    const long long max_rounds = __ldcg(&ctl->max_rounds);
-    const double eps = __ldcg(&ctl->eps);
-    const double eps_eff = __ldcg(&ctl->eps_eff);
-    const double switch_frac = __ldcg(&ctl->switch_frac);
-    const double tau_now = __ldcg(&ctl->tau);
-    const unsigned overflow = __ldcg(&ctl->overflow);
-    const double resid = Op::kIsSum ? resid_acc : static_cast<double>(pend);
-    // A phase that ends early (the FP64 warm-up of the mixed-precision run)
-    // stops at switch_frac times the residual its first scan measured.
-    double eps_now = eps_eff;
-    if (rounds == 0) {
-      eps_now = eps;
-      if (switch_frac > 0.0 && switch_frac * resid > eps_now) eps_now = switch_frac * resid;
-      ctl->eps_eff = eps_now;
-    }
-    const bool converged =
-        Op::kIsSum ? (resid < eps_now || pend == 0 || (rounds == 0 && switch_frac >= 1.0))
-                   : (pend == 0);
-    unsigned cont = 0;
-    ctl->residual = resid;
-    if (overflow) {
-      ctl->status = 3;
-    } else if (converged) {
-      ctl->status = 1;
-    } else if (static_cast<long long>(rounds) >= max_rounds) {
-      ctl->status = 2;
-    } else {
-      cont = 1;
-      ctl->rounds = rounds + 1;
-      ctl->activations = activations + act;
-      ctl->pushes = pushes + psh;
-      // Threshold selected nothing although work remains: lower it (x0.1, to 0)
-      // so the run always terminates.
-      if (Op::kIsSum && act == 0) ctl->tau = (tau_now < 1e-300) ? 0.0 : tau_now * 0.1;
-    }
-    s_cont = cont;
-    s_overflow = overflow;
-  }
-  __syncthreads();
-  const unsigned cont = s_cont;
-  volatile DevCtl* vc = ctl;
-  if (!cont && !s_overflow) {
-    const unsigned nl = vc->cnt[ws][2] < a.large_cap ? vc->cnt[ws][2] : a.large_cap;
-    for (unsigned i = threadIdx.x; i < nl; i += BLOCK) {
-      const int2 e = a.large[i];
-      if (e.y == 0) Op::untake(e.x, a.large_d[i], a.delta);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  ctl->resid_acc = 0.0;
-  ctl->act_acc = 0;
-  ctl->push_acc = 0;
-  ctl->pend_acc = 0;
-  ctl->ticket = 0;
-  // The lists just written are pushed next; the other count set is recycled.
-  if (cont) {
-    ctl->rset = ws;
-    ctl->wset = ws ^ 1u;
-    for (int b = 0; b < 4; ++b) ctl->cnt[ws ^ 1u][b] = 0;
-  } else {
-    for (int b = 0; b < 4; ++b) ctl->cnt[ws][b] = 0;
-  }
-  __threadfence();
-  if (use_cond) cudaGraphSetConditional(cond, cont);
 }
 
 // ------------------------------------------------------------------ push
@@ -385,19 +304,96 @@ __device__ __forceinline__ void scatter_range(const EdgeCtx& g, int e, int end,
 }
 
 template <class Op, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a) {
+__global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a,
+                                                                cudaGraphConditionalHandle cond,
+                                                                int use_cond) {
   using Msg = typename Op::Msg;
-  const DevCtl* ctl = a.ctl;
-  // both count sets and the selector in one round trip, then pick
-  const uint4 c0 = *reinterpret_cast<const uint4*>(ctl->cnt[0]);
-  const uint4 c1 = *reinterpret_cast<const uint4*>(ctl->cnt[1]);
-  const unsigned rs = ctl->rset;
-  const int cS = static_cast<int>(rs ? c1.x : c0.x);
-  const int cM = static_cast<int>(rs ? c1.y : c0.y);
-  const int cL = static_cast<int>(rs ? c1.z : c0.z);
+  DevCtl* ctl = a.ctl;
   const int lane = threadIdx.x & 31;
-  // rounds of the updates this launch performs (for the scorer's age feature)
-  const unsigned round = static_cast<unsigned>(ctl->rounds);
+
+  // Termination decision (the progress check of Section 5.1) on the totals
+  // of the scan that just ended.  Thread 0 of every CTA loads the words it
+  // needs in one round trip (both sets, then picks) and decides; all CTAs
+  // reach the same decision, and CTA 0 records it.
+  __shared__ int s_cnt[3];
+  __shared__ unsigned s_cont, s_round, s_overflow;
+  if (threadIdx.x == 0) {
+    const unsigned ps = ctl->push_set;
+    const uint4 c0 = *reinterpret_cast<const uint4*>(ctl->cnt[0]);
+    const uint4 c1 = *reinterpret_cast<const uint4*>(ctl->cnt[1]);
+    const double r0 = ctl->resid_acc[0], r1 = ctl->resid_acc[1];
+    const unsigned long long a0 = ctl->act_acc[0], a1 = ctl->act_acc[1];
+    const unsigned long long p0 = ctl->push_acc[0], p1 = ctl->push_acc[1];
+    const unsigned long long q0 = ctl->pend_acc[0], q1 = ctl->pend_acc[1];
+    const unsigned o0 = ctl->overflow[0], o1 = ctl->overflow[1];
+    const unsigned long long rounds = ctl->rounds;
+    const long long max_rounds = ctl->max_rounds;
+    const double eps = ctl->eps, eps_eff = ctl->eps_eff, switch_frac = ctl->switch_frac;
+    const uint4 c = ps ? c1 : c0;
+    const unsigned long long act = ps ? a1 : a0, psh = ps ? p1 : p0, pend = ps ? q1 : q0;
+    const unsigned overflow = ps ? o1 : o0;
+    const double resid = Op::kIsSum ? (ps ? r1 : r0) : static_cast<double>(pend);
+    // A phase that ends early (the FP64 warm-up of the mixed-precision run)
+    // stops at switch_frac times the residual its first scan measured.
+    double eps_now = eps_eff;
+    if (rounds == 0) {
+      eps_now = eps;
+      if (switch_frac > 0.0 && switch_frac * resid > eps_now) eps_now = switch_frac * resid;
+    }
+    const bool converged =
+        Op::kIsSum ? (resid < eps_now || pend == 0 || (rounds == 0 && switch_frac >= 1.0))
+                   : (pend == 0);
+    int status = 0;
+    if (overflow) status = 3;
+    else if (converged) status = 1;
+    else if (static_cast<long long>(rounds) >= max_rounds) status = 2;
+    const unsigned cont = status == 0;
+    if (blockIdx.x == 0) {
+      ctl->residual = resid;
+      if (rounds == 0) ctl->eps_eff = eps_now;
+      if (cont) {
+        ctl->rounds = rounds + 1;
+        ctl->activations = ctl->activations + act;
+        ctl->pushes = ctl->pushes + psh;
+        // Threshold selected nothing although work remains: lower it (x0.1,
+        // to 0) so the run always terminates.
+        if (Op::kIsSum && act == 0) {
+          const double t = ctl->tau;
+          ctl->tau = (t < 1e-300) ? 0.0 : t * 0.1;
+        }
+      } else {
+        ctl->status = status;
+      }
+      // the other set starts empty for the next scan
+      const unsigned ns = ps ^ 1u;
+      for (int b = 0; b < 4; ++b) ctl->cnt[ns][b] = 0;
+      ctl->resid_acc[ns] = 0.0;
+      ctl->act_acc[ns] = ctl->push_acc[ns] = ctl->pend_acc[ns] = 0;
+      ctl->overflow[ns] = 0;
+      ctl->scan_set = ns;
+      if (use_cond) cudaGraphSetConditional(cond, cont);
+    }
+    s_cnt[0] = static_cast<int>(c.x);
+    s_cnt[1] = static_cast<int>(c.y);
+    s_cnt[2] = static_cast<int>(min(c.z, a.large_cap));
+    s_cont = cont;
+    s_overflow = overflow;
+    // rounds of the updates this launch performs (for the scorer's age feature)
+    s_round = static_cast<unsigned>(rounds + 1);
+  }
+  __syncthreads();
+  const int cS = s_cnt[0], cM = s_cnt[1], cL = s_cnt[2];
+  const unsigned round = s_round;
+  if (!s_cont) {
+    // No push follows: hand the deltas the scan took from large vertices back
+    // (after an overflow the list is incomplete and the run is failed anyway).
+    if (s_overflow) return;
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < cL; i += gridDim.x * BLOCK) {
+      const int2 e = a.large[i];
+      if (e.y == 0) Op::untake(e.x, a.large_d[i], a.delta);
+    }
+    return;
+  }
 
   // Large vertices: one CTA per chunk of kChunk edges.  The delta was taken
   // by the scan; chunk 0 folds it into v_j.
@@ -496,13 +492,14 @@ static __global__ void k_to_f32(const double* __restrict__ d64, float* __restric
     ctl->warm_pushes = ctl->pushes;
     ctl->eps_eff = ctl->eps;
     ctl->switch_frac = 0.0;
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < 2; ++s) {
       for (int b = 0; b < 4; ++b) ctl->cnt[s][b] = 0;
-    ctl->rset = 0;
-    ctl->wset = 0;
-    ctl->ticket = 0;
-    ctl->resid_acc = 0.0;
-    ctl->act_acc = ctl->push_acc = ctl->pend_acc = 0;
+      ctl->resid_acc[s] = 0.0;
+      ctl->act_acc[s] = ctl->push_acc[s] = ctl->pend_acc[s] = 0;
+      ctl->overflow[s] = 0;
+    }
+    ctl->scan_set = 0;
+    ctl->push_set = 0;
     if (use_cond) cudaGraphSetConditional(cond, st == 1 ? 1u : 0u);
   }
 }

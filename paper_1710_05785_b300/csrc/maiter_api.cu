@@ -310,8 +310,8 @@ static int conversion_grid(const maiter_graph* g) { return g->num_sms * 4; }
 
 // Builds the executable graph of a run: WHILE{round} for one phase, or
 // WHILE{round FP64} -> k_to_f32 -> WHILE{round FP32} for mixed precision.
-// The first body pass of a phase pushes an empty frontier (its counts start
-// at zero) and its scan builds the first frontier.
+// Each body pass scans, then pushes; the push decides whether another pass
+// follows, so a phase whose first scan finds nothing to do pushes nothing.
 static maiter_status build_graph(const maiter_graph* g, maiter_result* r, int op,
                                  const RunPlan& plan) {
   if (r->exec) { cudaGraphExecDestroy(r->exec); r->exec = nullptr; }

@@ -9,7 +9,7 @@
 // can pass their graph and output buffers, but they cannot let the library
 // call cudaMalloc for its working memory.
 //
-// How: the same round kernels as maiter_run (k_push / k_scan for the min
+// How: the same round kernels as maiter_run (k_scan / k_push for the min
 // operator), with their working memory - the three frontier lists and the
 // control block - carved out of one file-scope device array of fixed size.
 // Every GPU that loads this library holds that array until the process exits.
@@ -181,8 +181,8 @@ extern "C" maiter_status maiter_sssp_noalloc(int64_t n, int64_t m, const int32_t
 
   DevCtl h{};
   for (;;) {
-    k_push<OpMinU32, kBlock><<<push_grid, kBlock, 0, st>>>(a);
-    k_scan<OpMinU32, kBlock><<<scan_grid, kBlock, 0, st>>>(a, cudaGraphConditionalHandle{}, 0);
+    k_scan<OpMinU32, kBlock><<<scan_grid, kBlock, 0, st>>>(a);
+    k_push<OpMinU32, kBlock><<<push_grid, kBlock, 0, st>>>(a, cudaGraphConditionalHandle{}, 0);
     MAITER_CUDA(cudaGetLastError());
     MAITER_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
     MAITER_CUDA(cudaStreamSynchronize(st));

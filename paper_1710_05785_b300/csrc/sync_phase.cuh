@@ -83,13 +83,15 @@ struct Phase {
     k_topq_hist<Op, kBlock, 2><<<hist_grid, kBlock, 0, s>>>(a, tq);
   }
 
+  // One round: [selection passes], frontier scan, then the push, whose CTAs
+  // decide termination and set the WHILE condition.
   void launch_round(cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) const {
-    k_push<Op, kBlock><<<push_grid, kBlock, 0, s>>>(a);
     launch_select(s);
-    k_scan<Op, kBlock><<<scan_grid, kBlock, 0, s>>>(a, h, use_cond);
+    k_scan<Op, kBlock><<<scan_grid, kBlock, 0, s>>>(a);
+    k_push<Op, kBlock><<<push_grid, kBlock, 0, s>>>(a, h, use_cond);
   }
 
-  // Adds WHILE(h) { k_push ; k_scan } after `deps` (graph mode).
+  // Adds WHILE(h) { [select] ; k_scan ; k_push } after `deps` (graph mode).
   maiter_status add_to(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps,
                        cudaGraphConditionalHandle h, cudaGraphNode_t* node) const {
     cudaGraphNodeParams np{};
@@ -119,8 +121,11 @@ struct Phase {
                           TraceSink* trace = nullptr) const {
     for (;;) {
       MAITER_CUDA(cudaEventRecord(e[0], st));
-      k_push<Op, kBlock><<<push_grid, kBlock, 0, st>>>(a);
+      launch_select(st);
+      k_scan<Op, kBlock><<<scan_grid, kBlock, 0, st>>>(a);
       MAITER_CUDA(cudaEventRecord(e[1], st));
+      k_push<Op, kBlock><<<push_grid, kBlock, 0, st>>>(a, cudaGraphConditionalHandle{}, 0);
+      MAITER_CUDA(cudaEventRecord(e[2], st));
       if (trace && trace->records < trace->max_records) {
         const int64_t o = static_cast<int64_t>(trace->records) * trace->ns;
         k_trace<Op><<<(trace->ns + 255) / 256, 256, 0, st>>>(
@@ -128,17 +133,14 @@ struct Phase {
             trace->vs + o, trace->la + o);
         ++trace->records;
       }
-      launch_select(st);
-      k_scan<Op, kBlock><<<scan_grid, kBlock, 0, st>>>(a, cudaGraphConditionalHandle{}, 0);
-      MAITER_CUDA(cudaEventRecord(e[2], st));
       MAITER_CUDA(cudaGetLastError());
       MAITER_CUDA(cudaMemcpyAsync(r->h_ctl, r->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
       MAITER_CUDA(cudaStreamSynchronize(st));
       float t1 = 0.f, t2 = 0.f;
       cudaEventElapsedTime(&t1, e[0], e[1]);
       cudaEventElapsedTime(&t2, e[1], e[2]);
-      s.push_ms += t1;
-      s.scan_ms += t2;
+      s.scan_ms += t1;
+      s.push_ms += t2;
       s.push_launches++;
       s.scan_launches++;
       if (r->h_ctl->status != 0) return MAITER_OK;
