@@ -166,7 +166,7 @@ static maiter_status dense_add_init(cudaGraph_t graph, const maiter_batch* b, in
 static DevCtl dense_ctl(const BQuery& Q, const maiter_batch_params* p, double eps) {
   DevCtl c{};
   c.eps = Q.op == 0 ? eps : 0.0;
-  c.eps_eff = c.eps;
+  c.eps_in[0] = c.eps_in[1] = c.eps;
   c.max_rounds = p->max_rounds > 0 ? p->max_rounds : 1000000;
   c.sched = MAITER_SCHED_ALL;
   return c;

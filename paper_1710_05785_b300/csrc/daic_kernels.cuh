@@ -51,15 +51,19 @@ struct DevCtl {
   unsigned long long act_acc[2];   // [set] selected vertices
   unsigned long long push_acc[2];  // [set] sum of out-degrees of selected vertices
   unsigned long long pend_acc[2];  // [set] pending vertices (Delta != 0 / Delta < v)
+  // Decision inputs that change from round to round, per set: the push
+  // reading set s writes set s ^ 1, so no CTA reads a word another CTA of the
+  // same launch writes.
+  unsigned long long rounds_in[2];  // [set] pushes performed before this round
+  double eps_in[2];                 // [set] termination bound of the current phase
   int status;                    // 0 running, 1 converged, 2 round cap hit, 3 overflow
   int sched;                     // maiter_sched
-  unsigned long long rounds;     // pushes performed
+  unsigned long long rounds;     // pushes performed (host-facing copy)
   unsigned long long activations;
   unsigned long long pushes;
   double residual;               // last decided residual
   double tau;                    // current activation threshold (sum ops)
   double eps;                    // termination bound (sum ops)
-  double eps_eff;                // bound of the current phase (set by the first decision)
   double switch_frac;            // > 0: this phase ends at switch_frac x first residual
   long long max_rounds;
   int phase;                     // 1 once the FP32 phase of a mixed run has started
@@ -326,9 +330,12 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a,
     const unsigned long long p0 = ctl->push_acc[0], p1 = ctl->push_acc[1];
     const unsigned long long q0 = ctl->pend_acc[0], q1 = ctl->pend_acc[1];
     const unsigned o0 = ctl->overflow[0], o1 = ctl->overflow[1];
-    const unsigned long long rounds = ctl->rounds;
+    const unsigned long long rn0 = ctl->rounds_in[0], rn1 = ctl->rounds_in[1];
+    const double e0 = ctl->eps_in[0], e1 = ctl->eps_in[1];
     const long long max_rounds = ctl->max_rounds;
-    const double eps = ctl->eps, eps_eff = ctl->eps_eff, switch_frac = ctl->switch_frac;
+    const double eps = ctl->eps, switch_frac = ctl->switch_frac;
+    const unsigned long long rounds = ps ? rn1 : rn0;
+    const double eps_eff = ps ? e1 : e0;
     const uint4 c = ps ? c1 : c0;
     const unsigned long long act = ps ? a1 : a0, psh = ps ? p1 : p0, pend = ps ? q1 : q0;
     const unsigned overflow = ps ? o1 : o0;
@@ -349,8 +356,10 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a,
     else if (static_cast<long long>(rounds) >= max_rounds) status = 2;
     const unsigned cont = status == 0;
     if (blockIdx.x == 0) {
+      const unsigned ns = ps ^ 1u;
       ctl->residual = resid;
-      if (rounds == 0) ctl->eps_eff = eps_now;
+      ctl->rounds_in[ns] = rounds + cont;
+      ctl->eps_in[ns] = eps_now;
       if (cont) {
         ctl->rounds = rounds + 1;
         ctl->activations = ctl->activations + act;
@@ -365,7 +374,6 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a,
         ctl->status = status;
       }
       // the other set starts empty for the next scan
-      const unsigned ns = ps ^ 1u;
       for (int b = 0; b < 4; ++b) ctl->cnt[ns][b] = 0;
       ctl->resid_acc[ns] = 0.0;
       ctl->act_acc[ns] = ctl->push_acc[ns] = ctl->pend_acc[ns] = 0;
@@ -490,9 +498,10 @@ static __global__ void k_to_f32(const double* __restrict__ d64, float* __restric
     ctl->warm_rounds = ctl->rounds;
     ctl->warm_activations = ctl->activations;
     ctl->warm_pushes = ctl->pushes;
-    ctl->eps_eff = ctl->eps;
     ctl->switch_frac = 0.0;
     for (int s = 0; s < 2; ++s) {
+      ctl->rounds_in[s] = ctl->rounds;
+      ctl->eps_in[s] = ctl->eps;
       for (int b = 0; b < 4; ++b) ctl->cnt[s][b] = 0;
       ctl->resid_acc[s] = 0.0;
       ctl->act_acc[s] = ctl->push_acc[s] = ctl->pend_acc[s] = 0;

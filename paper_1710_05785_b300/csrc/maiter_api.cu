@@ -385,7 +385,7 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   DevCtl c{};
   c.tau = (p->sched == MAITER_SCHED_THRESHOLD) ? p->threshold : 0.0;
   c.eps = p->eps;
-  c.eps_eff = p->eps;
+  c.eps_in[0] = c.eps_in[1] = p->eps;
   c.switch_frac = plan.mixed ? p->mixed_switch : 0.0;
   c.max_rounds = p->max_rounds > 0 ? p->max_rounds : 1000000;
   c.sched = p->sched;
