@@ -85,11 +85,18 @@ typedef enum {
   MAITER_SCHED_TOPFRAC = 2,   /* the top_frac fraction of pending vertices by
                                  priority, ties included (priority queue of
                                  Section 5.1) */
-  MAITER_SCHED_LEARNED = 3    /* the top_frac fraction of pending vertices by the
+  MAITER_SCHED_LEARNED = 3,   /* the top_frac fraction of pending vertices by the
                                  score of a learned network (params.scorer, a
                                  maiter_mlp); every 8th round activates every
                                  pending vertex, so none can starve (Theorem 3
                                  needs every vertex updated again eventually) */
+  MAITER_SCHED_BUCKET = 4     /* min only, distance-ordered (delta-stepping): the
+                                 pending vertices with Delta_j < tau, where tau starts
+                                 at the bucket width `threshold` and, whenever no
+                                 pending vertex lies below it, moves to the smallest
+                                 pending Delta plus the width (priority by distance,
+                                 the ordered variant of the SSSP priority of
+                                 Section 4.1); same fixed point */
 } maiter_sched;
 
 typedef struct maiter_mlp maiter_mlp;       /* opaque: learned priority scorer */
@@ -141,7 +148,8 @@ typedef struct maiter_run_params {
   double threshold;    /* THRESHOLD: activate |Delta_j| > threshold.  When a
                           round selects nothing while the residual is still
                           >= eps, the threshold is divided by 10 (down to 0) so
-                          every run terminates. */
+                          every run terminates.  BUCKET: the bucket width (> 0,
+                          at least 1 is meaningful for integer distances). */
   double top_frac;     /* TOPFRAC: fraction q in (0, 1] */
   double eps;          /* sums: stop when sum_j |Delta_j| < eps (FP64 reduction) */
   double mixed_switch; /* SUM_MIXED: deltas are FP64 until the residual has

@@ -32,7 +32,7 @@ _STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CON
 # maiter_op / maiter_g / maiter_sched / maiter_engine
 OP_SUM_F64, OP_SUM_MIXED, OP_MIN_U32 = 0, 1, 2
 G_SCALE_BY_SRC, G_ADD_EDGE = 0, 1
-SCHED_ALL, SCHED_THRESHOLD, SCHED_TOPFRAC, SCHED_LEARNED = 0, 1, 2, 3
+SCHED_ALL, SCHED_THRESHOLD, SCHED_TOPFRAC, SCHED_LEARNED, SCHED_BUCKET = 0, 1, 2, 3, 4
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 8, 64, 641
 ENGINE_SYNC, ENGINE_ASYNC = 0, 1
 FLAG_PROFILE_KERNELS, FLAG_INJECT_STALL = 1, 2

@@ -51,6 +51,7 @@ struct DevCtl {
   unsigned long long act_acc[2];   // [set] selected vertices
   unsigned long long push_acc[2];  // [set] sum of out-degrees of selected vertices
   unsigned long long pend_acc[2];  // [set] pending vertices (Delta != 0 / Delta < v)
+  unsigned int minpend_acc[2];     // [set] min: smallest pending Delta (BUCKET scheduling)
   // Decision inputs that change from round to round, per set: the push
   // reading set s writes set s ^ 1, so no CTA reads a word another CTA of the
   // same launch writes.
@@ -62,7 +63,8 @@ struct DevCtl {
   unsigned long long activations;
   unsigned long long pushes;
   double residual;               // last decided residual
-  double tau;                    // current activation threshold (sum ops)
+  double tau;                    // current activation threshold (sums) / bucket bound (BUCKET)
+  double bucket_width;           // BUCKET: width of a distance bucket
   double eps;                    // termination bound (sum ops)
   double switch_frac;            // > 0: this phase ends at switch_frac x first residual
   long long max_rounds;
@@ -118,6 +120,7 @@ struct KArgs {
   unsigned* last_act;            // non-null: round of each vertex's last update (1-based)
   int cut_warp;                  // deg <  cut_warp : small bucket
   int cut_cta;                   // deg >= cut_cta  : large bucket (chunked)
+  int bucket;                    // min: distance-ordered selection (Delta_j < tau)
 };
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -157,6 +160,8 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
 
   double rsum = 0.0;
   unsigned long long nact = 0, npush = 0, npend = 0;
+  unsigned dmin = kInfU32;                   // min: smallest pending Delta seen
+  const bool bucket = !Op::kIsSum && a.bucket;
   __shared__ int s_woff[3][kWarps];          // per-warp exclusive offsets, per bucket
   __shared__ unsigned s_base[3];             // the tile's base position, per bucket
 
@@ -192,7 +197,9 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
         rsum += p;
         s = pend && p > tau;
       } else {
-        s = pend;
+        // BUCKET: only pending distances below the bucket bound tau
+        s = pend && (!bucket || static_cast<double>(dd[u]) < tau);
+        if (pend) dmin = min(dmin, static_cast<unsigned>(dd[u]));
       }
       if (a.topq) s = pend && (a.keys ? a.keys[j] : priority_key<Op>(dd[u], vv[u])) >= key_thr;
       sel[u] = s;
@@ -271,20 +278,26 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
   // push reads the totals after this kernel ends.
   __shared__ double s_r[BLOCK / 32];
   __shared__ unsigned long long s_a[BLOCK / 32], s_p[BLOCK / 32], s_q[BLOCK / 32];
+  __shared__ unsigned s_m[BLOCK / 32];
   rsum = warp_sum(rsum);
   nact = warp_sum(nact);
   npush = warp_sum(npush);
   npend = warp_sum(npend);
-  if (lane == 0) { s_r[wid] = rsum; s_a[wid] = nact; s_p[wid] = npush; s_q[wid] = npend; }
+  if (bucket) dmin = __reduce_min_sync(0xffffffffu, dmin);
+  if (lane == 0) { s_r[wid] = rsum; s_a[wid] = nact; s_p[wid] = npush; s_q[wid] = npend; s_m[wid] = dmin; }
   __syncthreads();
   if (threadIdx.x == 0) {
     double r = 0.0;
     unsigned long long x = 0, y = 0, z = 0;
-    for (int i = 0; i < BLOCK / 32; ++i) { r += s_r[i]; x += s_a[i]; y += s_p[i]; z += s_q[i]; }
+    unsigned mn = kInfU32;
+    for (int i = 0; i < BLOCK / 32; ++i) {
+      r += s_r[i]; x += s_a[i]; y += s_p[i]; z += s_q[i]; mn = min(mn, s_m[i]);
+    }
     if (Op::kIsSum && r != 0.0) atomicAdd(&ctl->resid_acc[ws], r);
     if (x) atomicAdd(&ctl->act_acc[ws], x);
     if (y) atomicAdd(&ctl->push_acc[ws], y);
     if (z) atomicAdd(&ctl->pend_acc[ws], z);
+    if (bucket && mn != kInfU32) atomicMin(&ctl->minpend_acc[ws], mn);
     if (blockIdx.x == 0) ctl->push_set = ws;
   }
 }
@@ -370,6 +383,12 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a,
           const double t = ctl->tau;
           ctl->tau = (t < 1e-300) ? 0.0 : t * 0.1;
         }
+        // BUCKET: the bucket below tau is empty; the next one starts at the
+        // smallest pending distance
+        if (!Op::kIsSum && a.bucket && act == 0) {
+          const unsigned mp = ps ? ctl->minpend_acc[1] : ctl->minpend_acc[0];
+          ctl->tau = static_cast<double>(mp) + ctl->bucket_width;
+        }
       } else {
         ctl->status = status;
       }
@@ -378,6 +397,7 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a,
       ctl->resid_acc[ns] = 0.0;
       ctl->act_acc[ns] = ctl->push_acc[ns] = ctl->pend_acc[ns] = 0;
       ctl->overflow[ns] = 0;
+      ctl->minpend_acc[ns] = kInfU32;
       ctl->scan_set = ns;
       if (use_cond) cudaGraphSetConditional(cond, cont);
     }
@@ -506,6 +526,7 @@ static __global__ void k_to_f32(const double* __restrict__ d64, float* __restric
       ctl->resid_acc[s] = 0.0;
       ctl->act_acc[s] = ctl->push_acc[s] = ctl->pend_acc[s] = 0;
       ctl->overflow[s] = 0;
+      ctl->minpend_acc[s] = kInfU32;
     }
     ctl->scan_set = 0;
     ctl->push_set = 0;

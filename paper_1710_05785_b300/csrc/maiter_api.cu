@@ -301,7 +301,10 @@ static maiter_status setup_plan(const maiter_graph* g, const maiter_run_params* 
       plan->warm.setup(g, r, r->delta_wide, coef, p->damping, tu, topq, W, track);
       plan->f32.setup(g, r, r->delta, coef, p->damping, tu, topq, W, track);
       break;
-    default: plan->umin.setup(g, r, r->delta, nullptr, 0.0, tu, topq, W, track); break;
+    default:
+      plan->umin.setup(g, r, r->delta, nullptr, 0.0, tu, topq, W, track);
+      plan->umin.a.bucket = p->sched == MAITER_SCHED_BUCKET;
+      break;
   }
   return MAITER_OK;
 }
@@ -383,7 +386,10 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
     r->exec_key = key;
   }
   DevCtl c{};
-  c.tau = (p->sched == MAITER_SCHED_THRESHOLD) ? p->threshold : 0.0;
+  c.tau = (p->sched == MAITER_SCHED_THRESHOLD || p->sched == MAITER_SCHED_BUCKET) ? p->threshold
+                                                                                : 0.0;
+  c.minpend_acc[0] = c.minpend_acc[1] = kInfU32;
+  c.bucket_width = (p->sched == MAITER_SCHED_BUCKET) ? p->threshold : 0.0;
   c.eps = p->eps;
   c.eps_in[0] = c.eps_in[1] = p->eps;
   c.switch_frac = plan.mixed ? p->mixed_switch : 0.0;
@@ -533,8 +539,17 @@ static maiter_status run_impl(const maiter_graph* g, const maiter_run_params* p,
   MAITER_REQUIRE(g && p && out, "maiter_run: NULL argument");
   MAITER_REQUIRE(p->op >= MAITER_OP_SUM_F64 && p->op <= MAITER_OP_MIN_U32, "unknown op %d", p->op);
   const bool is_sum = p->op != MAITER_OP_MIN_U32;
-  MAITER_REQUIRE(p->sched >= MAITER_SCHED_ALL && p->sched <= MAITER_SCHED_LEARNED,
+  MAITER_REQUIRE(p->sched >= MAITER_SCHED_ALL && p->sched <= MAITER_SCHED_BUCKET,
                  "unknown sched %d", p->sched);
+  if (p->sched == MAITER_SCHED_BUCKET) {
+    MAITER_REQUIRE(!is_sum, "BUCKET scheduling orders distances: min only");
+    MAITER_REQUIRE(std::isfinite(p->threshold) && p->threshold > 0.0,
+                   "BUCKET scheduling needs a bucket width threshold > 0");
+    if (p->engine != MAITER_ENGINE_SYNC) {
+      set_error("BUCKET scheduling runs on the round engine");
+      return MAITER_ERR_UNSUPPORTED;
+    }
+  }
   if (p->sched == MAITER_SCHED_LEARNED) {
     MAITER_REQUIRE(p->scorer, "LEARNED scheduling needs params.scorer");
     MAITER_REQUIRE(mlp_device(p->scorer) == g->device, "the scorer lives on another device");

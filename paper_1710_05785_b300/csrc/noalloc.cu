@@ -24,7 +24,7 @@ namespace maiter {
 namespace {
 
 constexpr int64_t kNoallocMaxN = int64_t(1) << 20;   // vertices
-constexpr size_t kCtlBytes = 256;
+constexpr size_t kCtlBytes = 512;
 constexpr int kNoallocLists = 3;   // small and medium lists, plus one spare list slot
 constexpr size_t kScratchBytes = kCtlBytes + sizeof(int) * kNoallocLists * size_t(kNoallocMaxN);
 // slot layout: [DevCtl | ... | validation flag (last 4 bytes)]
