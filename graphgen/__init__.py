@@ -36,7 +36,7 @@ def build(force: bool = False) -> str:
     """Compile ``rmat.c`` into ``libgraphgen.so`` (gcc, OpenMP)."""
     src = os.path.join(_HERE, "rmat.c")
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
-        subprocess.check_call(["gcc", "-O3", "-fopenmp", "-fPIC", "-shared", "-o", _SO, src])
+        subprocess.check_call(["gcc", "-O3", "-fopenmp", "-fPIC", "-shared", "-o", _SO, src, "-lm"])
     return _SO
 
 
@@ -57,6 +57,10 @@ def _load():
         lib.gg_uniform01.argtypes = [i64, u64, u64, P]
         lib.gg_draw.argtypes = [u64, u64]
         lib.gg_draw.restype = u64
+        lib.gg_lognormal_indegrees.argtypes = [i64, u64, d, d, i64, P]
+        lib.gg_lognormal_indegrees.restype = i64
+        lib.gg_lognormal_edges.argtypes = [i64, u64, P, P, P]
+        lib.gg_lognormal_weights.argtypes = [i64, u64, d, d, P]
         lib.gg_stream_key.argtypes = [u64, u64]
         lib.gg_stream_key.restype = u64
         _lib = lib
@@ -135,6 +139,38 @@ def rmat(scale: int, edge_factor: int, seed: int | None = None, weights: bool = 
     w = uniform_weights(src.shape[0], seed) if weights else None
     perm = permutation(n, seed) if permute else None
     return csr_from_edges(n, src, dst, w, perm, name=f"rmat{scale}-ef{edge_factor}-s{seed}")
+
+
+def lognormal(n: int, seed: int | None = None, mu: float = -0.5, sigma: float = 2.3,
+              weights: bool = False, wmu: float = 0.0, wsigma: float = 1.0,
+              cap: int | None = None) -> CSRGraph:
+    """The paper's synthetic graphs (Section 6.1): each vertex's in-degree is
+    round(exp(N(mu, sigma))) (capped at ``cap``, default n), its in-neighbours
+    uniform vertex ids drawn with replacement.  With ``weights``, each edge
+    gets an IEEE single weight exp(N(wmu, wsigma)) (the paper's SSSP graphs use
+    (0, 1)), stored in ``w`` as its uint32 bit pattern (``float_weights(g)``
+    reads it back).  Canonical CSR of out-edges, no relabelling."""
+    lib = _load()
+    if seed is None:
+        seed = DEFAULT_SEED_BASE + 2000 + int(np.log2(max(n, 1)))
+    deg = np.empty(n, dtype=np.int64)
+    m = int(lib.gg_lognormal_indegrees(n, seed, mu, sigma, int(cap if cap is not None else n),
+                                       _ptr(deg)))
+    offs = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(deg, out=offs[1:])
+    src = np.empty(m, dtype=np.int32)
+    dst = np.empty(m, dtype=np.int32)
+    lib.gg_lognormal_edges(n, seed, _ptr(offs), _ptr(src), _ptr(dst))
+    w = None
+    if weights:
+        w = np.empty(m, dtype=np.uint32)
+        lib.gg_lognormal_weights(m, seed, wmu, wsigma, _ptr(w))
+    return csr_from_edges(n, src, dst, w, None, name=f"lognormal-n{n}-s{seed}")
+
+
+def float_weights(g: CSRGraph) -> np.ndarray:
+    """The float32 view of a graph whose ``w`` holds IEEE single bit patterns."""
+    return g.w.view(np.float32)
 
 
 def pick(candidates: np.ndarray, k: int, seed: int, stream: int = 0) -> np.ndarray:

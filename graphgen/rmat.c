@@ -45,7 +45,7 @@ static inline uint64_t bounded(uint64_t r, uint64_t bound) {
 }
 
 enum { STREAM_EDGES = 0, STREAM_PERM = 1, STREAM_WEIGHTS = 2, STREAM_SOURCES = 3,
-       STREAM_LOGNORMAL = 4 };
+       STREAM_LOGNORMAL = 4, STREAM_LN_DEGREE = 5, STREAM_LN_SOURCE = 6, STREAM_LN_WEIGHT = 7 };
 
 /* Fill perm[0..n) with a seeded uniform permutation (Fisher-Yates, Durstenfeld). */
 void gg_permutation(int64_t n, uint64_t seed, int32_t* perm) {
@@ -165,4 +165,60 @@ void gg_uniform01(int64_t count, uint64_t seed, uint64_t stream, double* out) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < count; ++i)
     out[i] = (double)(gg_draw(key, (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/*
+ * Log-normal synthetic graphs of the paper's evaluation (Section 6.1): the
+ * in-degree of every vertex is drawn from a log-normal distribution
+ * LN(mu, sigma) and rounded to the nearest integer (capped at cap), and each
+ * in-edge's source is a uniform vertex id (with replacement).  Edge weights,
+ * when asked for, are LN(wmu, wsigma) rounded to IEEE single.
+ *
+ * Standard normal deviates by the Box-Muller transform (Box and Muller, Ann.
+ * Math. Stat. 1958) from two 53-bit uniforms of the same counter; u1 lies in
+ * (0, 1] so its logarithm is finite.
+ */
+static inline double normal01(uint64_t key, uint64_t counter) {
+  const double u1 = (double)((gg_draw(key, 2 * counter) >> 11) + 1) * (1.0 / 9007199254740992.0);
+  const double u2 = (double)(gg_draw(key, 2 * counter + 1) >> 11) * (1.0 / 9007199254740992.0);
+  return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+/* In-degrees deg[0..n); returns their sum m. */
+int64_t gg_lognormal_indegrees(int64_t n, uint64_t seed, double mu, double sigma, int64_t cap,
+                               int64_t* deg) {
+  const uint64_t key = gg_stream_key(seed, STREAM_LN_DEGREE);
+  int64_t m = 0;
+#pragma omp parallel for schedule(static) reduction(+ : m)
+  for (int64_t k = 0; k < n; ++k) {
+    double d = floor(exp(mu + sigma * normal01(key, (uint64_t)k)) + 0.5);
+    if (d > (double)cap) d = (double)cap;
+    deg[k] = (int64_t)d;
+    m += deg[k];
+  }
+  return m;
+}
+
+/* Edges of target k at [offs[k], offs[k+1]): dst = k, src uniform in [0, n). */
+void gg_lognormal_edges(int64_t n, uint64_t seed, const int64_t* offs, int32_t* src,
+                        int32_t* dst) {
+  const uint64_t key = gg_stream_key(seed, STREAM_LN_SOURCE);
+#pragma omp parallel for schedule(dynamic, 4096)
+  for (int64_t k = 0; k < n; ++k)
+    for (int64_t e = offs[k]; e < offs[k + 1]; ++e) {
+      src[e] = (int32_t)bounded(gg_draw(key, (uint64_t)e), (uint64_t)n);
+      dst[e] = (int32_t)k;
+    }
+}
+
+/* Float weights LN(mu, sigma), one per edge index, as IEEE single bit patterns. */
+void gg_lognormal_weights(int64_t m, uint64_t seed, double mu, double sigma, uint32_t* w) {
+  const uint64_t key = gg_stream_key(seed, STREAM_LN_WEIGHT);
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < m; ++e) {
+    float f = (float)exp(mu + sigma * normal01(key, (uint64_t)e));
+    uint32_t bits;
+    memcpy(&bits, &f, sizeof(bits));
+    w[e] = bits;
+  }
 }

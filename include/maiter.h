@@ -65,7 +65,13 @@ typedef enum {
   MAITER_OP_SUM_MIXED = 1, /* (+) = +; Delta and coefficients FP32, v and the
                               residual reduction FP64 (after an FP64-delta
                               warm-up phase, see mixed_switch) */
-  MAITER_OP_MIN_U32 = 2    /* (+) = min over uint32, identity UINT32_MAX (inf) */
+  MAITER_OP_MIN_U32 = 2,   /* (+) = min over uint32, identity UINT32_MAX (inf) */
+  MAITER_OP_MIN_F32 = 3    /* (+) = min over IEEE float32 distances >= 0, identity
+                              +inf; the graph's 32-bit weights are read as floats
+                              (finite, >= 0: checked once per graph), messages are
+                              fl(Delta_j + w) rounded to nearest.  v and Delta are
+                              returned as float32.  Round engine, schedules ALL,
+                              THRESHOLD (as ALL), TOPFRAC and BUCKET. */
 } maiter_op;
 
 /* The message function g_{j,k}. */

@@ -51,6 +51,9 @@ def _load():
         lib.or_dijkstra.argtypes = [i64, P, P, P, ctypes.c_int32, P]
         lib.or_dijkstra.restype = i32
         lib.or_bellman_ford.argtypes = [i64, P, P, P, ctypes.c_int32, P]
+        lib.or_dijkstra_f32.argtypes = [i64, P, P, P, ctypes.c_int32, P]
+        lib.or_dijkstra_f32.restype = i32
+        lib.or_bellman_ford_f32.argtypes = [i64, P, P, P, ctypes.c_int32, P]
         _lib = lib
     return _lib
 
@@ -202,6 +205,32 @@ def bellman_ford(g, source: int) -> np.ndarray:
     w = np.ascontiguousarray(g.w, dtype=np.uint32)
     out = np.empty(g.n, dtype=np.uint32)
     _load().or_bellman_ford(g.n, _p(rp), _p(col), _p(w), int(source), _p(out))
+    return out
+
+
+def _float_weights(g) -> np.ndarray:
+    w = np.asarray(g.w)
+    return np.ascontiguousarray(w.view(np.float32) if w.dtype == np.uint32 else w,
+                                dtype=np.float32)
+
+
+def dijkstra_f32(g, source: int) -> np.ndarray:
+    """Shortest distances over float weights (float32, +inf if unreachable),
+    every distance formed as fl(d + w) in single precision.  ``g.w`` holds the
+    weights as float32 or as their uint32 bit patterns."""
+    rp, col = _csr(g)
+    w = _float_weights(g)
+    out = np.empty(g.n, dtype=np.float32)
+    if _load().or_dijkstra_f32(g.n, _p(rp), _p(col), _p(w), int(source), _p(out)) != 0:
+        raise MemoryError("or_dijkstra_f32")
+    return out
+
+
+def bellman_ford_f32(g, source: int) -> np.ndarray:
+    rp, col = _csr(g)
+    w = _float_weights(g)
+    out = np.empty(g.n, dtype=np.float32)
+    _load().or_bellman_ford_f32(g.n, _p(rp), _p(col), _p(w), int(source), _p(out))
     return out
 
 

@@ -16,6 +16,10 @@
  *   or_daic_min        - asynchronous DAIC with min (SSSP row of Table 1).
  *   or_dijkstra        - textbook single-source shortest paths (binary heap).
  *   or_bellman_ford    - brute-force relaxation to a fixed point (tiny inputs).
+ *   or_dijkstra_f32 / or_bellman_ford_f32 - the same with IEEE single
+ *                        weights and distances (the paper's float-weighted
+ *                        synthetic SSSP graphs, Section 6.1): every tentative
+ *                        distance is fl(d_j + w_jk), rounded to nearest.
  *
  * Conventions: CSR of out-edges, row_ptr[n+1] int64, col[m] int32,
  * per-source coefficient coef[j] (so g_{j,k}(x) = coef[j] * x), integer
@@ -399,6 +403,67 @@ void or_bellman_ford(int64_t n, const int64_t* row_ptr, const int32_t* col, cons
       for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
         uint64_t nd = (uint64_t)dist[i] + w[e];
         if (nd < dist[col[e]]) { dist[col[e]] = (uint32_t)nd; changed = 1; }
+      }
+    }
+    if (!changed) break;
+  }
+}
+
+/* ------------------------------------------------- float shortest paths */
+
+/*
+ * Dijkstra's algorithm on float weights w (IEEE single, finite, >= 0), every
+ * distance formed in single precision as fl(dist[j] + w[e]) (C float
+ * addition, round to nearest).  With w >= 0, fl(d + w) >= d, so a vertex's
+ * distance is final when it leaves the heap, exactly as with exact
+ * arithmetic; the result is the least, over paths from src, of the path's
+ * sum accumulated from the source in single precision.  Unreachable: +inf.
+ * Heap keys are the distances' bit patterns (ordered like the values for
+ * non-negative floats).  Returns 0, or -1 on allocation failure.
+ */
+static uint32_t f2u(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+
+int or_dijkstra_f32(int64_t n, const int64_t* row_ptr, const int32_t* col, const float* w,
+                    int32_t src, float* dist) {
+  int64_t m = row_ptr[n];
+  char* done = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+  hitem* h = (hitem*)malloc((size_t)(m + 2) * sizeof(hitem));
+  if (!done || !h) { free(done); free(h); return -1; }
+  for (int64_t j = 0; j < n; ++j) dist[j] = INFINITY;
+  int64_t sz = 0;
+  dist[src] = 0.0f;
+  hitem s0 = {0, src};
+  hpush(h, &sz, s0);
+  while (sz > 0) {
+    hitem t = hpop(h, &sz);
+    if (done[t.v]) continue;
+    done[t.v] = 1;
+    for (int64_t e = row_ptr[t.v]; e < row_ptr[t.v + 1]; ++e) {
+      float nd = dist[t.v] + w[e];
+      int32_t k = col[e];
+      if (nd < dist[k]) {
+        dist[k] = nd;
+        hitem x = {f2u(nd), k};
+        hpush(h, &sz, x);
+      }
+    }
+  }
+  free(done); free(h);
+  return 0;
+}
+
+/* Float Bellman-Ford: relax every edge in single precision until nothing changes. */
+void or_bellman_ford_f32(int64_t n, const int64_t* row_ptr, const int32_t* col, const float* w,
+                         int32_t src, float* dist) {
+  for (int64_t j = 0; j < n; ++j) dist[j] = INFINITY;
+  dist[src] = 0.0f;
+  for (int64_t pass = 0; pass < n; ++pass) {
+    int changed = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (isinf(dist[i])) continue;
+      for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        float nd = dist[i] + w[e];
+        if (nd < dist[col[e]]) { dist[col[e]] = nd; changed = 1; }
       }
     }
     if (!changed) break;

@@ -30,7 +30,7 @@ _STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CON
                  -5: "TIMEOUT", -6: "UNSUPPORTED"}
 
 # maiter_op / maiter_g / maiter_sched / maiter_engine
-OP_SUM_F64, OP_SUM_MIXED, OP_MIN_U32 = 0, 1, 2
+OP_SUM_F64, OP_SUM_MIXED, OP_MIN_U32, OP_MIN_F32 = 0, 1, 2, 3
 G_SCALE_BY_SRC, G_ADD_EDGE = 0, 1
 SCHED_ALL, SCHED_THRESHOLD, SCHED_TOPFRAC, SCHED_LEARNED, SCHED_BUCKET = 0, 1, 2, 3, 4
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 8, 64, 641
@@ -39,9 +39,12 @@ FLAG_PROFILE_KERNELS, FLAG_INJECT_STALL = 1, 2
 
 INF32 = 0xFFFFFFFF
 
-_STATE_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float64, OP_MIN_U32: np.uint32}
-_DELTA_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float32, OP_MIN_U32: np.uint32}
-_DELTA0_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float64, OP_MIN_U32: np.uint32}
+_STATE_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float64, OP_MIN_U32: np.uint32,
+                OP_MIN_F32: np.float32}
+_DELTA_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float32, OP_MIN_U32: np.uint32,
+                OP_MIN_F32: np.float32}
+_DELTA0_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float64, OP_MIN_U32: np.uint32,
+                 OP_MIN_F32: np.float32}
 _COEF_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float32}
 
 
@@ -205,7 +208,9 @@ class Graph:
             row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
         if isinstance(col, np.ndarray) or isinstance(col, (list, tuple)):
             col = np.ascontiguousarray(col, dtype=np.int32)
-        if w is not None and (isinstance(w, np.ndarray) or isinstance(w, (list, tuple))):
+        if isinstance(w, np.ndarray) and w.dtype == np.float32:
+            w = np.ascontiguousarray(w).view(np.uint32)   # float weights travel as their bits
+        elif w is not None and (isinstance(w, np.ndarray) or isinstance(w, (list, tuple))):
             w = np.ascontiguousarray(w, dtype=np.uint32)
         m = int(len(col))
         h = ctypes.c_void_p()
@@ -283,7 +288,7 @@ def run(graph: Graph, op: int = OP_SUM_F64, *, coef=None, damping: float = 0.8, 
     n = graph.n
     p = params_default()
     p.op = op
-    p.g = G_ADD_EDGE if op == OP_MIN_U32 else G_SCALE_BY_SRC
+    p.g = G_ADD_EDGE if op in (OP_MIN_U32, OP_MIN_F32) else G_SCALE_BY_SRC
     p.sched, p.engine, p.flags = sched, engine, flags
     keep = []
     if coef is not None:
@@ -468,7 +473,7 @@ def trace(graph: Graph, op: int, sample, max_records: int, **run_kwargs):
     la = np.empty((max_records, ns), dtype=np.uint32)
     p = params_default()
     p.op = op
-    p.g = G_ADD_EDGE if op == OP_MIN_U32 else G_SCALE_BY_SRC
+    p.g = G_ADD_EDGE if op in (OP_MIN_U32, OP_MIN_F32) else G_SCALE_BY_SRC
     for k, v in run_kwargs.items():
         setattr(p, k, v)
     rec = ctypes.c_int32(0)

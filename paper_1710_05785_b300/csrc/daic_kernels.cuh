@@ -96,9 +96,16 @@ __device__ __forceinline__ unsigned priority_key(typename Op::D d, typename Op::
     return __float_as_uint(fabsf(static_cast<float>(d)));
   } else {
     if (!(d < v)) return 0u;
-    if (v == kInfU32) return 0x7F800000u;
-    return __float_as_uint(static_cast<float>(v - d));
+    if (v == Op::kNone) return 0x7F800000u;
+    return __float_as_uint(static_cast<float>(Op::value(v) - Op::value(d)));
   }
+}
+
+// The distance a min operator's bit pattern stands for (0 for sums).
+template <class Op, class T>
+__device__ __forceinline__ double min_value(T x) {
+  if constexpr (Op::kIsSum) return 0.0;
+  else return Op::value(static_cast<typename Op::D>(x));
 }
 
 template <class Op>
@@ -160,7 +167,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
 
   double rsum = 0.0;
   unsigned long long nact = 0, npush = 0, npend = 0;
-  unsigned dmin = kInfU32;                   // min: smallest pending Delta seen
+  unsigned dmin = 0xFFFFFFFFu;               // min: smallest pending Delta seen (bits)
   const bool bucket = !Op::kIsSum && a.bucket;
   __shared__ int s_woff[3][kWarps];          // per-warp exclusive offsets, per bucket
   __shared__ unsigned s_base[3];             // the tile's base position, per bucket
@@ -175,7 +182,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
     // Three dependent stages, each with all of the thread's loads in flight
     // at once: (1) Delta and v of every item, (2) the selection, (3) the row
     // offsets of the selected items.
-    constexpr D kNone = Op::kIsSum ? D(0) : D(kInfU32);   // "nothing pending"
+    constexpr D kNone = Op::kNone;   // "nothing pending"
     D dd[kItems];
     typename Op::V vv[kItems];
     bool sel[kItems];
@@ -184,7 +191,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
       const int j = tile + u * BLOCK + static_cast<int>(threadIdx.x);
       const bool in = j < a.n;
       dd[u] = in ? a.delta[j] : kNone;
-      vv[u] = Op::kIsSum ? typename Op::V(0) : (in ? a.v[j] : typename Op::V(kInfU32));
+      vv[u] = Op::kIsSum ? typename Op::V(0) : (in ? a.v[j] : typename Op::V(Op::kNone));
     }
 #pragma unroll
     for (int u = 0; u < kItems; ++u) {
@@ -198,7 +205,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
         s = pend && p > tau;
       } else {
         // BUCKET: only pending distances below the bucket bound tau
-        s = pend && (!bucket || static_cast<double>(dd[u]) < tau);
+        s = pend && (!bucket || min_value<Op>(dd[u]) < tau);
         if (pend) dmin = min(dmin, static_cast<unsigned>(dd[u]));
       }
       if (a.topq) s = pend && (a.keys ? a.keys[j] : priority_key<Op>(dd[u], vv[u])) >= key_thr;
@@ -289,7 +296,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
   if (threadIdx.x == 0) {
     double r = 0.0;
     unsigned long long x = 0, y = 0, z = 0;
-    unsigned mn = kInfU32;
+    unsigned mn = 0xFFFFFFFFu;
     for (int i = 0; i < BLOCK / 32; ++i) {
       r += s_r[i]; x += s_a[i]; y += s_p[i]; z += s_q[i]; mn = min(mn, s_m[i]);
     }
@@ -297,7 +304,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
     if (x) atomicAdd(&ctl->act_acc[ws], x);
     if (y) atomicAdd(&ctl->push_acc[ws], y);
     if (z) atomicAdd(&ctl->pend_acc[ws], z);
-    if (bucket && mn != kInfU32) atomicMin(&ctl->minpend_acc[ws], mn);
+    if (bucket && mn != 0xFFFFFFFFu) atomicMin(&ctl->minpend_acc[ws], mn);
     if (blockIdx.x == 0) ctl->push_set = ws;
   }
 }
@@ -387,7 +394,7 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a,
         // smallest pending distance
         if (!Op::kIsSum && a.bucket && act == 0) {
           const unsigned mp = ps ? ctl->minpend_acc[1] : ctl->minpend_acc[0];
-          ctl->tau = static_cast<double>(mp) + ctl->bucket_width;
+          ctl->tau = min_value<Op>(mp) + ctl->bucket_width;
         }
       } else {
         ctl->status = status;
@@ -397,7 +404,7 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a,
       ctl->resid_acc[ns] = 0.0;
       ctl->act_acc[ns] = ctl->push_acc[ns] = ctl->pend_acc[ns] = 0;
       ctl->overflow[ns] = 0;
-      ctl->minpend_acc[ns] = kInfU32;
+      ctl->minpend_acc[ns] = 0xFFFFFFFFu;
       ctl->scan_set = ns;
       if (use_cond) cudaGraphSetConditional(cond, cont);
     }
@@ -526,7 +533,7 @@ static __global__ void k_to_f32(const double* __restrict__ d64, float* __restric
       ctl->resid_acc[s] = 0.0;
       ctl->act_acc[s] = ctl->push_acc[s] = ctl->pend_acc[s] = 0;
       ctl->overflow[s] = 0;
-      ctl->minpend_acc[s] = kInfU32;
+      ctl->minpend_acc[s] = 0xFFFFFFFFu;
     }
     ctl->scan_set = 0;
     ctl->push_set = 0;

@@ -39,6 +39,7 @@ struct OpSum {
   using C = CT;
   using Msg = DT;
   static constexpr bool kIsSum = true;
+  static constexpr DT kNone = DT(0);   // "nothing pending"
 
   // Pending-priority |v_j (+) Delta_j - v_j| = |Delta_j| (Section 3.5).
   __device__ static __forceinline__ double priority(D d, V) { return fabs(static_cast<double>(d)); }
@@ -105,6 +106,8 @@ struct OpMinU32 {
   using C = float;  // unused
   using Msg = uint32_t;
   static constexpr bool kIsSum = false;
+  static constexpr uint32_t kNone = kInfU32;   // infinity: identity of min, nothing pending
+  __device__ static __forceinline__ double value(uint32_t x) { return static_cast<double>(x); }
 
   __device__ static __forceinline__ double priority(D d, V v) {
     return d < v ? static_cast<double>(v - d) : 0.0;
@@ -136,6 +139,61 @@ struct OpMinU32 {
   __device__ static __forceinline__ void apply(Edge ed, Msg m, D* delta) {
     const uint32_t s = m + ed.w;
     const uint32_t nd = (s < m) ? kInfU32 : s;  // saturate: an overflowing message is infinity
+    if (nd < __ldcg(delta + ed.k)) atomicMin(delta + ed.k, nd);
+  }
+  __device__ static __forceinline__ void scatter(const EdgeCtx& g, int64_t e, Msg m, D* delta) {
+    apply(load(g, e), m, delta);
+  }
+};
+
+// ------------------------------------------- min over float32 (SSSP, FP32)
+// The same operator on non-negative IEEE single distances and weights (the
+// float weights of the paper's synthetic SSSP graphs, Section 6.1).  v and
+// Delta hold the bit patterns: for non-negative floats the unsigned order of
+// the bits is the order of the values, so the unsigned atomicMin is the float
+// min and every pending test is a bit comparison.  Infinity is +inf
+// (0x7F800000); a message is fl(Delta_j + w_jk) with IEEE round-to-nearest,
+// and an overflowing sum is +inf, i.e. no message.  Rounded addition is
+// monotone, so the fixed point is, for every vertex, the least over paths of
+// the path's sum accumulated from the source in this rounding.
+struct OpMinF32 {
+  using V = uint32_t;
+  using D = uint32_t;
+  using C = float;  // unused
+  using Msg = uint32_t;
+  static constexpr bool kIsSum = false;
+  static constexpr uint32_t kNone = 0x7F800000u;   // +inf
+  __device__ static __forceinline__ double value(uint32_t x) {
+    return static_cast<double>(__uint_as_float(x));
+  }
+
+  __device__ static __forceinline__ double priority(D d, V v) {
+    return d < v ? value(v) - value(d) : 0.0;
+  }
+  __device__ static __forceinline__ bool pending(D d, V v) { return d < v; }
+
+  __device__ static __forceinline__ Msg fold(int j, int, D* delta, V* v, const C*, double) {
+    const uint32_t d = __ldcg(delta + j);
+    const uint32_t cur = v[j];
+    if (d >= cur) return kNone;
+    v[j] = d;
+    return d;
+  }
+  __device__ static __forceinline__ D take(int j, D* delta, const V*) { return __ldcg(delta + j); }
+  __device__ static __forceinline__ void untake(int, D, D*) {}
+  __device__ static __forceinline__ Msg finish(int j, int, D d, V* v, const C*, double,
+                                               bool first_chunk) {
+    if (first_chunk && d < v[j]) v[j] = d;
+    return d;
+  }
+
+  __device__ static __forceinline__ bool live(Msg m) { return m != kNone; }
+  struct Edge { int k; uint32_t w; };
+  __device__ static __forceinline__ Edge load(const EdgeCtx& g, int64_t e) {
+    return Edge{__ldg(g.col + e), __ldg(g.w + e)};
+  }
+  __device__ static __forceinline__ void apply(Edge ed, Msg m, D* delta) {
+    const uint32_t nd = __float_as_uint(__fadd_rn(__uint_as_float(m), __uint_as_float(ed.w)));
     if (nd < __ldcg(delta + ed.k)) atomicMin(delta + ed.k, nd);
   }
   __device__ static __forceinline__ void scatter(const EdgeCtx& g, int64_t e, Msg m, D* delta) {

@@ -67,6 +67,7 @@ struct maiter_graph {
   int* col = nullptr;          // m targets
   uint32_t* w = nullptr;       // m weights or null
   int* indeg = nullptr;        // in-degrees (computed on first use by the learned scorer)
+  int wf32 = 0;                // w read as float: 0 unchecked, 1 finite and >= 0, 2 not
   int num_sms = 0;
 };
 

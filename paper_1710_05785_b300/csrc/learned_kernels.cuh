@@ -31,8 +31,8 @@ __device__ __forceinline__ void features_of(const KArgs<Op>& a, const int* __res
     vertex_features<true>(static_cast<double>(d), static_cast<double>(vv), true, true, indeg[j], deg,
                           age, static_cast<double>(a.n), f);
   } else {
-    vertex_features<false>(static_cast<double>(d), static_cast<double>(vv), d != kInfU32,
-                           vv != kInfU32, indeg[j], deg, age, static_cast<double>(a.n), f);
+    vertex_features<false>(Op::value(d), Op::value(vv), d != Op::kNone, vv != Op::kNone,
+                           indeg[j], deg, age, static_cast<double>(a.n), f);
   }
 }
 

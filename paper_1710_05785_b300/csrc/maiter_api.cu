@@ -212,7 +212,8 @@ void maiter_result_destroy(maiter_result* r) {
 
 namespace maiter {
 
-static size_t state_bytes(int op) { return op == MAITER_OP_MIN_U32 ? 4 : 8; }
+static bool is_min_op(int op) { return op == MAITER_OP_MIN_U32 || op == MAITER_OP_MIN_F32; }
+static size_t state_bytes(int op) { return is_min_op(op) ? 4 : 8; }
 static size_t delta_bytes(int op) { return op == MAITER_OP_SUM_F64 ? 8 : 4; }
 static size_t coef_bytes(int op) { return op == MAITER_OP_SUM_F64 ? 8 : 4; }
 
@@ -262,7 +263,35 @@ struct RunPlan {
   Phase<OpSumWarm> warm;
   Phase<OpSumMixed> f32;
   Phase<OpMinU32> umin;
+  Phase<OpMinF32> fmin;
 };
+
+// Float weights must be finite and >= 0 (sign bit clear, exponent not all
+// ones); checked once per graph, on the first float-distance run.
+static __global__ void k_check_f32(const uint32_t* __restrict__ w, int64_t m, unsigned* bad) {
+  unsigned b = 0;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < m;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    b |= (w[e] >= 0x7F800000u) ? 1u : 0u;   // negative, +-inf or NaN
+  if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1u);
+}
+
+static maiter_status check_float_weights(const maiter_graph* g) {
+  maiter_graph* mg = const_cast<maiter_graph*>(g);
+  if (mg->wf32 == 0) {
+    unsigned* bad = nullptr;
+    MAITER_CUDA(cudaMalloc(&bad, sizeof(unsigned)));
+    MAITER_CUDA(cudaMemset(bad, 0, sizeof(unsigned)));
+    k_check_f32<<<g->num_sms * 4, 256>>>(g->w, g->m, bad);
+    unsigned h = 0;
+    cudaError_t e = cudaMemcpy(&h, bad, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    cudaFree(bad);
+    MAITER_CUDA(e);
+    mg->wf32 = h ? 2 : 1;
+  }
+  MAITER_REQUIRE(mg->wf32 == 1, "float weights must be finite and >= 0");
+  return MAITER_OK;
+}
 
 // In-degrees of a graph (computed once, kept with the graph).
 static maiter_status ensure_indegree(const maiter_graph* g) {
@@ -301,6 +330,10 @@ static maiter_status setup_plan(const maiter_graph* g, const maiter_run_params* 
       plan->warm.setup(g, r, r->delta_wide, coef, p->damping, tu, topq, W, track);
       plan->f32.setup(g, r, r->delta, coef, p->damping, tu, topq, W, track);
       break;
+    case MAITER_OP_MIN_F32:
+      plan->fmin.setup(g, r, r->delta, nullptr, 0.0, tu, topq, W, track);
+      plan->fmin.a.bucket = p->sched == MAITER_SCHED_BUCKET;
+      break;
     default:
       plan->umin.setup(g, r, r->delta, nullptr, 0.0, tu, topq, W, track);
       plan->umin.a.bucket = p->sched == MAITER_SCHED_BUCKET;
@@ -326,6 +359,7 @@ static maiter_status build_graph(const maiter_graph* g, maiter_result* r, int op
   maiter_status s;
   if (op == MAITER_OP_SUM_F64) s = plan.f64.add_to(r->graph, nullptr, 0, h1, &n1);
   else if (op == MAITER_OP_SUM_MIXED) s = plan.warm.add_to(r->graph, nullptr, 0, h1, &n1);
+  else if (op == MAITER_OP_MIN_F32) s = plan.fmin.add_to(r->graph, nullptr, 0, h1, &n1);
   else s = plan.umin.add_to(r->graph, nullptr, 0, h1, &n1);
   if (s != MAITER_OK) return s;
   if (op == MAITER_OP_SUM_MIXED) {
@@ -426,6 +460,8 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
         MAITER_CUDA(cudaStreamSynchronize(st));
         if (r->h_ctl->status == 0) ls = plan.f32.host_loop(r, st, e, s);
       }
+    } else if (p->op == MAITER_OP_MIN_F32) {
+      ls = plan.fmin.host_loop(r, st, e, s, trace);
     } else {
       ls = plan.umin.host_loop(r, st, e, s, trace);
     }
@@ -473,7 +509,8 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
 // Initial v and Delta: copies when given, else the defaults of Table 1.
 template <class V, class D>
 static maiter_status init_state(const maiter_graph* g, const maiter_run_params* p, void* vbuf,
-                                void* dbuf, bool is_sum, cudaStream_t st, int* launches) {
+                                void* dbuf, bool is_sum, cudaStream_t st, int* launches,
+                                uint32_t inf = kInfU32) {
   const int64_t n = g->n;
   if (n == 0) return MAITER_OK;
   const int blocks = g->num_sms * 4;
@@ -482,7 +519,7 @@ static maiter_status init_state(const maiter_graph* g, const maiter_run_params* 
   if (p->v0) {
     MAITER_CUDA(cudaMemcpyAsync(v, p->v0, sizeof(V) * n, cudaMemcpyDefault, st));
   } else {
-    k_fill<V><<<blocks, 256, 0, st>>>(v, n, is_sum ? V(0) : V(kInfU32));
+    k_fill<V><<<blocks, 256, 0, st>>>(v, n, is_sum ? V(0) : V(inf));
     ++*launches;
   }
   if (p->delta0) {
@@ -491,7 +528,7 @@ static maiter_status init_state(const maiter_graph* g, const maiter_run_params* 
     k_fill<D><<<blocks, 256, 0, st>>>(d, n, static_cast<D>(1.0 - p->damping));
     ++*launches;
   } else {
-    k_fill<D><<<blocks, 256, 0, st>>>(d, n, D(kInfU32));
+    k_fill<D><<<blocks, 256, 0, st>>>(d, n, D(inf));
     k_fill<D><<<1, 32, 0, st>>>(d + p->source, 1, D(0));
     *launches += 2;
   }
@@ -509,6 +546,10 @@ static maiter_status run_op(const maiter_graph* g, const maiter_run_params* p, m
       break;
     case MAITER_OP_SUM_MIXED:
       s = init_state<double, double>(g, p, r->v, r->delta_wide, true, st, &init_launches);
+      break;
+    case MAITER_OP_MIN_F32:   // +inf everywhere, 0.0f (bits 0) at the source
+      s = init_state<uint32_t, uint32_t>(g, p, r->v, r->delta, false, st, &init_launches,
+                                         OpMinF32::kNone);
       break;
     default:
       s = init_state<uint32_t, uint32_t>(g, p, r->v, r->delta, false, st, &init_launches);
@@ -537,8 +578,13 @@ namespace maiter {
 static maiter_status run_impl(const maiter_graph* g, const maiter_run_params* p, maiter_result** out,
                               TraceSink* trace) {
   MAITER_REQUIRE(g && p && out, "maiter_run: NULL argument");
-  MAITER_REQUIRE(p->op >= MAITER_OP_SUM_F64 && p->op <= MAITER_OP_MIN_U32, "unknown op %d", p->op);
-  const bool is_sum = p->op != MAITER_OP_MIN_U32;
+  MAITER_REQUIRE(p->op >= MAITER_OP_SUM_F64 && p->op <= MAITER_OP_MIN_F32, "unknown op %d", p->op);
+  const bool is_sum = !is_min_op(p->op);
+  if (p->op == MAITER_OP_MIN_F32 &&
+      (p->engine != MAITER_ENGINE_SYNC || p->sched == MAITER_SCHED_LEARNED)) {
+    set_error("float distances run on the round engine with a fixed schedule");
+    return MAITER_ERR_UNSUPPORTED;
+  }
   MAITER_REQUIRE(p->sched >= MAITER_SCHED_ALL && p->sched <= MAITER_SCHED_BUCKET,
                  "unknown sched %d", p->sched);
   if (p->sched == MAITER_SCHED_BUCKET) {
@@ -593,6 +639,10 @@ static maiter_status run_impl(const maiter_graph* g, const maiter_run_params* p,
   MAITER_REQUIRE(p->sched != MAITER_SCHED_TOPFRAC || (p->top_frac > 0.0 && p->top_frac <= 1.0),
                  "top_frac must lie in (0, 1]");
   DeviceGuard guard(g->device);
+  if (p->op == MAITER_OP_MIN_F32 && g->m > 0) {
+    maiter_status ws = check_float_weights(g);
+    if (ws != MAITER_OK) return ws;
+  }
   maiter_result* r = *out;
   bool fresh = false;
   if (r) {
