@@ -79,8 +79,11 @@ typedef enum {
   MAITER_G_SCALE_BY_SRC = 0, /* g_{j,k}(x) = coef[j] * x.  With coef == NULL,
                                 coef[j] = damping / outdeg(j) (PageRank,
                                 Section 4.2, sender's out-degree). */
-  MAITER_G_ADD_EDGE = 1      /* g_{j,k}(x) = x + w[e] (SSSP, Table 1), saturating
+  MAITER_G_ADD_EDGE = 1,     /* g_{j,k}(x) = x + w[e] (SSSP, Table 1), saturating
                                 at UINT32_MAX; needs edge weights */
+  MAITER_G_SCALE_BY_EDGE = 2 /* g_{j,k}(x) = coef[e] * x with one FP64 coefficient
+                                per edge e = (j, k), in CSR order (SUM_F64 only):
+                                the Jacobi method's -A_kj / A_kk (Table 1); signed */
 } maiter_g;
 
 /* Which vertices an iteration activates (Section 3.5, Section 5.1). */
@@ -143,7 +146,8 @@ typedef struct maiter_run_params {
   int32_t flags;       /* maiter_flags */
   int32_t reserved0;   /* must be 0 */
   const void* coef;    /* n per-source coefficients (double for SUM_F64, float for
-                          SUM_MIXED), host or device, or NULL (see damping) */
+                          SUM_MIXED), host or device, or NULL (see damping);
+                          with g = SCALE_BY_EDGE: m per-edge doubles (required) */
   double damping;      /* d in coef[j] = d / outdeg(j) when coef == NULL */
   const void* v0;      /* n initial states (double for sums, uint32 for min), or
                           NULL: the identity (0 for +, UINT32_MAX for min) */

@@ -143,6 +143,22 @@ def dense_solve(g, coef, c) -> np.ndarray:
     return np.linalg.solve(A, np.asarray(c, dtype=np.float64))
 
 
+def katz(g, beta: float, s: int) -> np.ndarray:
+    """Katz metric from s (Table 1): x = sum_{k >= 0} (beta A^T)^k e_s, the fixed
+    point of x = e_s + beta A^T x (A the 0/1 adjacency, multi-edges counted),
+    by the synchronous iteration of Eq. 1."""
+    c = np.zeros(g.n)
+    c[s] = 1.0
+    v, _ = linear_power(g, np.full(g.n, float(beta)), c)
+    return v
+
+
+def solve_linear_system(A, b) -> np.ndarray:
+    """x with A x = b (dense LU with partial pivoting, library routine): what
+    the Jacobi method of Section 4.3 converges to."""
+    return np.linalg.solve(np.asarray(A, dtype=np.float64), np.asarray(b, dtype=np.float64))
+
+
 def daic_sum(g, coef, v0, delta0, sched: str = "roundrobin", eps: float = 1e-12,
              max_updates: int = 1 << 62):
     """Asynchronous DAIC with + (Eq. 5) from (v0, delta0), serial.

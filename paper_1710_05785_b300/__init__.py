@@ -31,7 +31,7 @@ _STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CON
 
 # maiter_op / maiter_g / maiter_sched / maiter_engine
 OP_SUM_F64, OP_SUM_MIXED, OP_MIN_U32, OP_MIN_F32 = 0, 1, 2, 3
-G_SCALE_BY_SRC, G_ADD_EDGE = 0, 1
+G_SCALE_BY_SRC, G_ADD_EDGE, G_SCALE_BY_EDGE = 0, 1, 2
 SCHED_ALL, SCHED_THRESHOLD, SCHED_TOPFRAC, SCHED_LEARNED, SCHED_BUCKET = 0, 1, 2, 3, 4
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 8, 64, 641
 ENGINE_SYNC, ENGINE_ASYNC = 0, 1
@@ -282,15 +282,25 @@ def run(graph: Graph, op: int = OP_SUM_F64, *, coef=None, damping: float = 0.8, 
         max_rounds: int = 1000000,
         timeout_ms: int = 0, stream=None, engine: int = ENGINE_SYNC, flags: int = 0,
         cut_warp: int = 0, cut_cta: int = 0, push_blocks_per_sm: int = 0, scorer=None,
-        result: Result | None = None, allow_not_converged: bool = False) -> Result:
+        edge_coef=None, result: Result | None = None,
+        allow_not_converged: bool = False) -> Result:
     """``maiter_run``: one DAIC run to termination.  ``stream`` is a raw
-    cudaStream_t handle (e.g. ``torch.cuda.current_stream().cuda_stream``)."""
+    cudaStream_t handle (e.g. ``torch.cuda.current_stream().cuda_stream``).
+    ``edge_coef`` (m float64, CSR order) selects g_{j,k}(x) = c_e x
+    (MAITER_G_SCALE_BY_EDGE, e.g. the Jacobi method's -A_kj / A_kk)."""
     n = graph.n
     p = params_default()
     p.op = op
     p.g = G_ADD_EDGE if op in (OP_MIN_U32, OP_MIN_F32) else G_SCALE_BY_SRC
     p.sched, p.engine, p.flags = sched, engine, flags
     keep = []
+    if edge_coef is not None:
+        if coef is not None:
+            raise ValueError("give coef (per source) or edge_coef (per edge), not both")
+        edge_coef = _as(edge_coef, np.float64, graph.m, "edge_coef")
+        keep.append(edge_coef)
+        p.g = G_SCALE_BY_EDGE
+        p.coef = _addr(edge_coef)
     if coef is not None:
         coef = _as(coef, _COEF_DTYPE[op], n, "coef")
         keep.append(coef)

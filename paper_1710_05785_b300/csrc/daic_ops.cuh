@@ -21,6 +21,7 @@ constexpr uint32_t kInfU32 = 0xFFFFFFFFu;
 struct EdgeCtx {
   const int* __restrict__ col;
   const uint32_t* __restrict__ w;
+  const double* __restrict__ ecoef;   // per-edge coefficients (g = c_e x), or null
 };
 
 __device__ __forceinline__ double atomic_take(double* p) {
@@ -82,6 +83,51 @@ struct OpSum {
   }
   __device__ static __forceinline__ void apply(Edge ed, Msg m, D* delta) {
     atomicAdd(delta + ed.k, m);
+  }
+  __device__ static __forceinline__ void scatter(const EdgeCtx& g, int64_t e, Msg m, D* delta) {
+    apply(load(g, e), m, delta);
+  }
+};
+
+// + with a coefficient per edge, g_{j,k}(x) = c_{jk} x, all FP64: the Jacobi
+// method's -A_kj / A_kk (Section 4.3) and any other linear update whose weights
+// depend on the receiver.  A vertex's message is Delta_j itself; each edge
+// scales it.  Coefficients may be negative, so Delta is signed and the
+// priority and the residual use |Delta|.
+struct OpSumEdge {
+  using V = double;
+  using D = double;
+  using C = double;
+  using Msg = double;
+  static constexpr bool kIsSum = true;
+  static constexpr double kNone = 0.0;
+
+  __device__ static __forceinline__ double priority(D d, V) { return fabs(d); }
+  __device__ static __forceinline__ bool pending(D d, V) { return d != 0.0; }
+  __device__ static __forceinline__ Msg fold(int j, int deg, D* delta, V* v, const C*, double) {
+    const double d = atomic_take(delta + j);
+    if (d == 0.0) return 0.0;
+    v[j] += d;
+    return deg == 0 ? 0.0 : d;
+  }
+  __device__ static __forceinline__ D take(int j, D* delta, const V*) { return atomic_take(delta + j); }
+  __device__ static __forceinline__ void untake(int j, D d, D* delta) {
+    if (d != 0.0) atomicAdd(delta + j, d);
+  }
+  __device__ static __forceinline__ Msg finish(int j, int deg, D d, V* v, const C*, double,
+                                               bool first_chunk) {
+    if (d == 0.0) return 0.0;
+    if (first_chunk) v[j] += d;
+    return deg == 0 ? 0.0 : d;
+  }
+  __device__ static __forceinline__ bool live(Msg m) { return m != 0.0; }
+  struct Edge { int k; double c; };
+  __device__ static __forceinline__ Edge load(const EdgeCtx& g, int64_t e) {
+    return Edge{__ldg(g.col + e), __ldg(g.ecoef + e)};
+  }
+  __device__ static __forceinline__ void apply(Edge ed, Msg m, D* delta) {
+    const double x = ed.c * m;
+    if (x != 0.0) atomicAdd(delta + ed.k, x);
   }
   __device__ static __forceinline__ void scatter(const EdgeCtx& g, int64_t e, Msg m, D* delta) {
     apply(load(g, e), m, delta);

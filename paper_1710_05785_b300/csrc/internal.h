@@ -80,6 +80,7 @@ struct maiter_result {
   void* delta = nullptr;       // n x D
   void* delta_wide = nullptr;  // n x double: FP64 deltas of the mixed run's warm-up phase
   void* coef = nullptr;        // n x C (allocated on first use)
+  double* ecoef = nullptr;     // m per-edge coefficients (SCALE_BY_EDGE, on first use)
   int* list[2] = {nullptr, nullptr};   // small / medium frontier (n entries each)
   int2* large = nullptr;               // large-vertex chunk entries
   void* large_d = nullptr;             // their taken deltas (8 bytes per entry)

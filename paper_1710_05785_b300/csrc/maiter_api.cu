@@ -194,6 +194,7 @@ void maiter_result_destroy(maiter_result* r) {
   cudaFree(r->delta);
   cudaFree(r->delta_wide);
   cudaFree(r->coef);
+  cudaFree(r->ecoef);
   for (int b = 0; b < 2; ++b) cudaFree(r->list[b]);
   cudaFree(r->large);
   cudaFree(r->large_d);
@@ -264,6 +265,8 @@ struct RunPlan {
   Phase<OpSumMixed> f32;
   Phase<OpMinU32> umin;
   Phase<OpMinF32> fmin;
+  Phase<OpSumEdge> fedge;
+  bool edge = false;      // SUM_F64 with one coefficient per edge
 };
 
 // Float weights must be finite and >= 0 (sign bit clear, exponent not all
@@ -324,7 +327,14 @@ static maiter_status setup_plan(const maiter_graph* g, const maiter_run_params* 
   }
   const MlpWeights* W = learned ? mlp_device_weights(p->scorer) : nullptr;
   switch (p->op) {
-    case MAITER_OP_SUM_F64: plan->f64.setup(g, r, r->delta, coef, p->damping, tu, topq, W, track); break;
+    case MAITER_OP_SUM_F64:
+      if (p->g == MAITER_G_SCALE_BY_EDGE) {
+        plan->edge = true;
+        plan->fedge.setup(g, r, r->delta, nullptr, 0.0, tu, topq, W, track);
+      } else {
+        plan->f64.setup(g, r, r->delta, coef, p->damping, tu, topq, W, track);
+      }
+      break;
     case MAITER_OP_SUM_MIXED:
       plan->mixed = true;
       plan->warm.setup(g, r, r->delta_wide, coef, p->damping, tu, topq, W, track);
@@ -357,7 +367,8 @@ static maiter_status build_graph(const maiter_graph* g, maiter_result* r, int op
   MAITER_CUDA(cudaGraphConditionalHandleCreate(&h1, r->graph, 1, cudaGraphCondAssignDefault));
   cudaGraphNode_t n1;
   maiter_status s;
-  if (op == MAITER_OP_SUM_F64) s = plan.f64.add_to(r->graph, nullptr, 0, h1, &n1);
+  if (plan.edge) s = plan.fedge.add_to(r->graph, nullptr, 0, h1, &n1);
+  else if (op == MAITER_OP_SUM_F64) s = plan.f64.add_to(r->graph, nullptr, 0, h1, &n1);
   else if (op == MAITER_OP_SUM_MIXED) s = plan.warm.add_to(r->graph, nullptr, 0, h1, &n1);
   else if (op == MAITER_OP_MIN_F32) s = plan.fmin.add_to(r->graph, nullptr, 0, h1, &n1);
   else s = plan.umin.add_to(r->graph, nullptr, 0, h1, &n1);
@@ -407,6 +418,7 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   std::memcpy(&dbits, &p->damping, sizeof(dbits));
   mix(static_cast<uint64_t>(p->op));
   mix(p->coef ? 1 : 0);
+  mix(static_cast<uint64_t>(p->g));
   mix(dbits);
   mix(static_cast<uint64_t>(tu.cut_warp));
   mix(static_cast<uint64_t>(tu.cut_cta));
@@ -448,7 +460,8 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
     MAITER_CUDA(cudaEventRecord(r->ev0, st));
     maiter_status ls;
     if (p->op == MAITER_OP_SUM_F64) {
-      ls = plan.f64.host_loop(r, st, e, s, trace);
+      ls = plan.edge ? plan.fedge.host_loop(r, st, e, s, trace)
+                     : plan.f64.host_loop(r, st, e, s, trace);
     } else if (p->op == MAITER_OP_SUM_MIXED) {
       ls = plan.warm.host_loop(r, st, e, s);
       if (ls == MAITER_OK) {
@@ -556,7 +569,11 @@ static maiter_status run_op(const maiter_graph* g, const maiter_run_params* p, m
       break;
   }
   if (s != MAITER_OK) return s;
-  if (p->coef && g->n > 0) {
+  if (p->g == MAITER_G_SCALE_BY_EDGE) {
+    if (!r->ecoef) MAITER_CUDA(cudaMalloc(&r->ecoef, sizeof(double) * (g->m > 0 ? g->m : 1)));
+    if (g->m > 0)
+      MAITER_CUDA(cudaMemcpyAsync(r->ecoef, p->coef, sizeof(double) * g->m, cudaMemcpyDefault, st));
+  } else if (p->coef && g->n > 0) {
     if (!r->coef) MAITER_CUDA(cudaMalloc(&r->coef, coef_bytes(r->op) * g->n));
     MAITER_CUDA(cudaMemcpyAsync(r->coef, p->coef, coef_bytes(r->op) * g->n, cudaMemcpyDefault, st));
   }
@@ -621,7 +638,16 @@ static maiter_status run_impl(const maiter_graph* g, const maiter_run_params* p,
                      p->reserved0 == 0,
                  "unknown flags 0x%x", p->flags);
   if (is_sum) {
-    MAITER_REQUIRE(p->g == MAITER_G_SCALE_BY_SRC, "sum ops take g = MAITER_G_SCALE_BY_SRC");
+    MAITER_REQUIRE(p->g == MAITER_G_SCALE_BY_SRC ||
+                       (p->g == MAITER_G_SCALE_BY_EDGE && p->op == MAITER_OP_SUM_F64),
+                   "sum ops take g = MAITER_G_SCALE_BY_SRC (or SCALE_BY_EDGE with SUM_F64)");
+    MAITER_REQUIRE(p->g != MAITER_G_SCALE_BY_EDGE || p->coef || g->m == 0,
+                   "g = SCALE_BY_EDGE needs m per-edge coefficients");
+    if (p->g == MAITER_G_SCALE_BY_EDGE &&
+        (p->engine != MAITER_ENGINE_SYNC || p->sched == MAITER_SCHED_LEARNED)) {
+      set_error("per-edge coefficients run on the round engine with a fixed schedule");
+      return MAITER_ERR_UNSUPPORTED;
+    }
     MAITER_REQUIRE(p->coef || std::isfinite(p->damping),
                    "damping must be finite when coef is NULL");
     MAITER_REQUIRE(std::isfinite(p->eps) && p->eps >= 0.0, "eps must be finite and >= 0");

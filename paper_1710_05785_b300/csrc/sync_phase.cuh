@@ -51,6 +51,7 @@ struct Phase {
     a.rp = g->rp;
     a.edges.col = g->col;
     a.edges.w = g->w;
+    a.edges.ecoef = r->ecoef;
     a.coef = static_cast<const typename Op::C*>(coef);
     a.damping = damping;
     a.v = static_cast<typename Op::V*>(r->v);
