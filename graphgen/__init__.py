@@ -168,6 +168,15 @@ def lognormal(n: int, seed: int | None = None, mu: float = -0.5, sigma: float = 
     return csr_from_edges(n, src, dst, w, None, name=f"lognormal-n{n}-s{seed}")
 
 
+def symmetrize(g: CSRGraph) -> CSRGraph:
+    """The graph with every edge also reversed (an undirected graph as a
+    directed one; weights, if any, copied to the reverse edge)."""
+    src = np.repeat(np.arange(g.n, dtype=np.int32), np.diff(g.row_ptr))
+    w = None if g.w is None else np.concatenate([g.w, g.w])
+    return csr_from_edges(g.n, np.concatenate([src, g.col]), np.concatenate([g.col, src]), w,
+                          name=g.name + "-sym")
+
+
 def float_weights(g: CSRGraph) -> np.ndarray:
     """The float32 view of a graph whose ``w`` holds IEEE single bit patterns."""
     return g.w.view(np.float32)

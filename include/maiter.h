@@ -66,12 +66,19 @@ typedef enum {
                               residual reduction FP64 (after an FP64-delta
                               warm-up phase, see mixed_switch) */
   MAITER_OP_MIN_U32 = 2,   /* (+) = min over uint32, identity UINT32_MAX (inf) */
-  MAITER_OP_MIN_F32 = 3    /* (+) = min over IEEE float32 distances >= 0, identity
+  MAITER_OP_MIN_F32 = 3,   /* (+) = min over IEEE float32 distances >= 0, identity
                               +inf; the graph's 32-bit weights are read as floats
                               (finite, >= 0: checked once per graph), messages are
                               fl(Delta_j + w) rounded to nearest.  v and Delta are
                               returned as float32.  Round engine, schedules ALL,
                               THRESHOLD (as ALL), TOPFRAC and BUCKET. */
+  MAITER_OP_MAX_I32 = 4    /* (+) = max over int32 labels, identity -1 (connected
+                              components, Table 1): with g = IDENTITY, v0 = -1 and
+                              Delta^1_j = j by default, every vertex ends with the
+                              largest id among the vertices that reach it (its
+                              component's largest id on a symmetric graph).
+                              Round engine, schedules ALL, THRESHOLD (as ALL) and
+                              TOPFRAC (priority Delta_j - v_j). */
 } maiter_op;
 
 /* The message function g_{j,k}. */
@@ -81,9 +88,10 @@ typedef enum {
                                 Section 4.2, sender's out-degree). */
   MAITER_G_ADD_EDGE = 1,     /* g_{j,k}(x) = x + w[e] (SSSP, Table 1), saturating
                                 at UINT32_MAX; needs edge weights */
-  MAITER_G_SCALE_BY_EDGE = 2 /* g_{j,k}(x) = coef[e] * x with one FP64 coefficient
+  MAITER_G_SCALE_BY_EDGE = 2, /* g_{j,k}(x) = coef[e] * x with one FP64 coefficient
                                 per edge e = (j, k), in CSR order (SUM_F64 only):
                                 the Jacobi method's -A_kj / A_kk (Table 1); signed */
+  MAITER_G_IDENTITY = 3      /* g_{j,k}(x) = x (connected components, MAX_I32) */
 } maiter_g;
 
 /* Which vertices an iteration activates (Section 3.5, Section 5.1). */
@@ -149,11 +157,13 @@ typedef struct maiter_run_params {
                           SUM_MIXED), host or device, or NULL (see damping);
                           with g = SCALE_BY_EDGE: m per-edge doubles (required) */
   double damping;      /* d in coef[j] = d / outdeg(j) when coef == NULL */
-  const void* v0;      /* n initial states (double for sums, uint32 for min), or
-                          NULL: the identity (0 for +, UINT32_MAX for min) */
-  const void* delta0;  /* n initial deltas (double for both sums, uint32 for min), or NULL:
-                          1 - damping everywhere for sums (PageRank, Table 1),
-                          0 at `source` and UINT32_MAX elsewhere for min */
+  const void* v0;      /* n initial states (double for sums, uint32 / float for min,
+                          int32 for max), or NULL: the identity (0 for +,
+                          infinity for min, -1 for max) */
+  const void* delta0;  /* n initial deltas (double for both sums, uint32 / float for
+                          min, int32 for max), or NULL: 1 - damping everywhere for
+                          sums (PageRank, Table 1), 0 at `source` and infinity
+                          elsewhere for min, Delta_j = j for max */
   int64_t source;      /* min with delta0 == NULL: the source vertex */
   double threshold;    /* THRESHOLD: activate |Delta_j| > threshold.  When a
                           round selects nothing while the residual is still

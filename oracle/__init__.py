@@ -51,6 +51,10 @@ def _load():
         lib.or_dijkstra.argtypes = [i64, P, P, P, ctypes.c_int32, P]
         lib.or_dijkstra.restype = i32
         lib.or_bellman_ford.argtypes = [i64, P, P, P, ctypes.c_int32, P]
+        lib.or_max_reach.argtypes = [i64, P, P, P]
+        lib.or_max_reach.restype = i32
+        lib.or_union_find_max.argtypes = [i64, P, P, P]
+        lib.or_union_find_max.restype = i32
         lib.or_dijkstra_f32.argtypes = [i64, P, P, P, ctypes.c_int32, P]
         lib.or_dijkstra_f32.restype = i32
         lib.or_bellman_ford_f32.argtypes = [i64, P, P, P, ctypes.c_int32, P]
@@ -221,6 +225,26 @@ def bellman_ford(g, source: int) -> np.ndarray:
     w = np.ascontiguousarray(g.w, dtype=np.uint32)
     out = np.empty(g.n, dtype=np.uint32)
     _load().or_bellman_ford(g.n, _p(rp), _p(col), _p(w), int(source), _p(out))
+    return out
+
+
+def max_reach_labels(g) -> np.ndarray:
+    """Connected-components labels of Table 1 (max): for every vertex the
+    largest id among the vertices that reach it, itself included (int32)."""
+    rp, col = _csr(g)
+    out = np.empty(g.n, dtype=np.int32)
+    if _load().or_max_reach(g.n, _p(rp), _p(col), _p(out)) != 0:
+        raise MemoryError("or_max_reach")
+    return out
+
+
+def component_labels(g) -> np.ndarray:
+    """Components of the graph taken as undirected (union-find), each vertex
+    labelled with its component's largest id (int32)."""
+    rp, col = _csr(g)
+    out = np.empty(g.n, dtype=np.int32)
+    if _load().or_union_find_max(g.n, _p(rp), _p(col), _p(out)) != 0:
+        raise MemoryError("or_union_find_max")
     return out
 
 

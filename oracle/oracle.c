@@ -16,6 +16,11 @@
  *   or_daic_min        - asynchronous DAIC with min (SSSP row of Table 1).
  *   or_dijkstra        - textbook single-source shortest paths (binary heap).
  *   or_bellman_ford    - brute-force relaxation to a fixed point (tiny inputs).
+ *   or_max_reach       - connected components by labels (Table 1, max): for
+ *                        every vertex the largest id among the vertices that
+ *                        reach it (itself included).
+ *   or_union_find_max  - components of the undirected version of the graph
+ *                        by union-find, labelled with their largest id.
  *   or_dijkstra_f32 / or_bellman_ford_f32 - the same with IEEE single
  *                        weights and distances (the paper's float-weighted
  *                        synthetic SSSP graphs, Section 6.1): every tentative
@@ -468,4 +473,54 @@ void or_bellman_ford_f32(int64_t n, const int64_t* row_ptr, const int32_t* col, 
     }
     if (!changed) break;
   }
+}
+
+/* ------------------------------------------------------- component labels */
+
+/*
+ * label[j] = max { i : there is a path i ->* j } (j reaches itself).  Sources
+ * in decreasing id order: a breadth-first search from i labels every vertex
+ * it reaches that is still unlabelled, and stops at labelled ones (whatever a
+ * labelled vertex reaches was already labelled from a larger id).  O(n + m).
+ * Returns 0, or -1 on allocation failure.
+ */
+int or_max_reach(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t* label) {
+  int32_t* queue = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+  if (!queue) return -1;
+  for (int64_t j = 0; j < n; ++j) label[j] = -1;
+  for (int64_t i = n - 1; i >= 0; --i) {
+    if (label[i] >= 0) continue;
+    int64_t head = 0, tail = 0;
+    label[i] = (int32_t)i;
+    queue[tail++] = (int32_t)i;
+    while (head < tail) {
+      int32_t u = queue[head++];
+      for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+        int32_t k = col[e];
+        if (label[k] < 0) { label[k] = (int32_t)i; queue[tail++] = k; }
+      }
+    }
+  }
+  free(queue);
+  return 0;
+}
+
+static int32_t uf_find(int32_t* parent, int32_t x) {
+  while (parent[x] != x) { parent[x] = parent[parent[x]]; x = parent[x]; }
+  return x;
+}
+
+/* Union-find over every edge as undirected; label = largest id of the set. */
+int or_union_find_max(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t* label) {
+  int32_t* parent = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+  if (!parent) return -1;
+  for (int64_t j = 0; j < n; ++j) parent[j] = (int32_t)j;
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t e = row_ptr[j]; e < row_ptr[j + 1]; ++e) {
+      int32_t a = uf_find(parent, (int32_t)j), b = uf_find(parent, col[e]);
+      if (a != b) { if (a < b) parent[a] = b; else parent[b] = a; }   /* larger id is the root */
+    }
+  for (int64_t j = 0; j < n; ++j) label[j] = uf_find(parent, (int32_t)j);
+  free(parent);
+  return 0;
 }

@@ -30,8 +30,8 @@ _STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_CON
                  -5: "TIMEOUT", -6: "UNSUPPORTED"}
 
 # maiter_op / maiter_g / maiter_sched / maiter_engine
-OP_SUM_F64, OP_SUM_MIXED, OP_MIN_U32, OP_MIN_F32 = 0, 1, 2, 3
-G_SCALE_BY_SRC, G_ADD_EDGE, G_SCALE_BY_EDGE = 0, 1, 2
+OP_SUM_F64, OP_SUM_MIXED, OP_MIN_U32, OP_MIN_F32, OP_MAX_I32 = 0, 1, 2, 3, 4
+G_SCALE_BY_SRC, G_ADD_EDGE, G_SCALE_BY_EDGE, G_IDENTITY = 0, 1, 2, 3
 SCHED_ALL, SCHED_THRESHOLD, SCHED_TOPFRAC, SCHED_LEARNED, SCHED_BUCKET = 0, 1, 2, 3, 4
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 8, 64, 641
 ENGINE_SYNC, ENGINE_ASYNC = 0, 1
@@ -40,11 +40,11 @@ FLAG_PROFILE_KERNELS, FLAG_INJECT_STALL = 1, 2
 INF32 = 0xFFFFFFFF
 
 _STATE_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float64, OP_MIN_U32: np.uint32,
-                OP_MIN_F32: np.float32}
+                OP_MIN_F32: np.float32, OP_MAX_I32: np.int32}
 _DELTA_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float32, OP_MIN_U32: np.uint32,
-                OP_MIN_F32: np.float32}
+                OP_MIN_F32: np.float32, OP_MAX_I32: np.int32}
 _DELTA0_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float64, OP_MIN_U32: np.uint32,
-                 OP_MIN_F32: np.float32}
+                 OP_MIN_F32: np.float32, OP_MAX_I32: np.int32}
 _COEF_DTYPE = {OP_SUM_F64: np.float64, OP_SUM_MIXED: np.float32}
 
 
@@ -291,7 +291,8 @@ def run(graph: Graph, op: int = OP_SUM_F64, *, coef=None, damping: float = 0.8, 
     n = graph.n
     p = params_default()
     p.op = op
-    p.g = G_ADD_EDGE if op in (OP_MIN_U32, OP_MIN_F32) else G_SCALE_BY_SRC
+    p.g = {OP_MIN_U32: G_ADD_EDGE, OP_MIN_F32: G_ADD_EDGE, OP_MAX_I32: G_IDENTITY}.get(
+        op, G_SCALE_BY_SRC)
     p.sched, p.engine, p.flags = sched, engine, flags
     keep = []
     if edge_coef is not None:

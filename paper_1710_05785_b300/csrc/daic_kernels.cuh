@@ -94,6 +94,9 @@ template <class Op>
 __device__ __forceinline__ unsigned priority_key(typename Op::D d, typename Op::V v) {
   if constexpr (Op::kIsSum) {
     return __float_as_uint(fabsf(static_cast<float>(d)));
+  } else if constexpr (Op::kIsMax) {
+    if (!Op::pending(d, v)) return 0u;
+    return __float_as_uint(static_cast<float>(Op::priority(d, v)));
   } else {
     if (!(d < v)) return 0u;
     if (v == Op::kNone) return 0x7F800000u;
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
       } else {
         // BUCKET: only pending distances below the bucket bound tau
         s = pend && (!bucket || min_value<Op>(dd[u]) < tau);
-        if (pend) dmin = min(dmin, static_cast<unsigned>(dd[u]));
+        if (bucket && pend) dmin = min(dmin, static_cast<unsigned>(dd[u]));
       }
       if (a.topq) s = pend && (a.keys ? a.keys[j] : priority_key<Op>(dd[u], vv[u])) >= key_thr;
       sel[u] = s;

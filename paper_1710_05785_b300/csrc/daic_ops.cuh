@@ -152,6 +152,7 @@ struct OpMinU32 {
   using C = float;  // unused
   using Msg = uint32_t;
   static constexpr bool kIsSum = false;
+  static constexpr bool kIsMax = false;
   static constexpr uint32_t kNone = kInfU32;   // infinity: identity of min, nothing pending
   __device__ static __forceinline__ double value(uint32_t x) { return static_cast<double>(x); }
 
@@ -208,6 +209,7 @@ struct OpMinF32 {
   using C = float;  // unused
   using Msg = uint32_t;
   static constexpr bool kIsSum = false;
+  static constexpr bool kIsMax = false;
   static constexpr uint32_t kNone = 0x7F800000u;   // +inf
   __device__ static __forceinline__ double value(uint32_t x) {
     return static_cast<double>(__uint_as_float(x));
@@ -241,6 +243,55 @@ struct OpMinF32 {
   __device__ static __forceinline__ void apply(Edge ed, Msg m, D* delta) {
     const uint32_t nd = __float_as_uint(__fadd_rn(__uint_as_float(m), __uint_as_float(ed.w)));
     if (nd < __ldcg(delta + ed.k)) atomicMin(delta + ed.k, nd);
+  }
+  __device__ static __forceinline__ void scatter(const EdgeCtx& g, int64_t e, Msg m, D* delta) {
+    apply(load(g, e), m, delta);
+  }
+};
+
+// ------------------------------------------- max over int32 (components)
+// Connected components (Table 1): (+) = max, g_{i,j}(x) = x, v^0 = -1,
+// Delta^1_j = j; every vertex ends with the largest id among the vertices
+// that reach it (on a symmetric graph, the largest id of its component).
+// Idempotent like min: Delta is kept, only ever grows, and j is pending iff
+// Delta_j > v_j.
+struct OpMaxI32 {
+  using V = int32_t;
+  using D = int32_t;
+  using C = float;  // unused
+  using Msg = int32_t;
+  static constexpr bool kIsSum = false;
+  static constexpr bool kIsMax = true;
+  static constexpr int32_t kNone = -1;   // identity of max over labels >= 0
+  __device__ static __forceinline__ double value(int32_t x) { return static_cast<double>(x); }
+
+  __device__ static __forceinline__ double priority(D d, V v) {
+    return d > v ? static_cast<double>(d) - static_cast<double>(v) : 0.0;
+  }
+  __device__ static __forceinline__ bool pending(D d, V v) { return d > v; }
+
+  __device__ static __forceinline__ Msg fold(int j, int, D* delta, V* v, const C*, double) {
+    const int32_t d = __ldcg(delta + j);
+    const int32_t cur = v[j];
+    if (d <= cur) return kNone;
+    v[j] = d;
+    return d;
+  }
+  __device__ static __forceinline__ D take(int j, D* delta, const V*) { return __ldcg(delta + j); }
+  __device__ static __forceinline__ void untake(int, D, D*) {}
+  __device__ static __forceinline__ Msg finish(int j, int, D d, V* v, const C*, double,
+                                               bool first_chunk) {
+    if (first_chunk && d > v[j]) v[j] = d;
+    return d;
+  }
+
+  __device__ static __forceinline__ bool live(Msg m) { return m != kNone; }
+  struct Edge { int k; };
+  __device__ static __forceinline__ Edge load(const EdgeCtx& g, int64_t e) {
+    return Edge{__ldg(g.col + e)};
+  }
+  __device__ static __forceinline__ void apply(Edge ed, Msg m, D* delta) {
+    if (m > __ldcg(delta + ed.k)) atomicMax(delta + ed.k, m);
   }
   __device__ static __forceinline__ void scatter(const EdgeCtx& g, int64_t e, Msg m, D* delta) {
     apply(load(g, e), m, delta);

@@ -214,7 +214,8 @@ void maiter_result_destroy(maiter_result* r) {
 namespace maiter {
 
 static bool is_min_op(int op) { return op == MAITER_OP_MIN_U32 || op == MAITER_OP_MIN_F32; }
-static size_t state_bytes(int op) { return is_min_op(op) ? 4 : 8; }
+static bool is_order_op(int op) { return is_min_op(op) || op == MAITER_OP_MAX_I32; }
+static size_t state_bytes(int op) { return is_order_op(op) ? 4 : 8; }
 static size_t delta_bytes(int op) { return op == MAITER_OP_SUM_F64 ? 8 : 4; }
 static size_t coef_bytes(int op) { return op == MAITER_OP_SUM_F64 ? 8 : 4; }
 
@@ -266,6 +267,7 @@ struct RunPlan {
   Phase<OpMinU32> umin;
   Phase<OpMinF32> fmin;
   Phase<OpSumEdge> fedge;
+  Phase<OpMaxI32> imax;
   bool edge = false;      // SUM_F64 with one coefficient per edge
 };
 
@@ -340,6 +342,9 @@ static maiter_status setup_plan(const maiter_graph* g, const maiter_run_params* 
       plan->warm.setup(g, r, r->delta_wide, coef, p->damping, tu, topq, W, track);
       plan->f32.setup(g, r, r->delta, coef, p->damping, tu, topq, W, track);
       break;
+    case MAITER_OP_MAX_I32:
+      plan->imax.setup(g, r, r->delta, nullptr, 0.0, tu, topq, W, track);
+      break;
     case MAITER_OP_MIN_F32:
       plan->fmin.setup(g, r, r->delta, nullptr, 0.0, tu, topq, W, track);
       plan->fmin.a.bucket = p->sched == MAITER_SCHED_BUCKET;
@@ -371,6 +376,7 @@ static maiter_status build_graph(const maiter_graph* g, maiter_result* r, int op
   else if (op == MAITER_OP_SUM_F64) s = plan.f64.add_to(r->graph, nullptr, 0, h1, &n1);
   else if (op == MAITER_OP_SUM_MIXED) s = plan.warm.add_to(r->graph, nullptr, 0, h1, &n1);
   else if (op == MAITER_OP_MIN_F32) s = plan.fmin.add_to(r->graph, nullptr, 0, h1, &n1);
+  else if (op == MAITER_OP_MAX_I32) s = plan.imax.add_to(r->graph, nullptr, 0, h1, &n1);
   else s = plan.umin.add_to(r->graph, nullptr, 0, h1, &n1);
   if (s != MAITER_OK) return s;
   if (op == MAITER_OP_SUM_MIXED) {
@@ -475,6 +481,8 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
       }
     } else if (p->op == MAITER_OP_MIN_F32) {
       ls = plan.fmin.host_loop(r, st, e, s, trace);
+    } else if (p->op == MAITER_OP_MAX_I32) {
+      ls = plan.imax.host_loop(r, st, e, s, trace);
     } else {
       ls = plan.umin.host_loop(r, st, e, s, trace);
     }
@@ -549,6 +557,36 @@ static maiter_status init_state(const maiter_graph* g, const maiter_run_params* 
   return MAITER_OK;
 }
 
+static __global__ void k_iota(int32_t* __restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    x[i] = static_cast<int32_t>(i);
+}
+
+// Max labels: copies when given, else v = -1 and Delta_j = j (Table 1).
+static maiter_status init_labels(const maiter_graph* g, const maiter_run_params* p,
+                                 maiter_result* r, cudaStream_t st, int* launches) {
+  const int64_t n = g->n;
+  if (n == 0) return MAITER_OK;
+  const int blocks = g->num_sms * 4;
+  int32_t* v = static_cast<int32_t*>(r->v);
+  int32_t* d = static_cast<int32_t*>(r->delta);
+  if (p->v0) {
+    MAITER_CUDA(cudaMemcpyAsync(v, p->v0, sizeof(int32_t) * n, cudaMemcpyDefault, st));
+  } else {
+    k_fill<int32_t><<<blocks, 256, 0, st>>>(v, n, -1);
+    ++*launches;
+  }
+  if (p->delta0) {
+    MAITER_CUDA(cudaMemcpyAsync(d, p->delta0, sizeof(int32_t) * n, cudaMemcpyDefault, st));
+  } else {
+    k_iota<<<blocks, 256, 0, st>>>(d, n);
+    ++*launches;
+  }
+  MAITER_CUDA(cudaGetLastError());
+  return MAITER_OK;
+}
+
 static maiter_status run_op(const maiter_graph* g, const maiter_run_params* p, maiter_result* r,
                             cudaStream_t st, TraceSink* trace = nullptr) {
   int init_launches = 0;
@@ -559,6 +597,9 @@ static maiter_status run_op(const maiter_graph* g, const maiter_run_params* p, m
       break;
     case MAITER_OP_SUM_MIXED:
       s = init_state<double, double>(g, p, r->v, r->delta_wide, true, st, &init_launches);
+      break;
+    case MAITER_OP_MAX_I32:   // v = -1, Delta_j = j (Table 1, connected components)
+      s = init_labels(g, p, r, st, &init_launches);
       break;
     case MAITER_OP_MIN_F32:   // +inf everywhere, 0.0f (bits 0) at the source
       s = init_state<uint32_t, uint32_t>(g, p, r->v, r->delta, false, st, &init_launches,
@@ -595,8 +636,14 @@ namespace maiter {
 static maiter_status run_impl(const maiter_graph* g, const maiter_run_params* p, maiter_result** out,
                               TraceSink* trace) {
   MAITER_REQUIRE(g && p && out, "maiter_run: NULL argument");
-  MAITER_REQUIRE(p->op >= MAITER_OP_SUM_F64 && p->op <= MAITER_OP_MIN_F32, "unknown op %d", p->op);
-  const bool is_sum = !is_min_op(p->op);
+  MAITER_REQUIRE(p->op >= MAITER_OP_SUM_F64 && p->op <= MAITER_OP_MAX_I32, "unknown op %d", p->op);
+  const bool is_sum = !is_order_op(p->op);
+  if (p->op == MAITER_OP_MAX_I32 &&
+      (p->engine != MAITER_ENGINE_SYNC || p->sched == MAITER_SCHED_LEARNED ||
+       p->sched == MAITER_SCHED_BUCKET)) {
+    set_error("max labels run on the round engine with ALL, THRESHOLD or TOPFRAC");
+    return MAITER_ERR_UNSUPPORTED;
+  }
   if (p->op == MAITER_OP_MIN_F32 &&
       (p->engine != MAITER_ENGINE_SYNC || p->sched == MAITER_SCHED_LEARNED)) {
     set_error("float distances run on the round engine with a fixed schedule");
@@ -656,6 +703,8 @@ static maiter_status run_impl(const maiter_graph* g, const maiter_run_params* p,
     MAITER_REQUIRE(p->sched != MAITER_SCHED_THRESHOLD ||
                        (std::isfinite(p->threshold) && p->threshold >= 0.0),
                    "threshold must be finite and >= 0");
+  } else if (p->op == MAITER_OP_MAX_I32) {
+    MAITER_REQUIRE(p->g == MAITER_G_IDENTITY, "max takes g = MAITER_G_IDENTITY");
   } else {
     MAITER_REQUIRE(p->g == MAITER_G_ADD_EDGE, "min takes g = MAITER_G_ADD_EDGE");
     MAITER_REQUIRE(g->w || g->m == 0, "min with g = x + w needs edge weights");

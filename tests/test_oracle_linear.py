@@ -1,6 +1,7 @@
-"""Pins of the oracle for the other linear rows of Table 1: the Katz metric
-(closed forms on a path and a cycle) and the linear system the Jacobi method
-solves (a system worked by hand)."""
+"""Pins of the oracle for the other rows of Table 1: the Katz metric (closed
+forms on a path and a cycle), the linear system the Jacobi method solves (a
+system worked by hand), and connected-components labels (by hand, by
+transitive closure, and two independent algorithms on symmetric graphs)."""
 import numpy as np
 
 import graphgen
@@ -34,3 +35,37 @@ def test_linear_system_solution_by_hand():
     # [[4, 1], [2, 3]] x = [1, 2]: det 10, x = (1*3 - 1*2, 4*2 - 2*1) / 10
     x = oracle.solve_linear_system([[4.0, 1.0], [2.0, 3.0]], [1.0, 2.0])
     np.testing.assert_allclose(x, [0.1, 0.6], rtol=1e-14)
+
+
+# ------------------------------------------ connected components (Table 1)
+
+def test_component_labels_by_hand():
+    # {0, 1, 2} joined both ways, {3, 4}, and 5 alone
+    e = [(0, 1), (1, 0), (1, 2), (2, 1), (3, 4), (4, 3)]
+    g = graphgen.small_graph(6, e)
+    np.testing.assert_array_equal(oracle.max_reach_labels(g), [2, 2, 2, 4, 4, 5])
+    np.testing.assert_array_equal(oracle.component_labels(g), [2, 2, 2, 4, 4, 5])
+
+
+def test_max_reach_follows_edge_direction():
+    up = graphgen.small_graph(3, [(0, 1), (1, 2)])
+    down = graphgen.small_graph(3, [(2, 1), (1, 0)])
+    np.testing.assert_array_equal(oracle.max_reach_labels(up), [0, 1, 2])
+    np.testing.assert_array_equal(oracle.max_reach_labels(down), [2, 2, 2])
+
+
+def test_max_reach_by_transitive_closure_and_union_find():
+    for trial in range(6):
+        n = 24
+        g = graphgen.random_graph(n, 30, seed=trial)
+        # brute force: reachability by repeated boolean products
+        R = np.eye(n, dtype=bool)
+        A = np.zeros((n, n), dtype=bool)
+        for j in range(n):
+            A[j, g.col[g.row_ptr[j]:g.row_ptr[j + 1]]] = True
+        for _ in range(n):
+            R = R | (R.astype(np.int64) @ A.astype(np.int64) > 0)
+        expect = np.array([np.nonzero(R[:, j])[0].max() for j in range(n)], dtype=np.int32)
+        np.testing.assert_array_equal(oracle.max_reach_labels(g), expect)
+        s = graphgen.symmetrize(g)
+        np.testing.assert_array_equal(oracle.max_reach_labels(s), oracle.component_labels(s))
