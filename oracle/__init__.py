@@ -51,6 +51,8 @@ def _load():
         lib.or_dijkstra.argtypes = [i64, P, P, P, ctypes.c_int32, P]
         lib.or_dijkstra.restype = i32
         lib.or_bellman_ford.argtypes = [i64, P, P, P, ctypes.c_int32, P]
+        lib.or_linear_power_edges.argtypes = [i64, P, P, P, P, d, i64, P]
+        lib.or_linear_power_edges.restype = i64
         lib.or_max_reach.argtypes = [i64, P, P, P]
         lib.or_max_reach.restype = i32
         lib.or_union_find_max.argtypes = [i64, P, P, P]
@@ -155,6 +157,22 @@ def katz(g, beta: float, s: int) -> np.ndarray:
     c[s] = 1.0
     v, _ = linear_power(g, np.full(g.n, float(beta)), c)
     return v
+
+
+def linear_power_edges(g, ecoef, c, tol: float = None, max_iter: int = 100000):
+    """Fixed point of v = c + M v with M[k, j] = sum of ecoef over the edges
+    j -> k, by synchronous iteration from v = 0 (the Jacobi row of Table 1).
+    tol defaults to 1e-13 * ||c||_1 on the L1 change.  Returns (v, iterations)."""
+    rp, col = _csr(g)
+    ecoef = np.ascontiguousarray(ecoef, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    if tol is None:
+        tol = 1e-13 * max(float(np.abs(c).sum()), 1e-300)
+    v = np.empty(g.n)
+    it = _load().or_linear_power_edges(g.n, _p(rp), _p(col), _p(ecoef), _p(c), tol, max_iter, _p(v))
+    if it < 0:
+        raise MemoryError("or_linear_power_edges")
+    return v, int(it)
 
 
 def solve_linear_system(A, b) -> np.ndarray:

@@ -11,6 +11,8 @@
  *                        v = c + P^T v (Eq. 1 with f affine, the PageRank update
  *                        of Eq. 2), by synchronous pull iteration (Section 2).
  *   or_linear_residual - one application of that update, r = c + P^T v - v.
+ *   or_linear_power_edges - the same fixed point with one coefficient per
+ *                        edge (the Jacobi row of Table 1, Section 4.3).
  *   or_daic_sum        - asynchronous DAIC with + (Eq. 5, receive/update), in
  *                        round-robin or priority order (Section 3.5).
  *   or_daic_min        - asynchronous DAIC with min (SSSP row of Table 1).
@@ -523,4 +525,34 @@ int or_union_find_max(int64_t n, const int64_t* row_ptr, const int32_t* col, int
   for (int64_t j = 0; j < n; ++j) label[j] = uf_find(parent, (int32_t)j);
   free(parent);
   return 0;
+}
+
+/* ----------------------------------------------- per-edge linear update */
+
+/*
+ * Synchronous iteration of v_k <- c_k + sum_{e = (j -> k)} ecoef_e * v_j from
+ * v = 0, edges taken in CSR order (the Jacobi method of Section 4.3 when
+ * ecoef_e = -A_kj / A_kk and c_k = b_k / A_kk).  Stops when the L1 change
+ * between two iterations is below tol, or after max_iter iterations.
+ * Returns the number of iterations, or -1 on allocation failure.
+ */
+int64_t or_linear_power_edges(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                              const double* ecoef, const double* c, double tol,
+                              int64_t max_iter, double* v_out) {
+  double* cur = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* nxt = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  if (!cur || !nxt) { free(cur); free(nxt); return -1; }
+  int64_t it = 0;
+  for (; it < max_iter; ++it) {
+    memcpy(nxt, c, (size_t)n * sizeof(double));
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t e = row_ptr[j]; e < row_ptr[j + 1]; ++e) nxt[col[e]] += ecoef[e] * cur[j];
+    double change = 0.0;
+    for (int64_t j = 0; j < n; ++j) change += fabs(nxt[j] - cur[j]);
+    double* t = cur; cur = nxt; nxt = t;
+    if (change < tol) { ++it; break; }
+  }
+  memcpy(v_out, cur, (size_t)n * sizeof(double));
+  free(cur); free(nxt);
+  return it;
 }

@@ -37,6 +37,35 @@ def test_linear_system_solution_by_hand():
     np.testing.assert_allclose(x, [0.1, 0.6], rtol=1e-14)
 
 
+def test_per_edge_iteration_solves_the_jacobi_system():
+    # A = [[4, 1, 0], [2, 5, 1], [0, 1, 3]], b = [1, 2, 3]: the Jacobi form has an
+    # edge j -> k with coefficient -A_kj / A_kk for each off-diagonal A_kj
+    A = np.array([[4.0, 1.0, 0.0], [2.0, 5.0, 1.0], [0.0, 1.0, 3.0]])
+    b = np.array([1.0, 2.0, 3.0])
+    edges, coef = [], []
+    for j in range(3):
+        for k in range(3):
+            if k != j and A[k, j] != 0.0:
+                edges.append((j, k))
+                coef.append(-A[k, j] / A[k, k])
+    g = graphgen.small_graph(3, edges)   # rows sorted by target, as listed above
+    x, it = oracle.linear_power_edges(g, np.array(coef), b / np.diag(A))
+    np.testing.assert_allclose(x, oracle.solve_linear_system(A, b), rtol=1e-12)
+    # the definition itself: A x = b
+    np.testing.assert_allclose(A @ x, b, rtol=1e-12)
+    assert it > 1
+
+
+def test_per_edge_iteration_equals_per_source_when_coefficients_agree():
+    g = graphgen.rmat(9, 4)
+    coef_src = np.where(np.diff(g.row_ptr) > 0, 0.8 / np.maximum(np.diff(g.row_ptr), 1), 0.0)
+    ecoef = np.repeat(coef_src, np.diff(g.row_ptr))
+    c = np.full(g.n, 0.2)
+    a, _ = oracle.linear_power_edges(g, ecoef, c)
+    b, _ = oracle.linear_power(g, coef_src, c)
+    np.testing.assert_allclose(a, b, rtol=1e-11)
+
+
 # ------------------------------------------ connected components (Table 1)
 
 def test_component_labels_by_hand():
