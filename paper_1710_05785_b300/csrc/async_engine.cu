@@ -51,6 +51,7 @@ struct AsyncPlan {
     a.n = static_cast<int>(g->n);
     a.rp = g->rp;
     a.edges.col = g->col;
+    a.edges.cw = g->cw;
     a.edges.w = g->w;
     a.coef = static_cast<const typename Op::C*>(coef);
     a.damping = damping;

@@ -22,6 +22,7 @@ struct EdgeCtx {
   const int* __restrict__ col;
   const uint32_t* __restrict__ w;
   const double* __restrict__ ecoef;   // per-edge coefficients (g = c_e x), or null
+  const uint2* __restrict__ cw;       // weighted graphs: (target, weight) pairs
 };
 
 __device__ __forceinline__ double atomic_take(double* p) {
@@ -181,7 +182,11 @@ struct OpMinU32 {
   __device__ static __forceinline__ bool live(Msg m) { return m != kInfU32; }
   struct Edge { int k; uint32_t w; };
   __device__ static __forceinline__ Edge load(const EdgeCtx& g, int64_t e) {
-    return Edge{__ldg(g.col + e), __ldg(g.w + e)};
+    if (g.cw) {
+      const uint2 x = __ldg(g.cw + e);
+      return Edge{static_cast<int>(x.x), x.y};
+    }
+    return Edge{__ldg(g.col + e), __ldg(g.w + e)};   // caller-owned arrays (no pairs)
   }
   __device__ static __forceinline__ void apply(Edge ed, Msg m, D* delta) {
     const uint32_t s = m + ed.w;
@@ -238,7 +243,11 @@ struct OpMinF32 {
   __device__ static __forceinline__ bool live(Msg m) { return m != kNone; }
   struct Edge { int k; uint32_t w; };
   __device__ static __forceinline__ Edge load(const EdgeCtx& g, int64_t e) {
-    return Edge{__ldg(g.col + e), __ldg(g.w + e)};
+    if (g.cw) {
+      const uint2 x = __ldg(g.cw + e);
+      return Edge{static_cast<int>(x.x), x.y};
+    }
+    return Edge{__ldg(g.col + e), __ldg(g.w + e)};   // caller-owned arrays (no pairs)
   }
   __device__ static __forceinline__ void apply(Edge ed, Msg m, D* delta) {
     const uint32_t nd = __float_as_uint(__fadd_rn(__uint_as_float(m), __uint_as_float(ed.w)));

@@ -66,6 +66,7 @@ struct maiter_graph {
   int* rp = nullptr;           // n + 1 int32 offsets
   int* col = nullptr;          // m targets
   uint32_t* w = nullptr;       // m weights or null
+  uint2* cw = nullptr;         // weighted graphs: (target, weight) per edge, one 8-byte load
   int* indeg = nullptr;        // in-degrees (computed on first use by the learned scorer)
   int wf32 = 0;                // w read as float: 0 unchecked, 1 finite and >= 0, 2 not
   int num_sms = 0;

@@ -63,6 +63,15 @@ __global__ void k_validate_col(const int* __restrict__ col, int64_t m, int64_t n
   }
 }
 
+// (target, weight) pairs of a weighted graph, so the min operators read each
+// edge with one 8-byte load.
+__global__ void k_interleave(const int* __restrict__ col, const uint32_t* __restrict__ w,
+                             int64_t m, uint2* __restrict__ cw) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < m;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    cw[e] = make_uint2(static_cast<uint32_t>(col[e]), w[e]);
+}
+
 }  // namespace maiter
 
 using namespace maiter;
@@ -111,6 +120,7 @@ void maiter_graph_destroy(maiter_graph* g) {
   cudaFree(g->rp);
   cudaFree(g->col);
   cudaFree(g->w);
+  cudaFree(g->cw);
   cudaFree(g->indeg);
   delete g;
 }
@@ -158,6 +168,7 @@ maiter_status maiter_graph_create(int64_t n, int64_t m, const int64_t* row_ptr,
   GC_CUDA(cudaMalloc(&g->rp, sizeof(int) * (n + 1)));
   GC_CUDA(cudaMalloc(&g->col, sizeof(int) * (m > 0 ? m : 1)));
   if (w) GC_CUDA(cudaMalloc(&g->w, sizeof(uint32_t) * (m > 0 ? m : 1)));
+  if (w) GC_CUDA(cudaMalloc(&g->cw, sizeof(uint2) * (m > 0 ? m : 1)));
   GC_CUDA(cudaMalloc(&rp64, sizeof(int64_t) * (n + 1)));
   GC_CUDA(cudaMalloc(&flag, sizeof(unsigned)));
   GC_CUDA(cudaMemset(flag, 0, sizeof(unsigned)));
@@ -167,6 +178,7 @@ maiter_status maiter_graph_create(int64_t n, int64_t m, const int64_t* row_ptr,
   const int blocks = g->num_sms * 4;
   k_validate_rowptr<<<blocks, 256>>>(rp64, n, m, g->rp, flag);
   if (m > 0) k_validate_col<<<blocks, 256>>>(g->col, m, n, flag);
+  if (w && m > 0) k_interleave<<<blocks, 256>>>(g->col, g->w, m, g->cw);
   GC_CUDA(cudaGetLastError());
   unsigned h_flag = 0;
   GC_CUDA(cudaMemcpy(&h_flag, flag, sizeof(unsigned), cudaMemcpyDeviceToHost));

@@ -52,6 +52,7 @@ struct Phase {
     a.edges.col = g->col;
     a.edges.w = g->w;
     a.edges.ecoef = r->ecoef;
+    a.edges.cw = g->cw;
     a.coef = static_cast<const typename Op::C*>(coef);
     a.damping = damping;
     a.v = static_cast<typename Op::V*>(r->v);
