@@ -158,6 +158,11 @@ template <class Op, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
   static_assert(BLOCK % 32 == 0 && BLOCK <= 1024, "block");
   using D = typename Op::D;
+  // Launched as a programmatic dependent of the kernel before it: wait until
+  // that grid's writes are visible (a no-op after an ordinary launch), and let
+  // the next kernel's CTAs be scheduled as this grid's CTAs retire.
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
   DevCtl* ctl = a.ctl;
   const unsigned ws = ctl->scan_set;
   const double tau = ctl->tau;
@@ -335,6 +340,8 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a,
                                                                 cudaGraphConditionalHandle cond,
                                                                 int use_cond) {
   using Msg = typename Op::Msg;
+  cudaGridDependencySynchronize();   // as in k_scan
+  cudaTriggerProgrammaticLaunchCompletion();
   DevCtl* ctl = a.ctl;
   const int lane = threadIdx.x & 31;
 

@@ -529,8 +529,13 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   // + 3 radix passes (TOPFRAC), + the scorer (LEARNED)
   const int per_round = (p->sched == MAITER_SCHED_TOPFRAC) ? 5
                         : (p->sched == MAITER_SCHED_LEARNED) ? 6 : 2;
-  s.kernel_launches +=
-      per_round * (static_cast<int64_t>(h.rounds) + phases) + (plan.mixed ? 1 : 0);
+  // graph mode runs whole passes of kRoundsPerPass rounds: the pass that
+  // decides to stop completes its remaining rounds (which push nothing)
+  constexpr int64_t kPass = Phase<OpSumF64>::kRoundsPerPass;
+  const int64_t rounds_run =
+      profile ? static_cast<int64_t>(h.rounds) + phases
+              : kPass * ((static_cast<int64_t>(h.rounds) + phases + kPass - 1) / kPass);
+  s.kernel_launches += per_round * rounds_run + (plan.mixed ? 1 : 0);
   s.status = h.status == 1 ? MAITER_OK : MAITER_ERR_NOT_CONVERGED;
   if (h.status != 1) {
     set_error("round cap of %lld reached before the termination test held (residual %g)",

@@ -86,14 +86,38 @@ struct Phase {
   }
 
   // One round: [selection passes], frontier scan, then the push, whose CTAs
-  // decide termination and set the WHILE condition.
-  void launch_round(cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) const {
+  // decide termination and set the WHILE condition.  With `chained`, the scan
+  // is launched as a programmatic dependent of the kernel before it; the push
+  // always is (of the scan): its CTAs are scheduled while the scan's retire
+  // and wait in griddepcontrol.wait for the scan's writes.
+  void launch_round(cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
+                    bool chained) const {
     launch_select(s);
-    k_scan<Op, kBlock><<<scan_grid, kBlock, 0, s>>>(a);
-    k_push<Op, kBlock><<<push_grid, kBlock, 0, s>>>(a, h, use_cond);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.blockDim = dim3(kBlock);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (chained && !a.topq) {
+      cfg.gridDim = dim3(scan_grid);
+      cudaLaunchKernelEx(&cfg, k_scan<Op, kBlock>, a);
+    } else {
+      k_scan<Op, kBlock><<<scan_grid, kBlock, 0, s>>>(a);
+    }
+    cfg.gridDim = dim3(push_grid);
+    cudaLaunchKernelEx(&cfg, k_push<Op, kBlock>, a, h, use_cond);
   }
 
-  // Adds WHILE(h) { [select] ; k_scan ; k_push } after `deps` (graph mode).
+  // Rounds per pass of the WHILE body: a push that follows a stopping decision
+  // decides the same way again (and gives back what its scan took), so a pass
+  // may hold several rounds and the loop condition is tested once per pass.
+  static constexpr int kRoundsPerPass = 2;
+
+  // Adds WHILE(h) { ([select] ; k_scan ; k_push) x kRoundsPerPass } after
+  // `deps` (graph mode).
   maiter_status add_to(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps,
                        cudaGraphConditionalHandle h, cudaGraphNode_t* node) const {
     cudaGraphNodeParams np{};
@@ -108,7 +132,7 @@ struct Phase {
     cudaError_t e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      launch_round(cap, h, 1);
+      for (int u = 0; u < kRoundsPerPass; ++u) launch_round(cap, h, 1, u > 0);
       cudaGraph_t captured = nullptr;
       e = cudaStreamEndCapture(cap, &captured);
     }
