@@ -228,6 +228,19 @@ maiter_status maiter_graph_create(int64_t n, int64_t m, const int64_t* row_ptr,
                                   const int32_t* col, const uint32_t* w, int device,
                                   maiter_graph** out);
 
+/* Replaces the contents of g with another CSR of the same n and m (and
+ * weights iff g has them), from host or device arrays, stream-ordered on
+ * `stream` (NULL = default stream; pinned host arrays copy asynchronously),
+ * then validates it like maiter_graph_create and returns after validation.
+ * Device buffers keep their addresses, so results created for g and their
+ * cached launch graphs stay valid: a stream of same-shaped inputs reuses
+ * them.  Quantities derived from the contents (in-degrees, the float-weight
+ * check) are recomputed on their next use.  The caller orders the update
+ * against runs of g on other streams.  Errors: INVALID_ARG (after which g
+ * refuses runs until a valid update), CUDA. */
+maiter_status maiter_graph_update(maiter_graph* g, const int64_t* row_ptr, const int32_t* col,
+                                  const uint32_t* w, void* stream);
+
 void maiter_graph_destroy(maiter_graph* g);
 
 /* Runs a DAIC to termination (Eq. 5 updates, Section 3.5 schedules).

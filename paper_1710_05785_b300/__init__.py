@@ -104,6 +104,8 @@ def lib():
                                           ctypes.POINTER(ctypes.c_void_p)]
         L.maiter_graph_create.restype = i32
         L.maiter_graph_destroy.argtypes = [P]
+        L.maiter_graph_update.argtypes = [P, P, P, P, P]
+        L.maiter_graph_update.restype = i32
         L.maiter_run.argtypes = [P, ctypes.POINTER(RunParams), ctypes.POINTER(ctypes.c_void_p)]
         L.maiter_run.restype = i32
         L.maiter_get_state.argtypes = [P, P, i64]
@@ -219,6 +221,22 @@ class Graph:
         self.handle = h
         self.n, self.m, self.device = n, m, device
         self.weighted = w is not None
+
+    def update(self, row_ptr, col, w=None, stream=None):
+        """``maiter_graph_update``: new contents of the same n and m (and
+        weights iff the graph has them), copied in place on ``stream``; results
+        of this graph stay valid."""
+        if isinstance(row_ptr, (np.ndarray, list, tuple)):
+            row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        if isinstance(col, (np.ndarray, list, tuple)):
+            col = np.ascontiguousarray(col, dtype=np.int32)
+        if isinstance(w, np.ndarray) and w.dtype == np.float32:
+            w = np.ascontiguousarray(w).view(np.uint32)
+        elif w is not None and isinstance(w, (np.ndarray, list, tuple)):
+            w = np.ascontiguousarray(w, dtype=np.uint32)
+        if int(len(row_ptr)) - 1 != self.n or int(len(col)) != self.m:
+            raise ValueError(f"update needs n = {self.n} and m = {self.m}")
+        _check(lib().maiter_graph_update(self.handle, _addr(row_ptr), _addr(col), _addr(w), stream))
 
     @classmethod
     def from_csr(cls, g, device: int = 0):

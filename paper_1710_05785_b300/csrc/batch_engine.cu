@@ -590,6 +590,7 @@ maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_gr
   MAITER_REQUIRE(num_graphs >= 1 && num_queries >= 1, "need at least one graph and one query");
   for (int i = 0; i < num_graphs; ++i) {
     MAITER_REQUIRE(graphs[i], "graph %d is NULL", i);
+    MAITER_REQUIRE(!graphs[i]->invalid, "graph %d: its last update failed validation", i);
     MAITER_REQUIRE(graphs[i]->device == graphs[0]->device, "all graphs must be on one device");
   }
   MAITER_REQUIRE(p->cut_large >= 0 && p->chunk >= 0 && (p->chunk == 0 || p->chunk >= 32),

@@ -69,6 +69,9 @@ struct maiter_graph {
   uint2* cw = nullptr;         // weighted graphs: (target, weight) per edge, one 8-byte load
   int* indeg = nullptr;        // in-degrees (computed on first use by the learned scorer)
   int wf32 = 0;                // w read as float: 0 unchecked, 1 finite and >= 0, 2 not
+  int64_t* rp64 = nullptr;     // staging of the int64 offsets (kept after the first update)
+  unsigned* flag = nullptr;    // validation flags (kept after the first update)
+  bool invalid = false;        // the last update failed validation: no runs
   int num_sms = 0;
 };
 

@@ -121,6 +121,8 @@ void maiter_graph_destroy(maiter_graph* g) {
   cudaFree(g->col);
   cudaFree(g->w);
   cudaFree(g->cw);
+  cudaFree(g->rp64);
+  cudaFree(g->flag);
   cudaFree(g->indeg);
   delete g;
 }
@@ -194,6 +196,47 @@ maiter_status maiter_graph_create(int64_t n, int64_t m, const int64_t* row_ptr,
   cudaFree(rp64);
   cudaFree(flag);
   *out = g;
+  return MAITER_OK;
+}
+
+maiter_status maiter_graph_update(maiter_graph* g, const int64_t* row_ptr, const int32_t* col,
+                                  const uint32_t* w, void* stream) {
+  begin_call();
+  MAITER_REQUIRE(g && row_ptr, "maiter_graph_update: NULL argument");
+  MAITER_REQUIRE(g->m == 0 || col, "col is NULL with m > 0");
+  MAITER_REQUIRE((w != nullptr) == (g->w != nullptr),
+                 "weights must be given exactly when the graph has them");
+  DeviceGuard guard(g->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = g->n, m = g->m;
+  if (!g->rp64) MAITER_CUDA(cudaMalloc(&g->rp64, sizeof(int64_t) * (n + 1)));
+  if (!g->flag) MAITER_CUDA(cudaMalloc(&g->flag, sizeof(unsigned)));
+  g->invalid = true;   // until this content has been validated
+  MAITER_CUDA(cudaMemsetAsync(g->flag, 0, sizeof(unsigned), st));
+  MAITER_CUDA(cudaMemcpyAsync(g->rp64, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDefault, st));
+  if (m > 0) MAITER_CUDA(cudaMemcpyAsync(g->col, col, sizeof(int) * m, cudaMemcpyDefault, st));
+  if (w && m > 0) MAITER_CUDA(cudaMemcpyAsync(g->w, w, sizeof(uint32_t) * m, cudaMemcpyDefault, st));
+  const int blocks = g->num_sms * 4;
+  k_validate_rowptr<<<blocks, 256, 0, st>>>(g->rp64, n, m, g->rp, g->flag);
+  if (m > 0) k_validate_col<<<blocks, 256, 0, st>>>(g->col, m, n, g->flag);
+  if (w && m > 0) k_interleave<<<blocks, 256, 0, st>>>(g->col, g->w, m, g->cw);
+  MAITER_CUDA(cudaGetLastError());
+  unsigned h_flag = 0;
+  MAITER_CUDA(cudaMemcpyAsync(&h_flag, g->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  MAITER_CUDA(cudaStreamSynchronize(st));
+  // contents changed: derived data is recomputed on its next use
+  cudaFree(g->indeg);
+  g->indeg = nullptr;
+  g->wf32 = 0;
+  if (h_flag & 1u) {
+    set_error("row_ptr must start at 0, be non-decreasing and end at m = %lld", (long long)m);
+    return MAITER_ERR_INVALID_ARG;
+  }
+  if (h_flag & 2u) {
+    set_error("col holds a target outside [0, n = %lld)", (long long)n);
+    return MAITER_ERR_INVALID_ARG;
+  }
+  g->invalid = false;
   return MAITER_OK;
 }
 
@@ -653,6 +696,7 @@ namespace maiter {
 static maiter_status run_impl(const maiter_graph* g, const maiter_run_params* p, maiter_result** out,
                               TraceSink* trace) {
   MAITER_REQUIRE(g && p && out, "maiter_run: NULL argument");
+  MAITER_REQUIRE(!g->invalid, "the graph's last update failed validation");
   MAITER_REQUIRE(p->op >= MAITER_OP_SUM_F64 && p->op <= MAITER_OP_MAX_I32, "unknown op %d", p->op);
   const bool is_sum = !is_order_op(p->op);
   if (p->op == MAITER_OP_MAX_I32 &&
