@@ -183,7 +183,7 @@ struct OpMinU32 {
   struct Edge { int k; uint32_t w; };
   __device__ static __forceinline__ Edge load(const EdgeCtx& g, int64_t e) {
     if (g.cw) {
-      const uint2 x = __ldg(g.cw + e);
+      const uint2 x = __ldcs(g.cw + e);   // streamed: leave L1 to the filter reads
       return Edge{static_cast<int>(x.x), x.y};
     }
     return Edge{__ldg(g.col + e), __ldg(g.w + e)};   // caller-owned arrays (no pairs)
@@ -191,7 +191,9 @@ struct OpMinU32 {
   __device__ static __forceinline__ void apply(Edge ed, Msg m, D* delta) {
     const uint32_t s = m + ed.w;
     const uint32_t nd = (s < m) ? kInfU32 : s;  // saturate: an overflowing message is infinity
-    if (nd < __ldcg(delta + ed.k)) atomicMin(delta + ed.k, nd);
+    // The filter read may come from L1: Delta only decreases, so a stale
+    // value is larger and the test can only let an extra atomic through.
+    if (nd < __ldca(delta + ed.k)) atomicMin(delta + ed.k, nd);
   }
   __device__ static __forceinline__ void scatter(const EdgeCtx& g, int64_t e, Msg m, D* delta) {
     apply(load(g, e), m, delta);
@@ -244,14 +246,16 @@ struct OpMinF32 {
   struct Edge { int k; uint32_t w; };
   __device__ static __forceinline__ Edge load(const EdgeCtx& g, int64_t e) {
     if (g.cw) {
-      const uint2 x = __ldg(g.cw + e);
+      const uint2 x = __ldcs(g.cw + e);   // streamed: leave L1 to the filter reads
       return Edge{static_cast<int>(x.x), x.y};
     }
     return Edge{__ldg(g.col + e), __ldg(g.w + e)};   // caller-owned arrays (no pairs)
   }
   __device__ static __forceinline__ void apply(Edge ed, Msg m, D* delta) {
     const uint32_t nd = __float_as_uint(__fadd_rn(__uint_as_float(m), __uint_as_float(ed.w)));
-    if (nd < __ldcg(delta + ed.k)) atomicMin(delta + ed.k, nd);
+    // The filter read may come from L1: Delta only decreases, so a stale
+    // value is larger and the test can only let an extra atomic through.
+    if (nd < __ldca(delta + ed.k)) atomicMin(delta + ed.k, nd);
   }
   __device__ static __forceinline__ void scatter(const EdgeCtx& g, int64_t e, Msg m, D* delta) {
     apply(load(g, e), m, delta);
