@@ -234,3 +234,26 @@ def test_invalid_arguments_are_rejected(mt):
         mt.run(G, mt.OP_MIN_U32, source=0)
     with pytest.raises(mt.MaiterError):   # bad eps
         mt.run(G, mt.OP_SUM_F64, eps=-1.0)
+
+
+@pytest.mark.parametrize("cap", [1, 2, 3, 4, 5])
+def test_round_cap_in_either_position_of_a_pass(mt, cap):
+    # the graph loop runs two rounds per pass; a cap that falls on either of
+    # them stops after exactly `cap` pushes with a valid DAIC state that resumes
+    g = graphgen.rmat(11, 8, weights=True)
+    G = mt.Graph.from_csr(g)
+    r = mt.run(G, mt.OP_SUM_F64, eps=1e-10, max_rounds=cap, allow_not_converged=True)
+    st = r.stats()
+    assert st["rounds"] == cap and st["status"] == mt.ERR_NOT_CONVERGED
+    v, dl = r.state(), r.delta()
+    dangling = np.diff(g.row_ptr) == 0
+    assert abs(oracle.pagerank_mass_invariant(v, dl, v[dangling].sum(), g.n, D)) < 1e-9 * g.n
+    r2 = mt.run(G, mt.OP_SUM_F64, v0=v, delta0=dl, eps=1e-10)
+    assert oracle.relative_error(r2.state(), oracle.pagerank(g, D)) <= TOL
+    s = int(graphgen.sssp_sources(g, 1)[0])
+    q = mt.run(G, mt.OP_MIN_U32, source=s, max_rounds=cap, allow_not_converged=True)
+    assert q.stats()["rounds"] == cap
+    exact = oracle.dijkstra(g, s)
+    assert (q.state() >= exact).all()            # never below the true distance
+    q2 = mt.run(G, mt.OP_MIN_U32, v0=q.state(), delta0=q.delta())
+    np.testing.assert_array_equal(q2.state(), exact)
