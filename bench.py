@@ -56,6 +56,21 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
+def random_access(mt, kind, n, device, edge_ops, push_ms, what):
+    """The push's edge loop against the rate this device sustains for
+    single-word operations at random addresses of an array of Delta's size
+    (maiter_probe_random_rate, measured now): every edge push makes one such
+    operation on Delta_k, so this is the ceiling of the edge loop while Delta
+    fits in L2, where the DRAM roofline says little."""
+    lg = max(10, min(28, int(np.ceil(np.log2(max(n, 2))))))
+    ceiling = mt.probe_random_rate(kind, lg, device)
+    achieved = edge_ops / (push_ms * 1e-3) / 1e9
+    return {"achieved_gops": achieved, "ceiling_gops": ceiling,
+            "frac": achieved / ceiling if ceiling > 0 else None,
+            "ceiling_kind": f"measured: {what} at random addresses of 2^{lg} words",
+            "unit": "G edge pushes/s vs G ops/s"}
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -247,7 +262,11 @@ def run_pagerank(args, wl):
                      "push_launches": prof["push_launches"],
                      "push_ms_per_launch": prof["push_ms"] / max(prof["push_launches"], 1),
                      "scan_ms_per_launch": prof["scan_ms"] / max(prof["scan_launches"], 1),
-                     "alg_bytes_per_launch": alg / max(prof["push_launches"], 1)},
+                     "alg_bytes_per_launch": alg / max(prof["push_launches"], 1),
+                     "random_access": random_access(
+                         mt, mt.PROBE_RED_F64 if cfg["op"] == "f64" else mt.PROBE_RED_F32, g.n,
+                         local, prof["edge_pushes"], prof["push_ms"],
+                         "f64 atomicAdd" if cfg["op"] == "f64" else "f32 atomicAdd")},
         "gpu_launches": int(sum(v["kernel_launches"] for v in results.values())),
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -811,7 +830,12 @@ def main():
                      "push_launches": push_launches,
                      "push_ms_per_launch": push_ms / max(push_launches, 1),
                      "scan_ms_per_launch": sum(p["scan_ms"] for p in prof) / max(push_launches, 1),
-                     "alg_bytes_per_launch": alg_bytes / max(push_launches, 1)},
+                     "alg_bytes_per_launch": alg_bytes / max(push_launches, 1),
+                     # each edge push reads Delta_k once (the filter); the
+                     # atomicMin follows only where the distance improves
+                     "random_access": random_access(
+                         mt, mt.PROBE_LOAD_32, g.n, local,
+                         sum(p["edge_pushes"] for p in prof), push_ms, "4-byte L2 loads")},
         "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "variants": variants,

@@ -421,6 +421,26 @@ const char* maiter_version(void);
  * key tuning caches.  Errors: INVALID_ARG, CUDA. */
 maiter_status maiter_device_info(int device, char* name, int32_t len, int32_t* num_sms);
 
+/* Diagnostic: the rate at which `device` serves 4- or 8-byte operations at
+ * random addresses of a device array of 2^log2_words elements (an integer
+ * hash of (thread, iteration) picks each address; a grid of one wave of
+ * 256-thread CTAs, 256 operations per thread).  The push kernels issue such
+ * operations on Delta_k (k a random vertex id), so this rate at the size of
+ * a workload's Delta array is the ceiling their edge loop is held to while
+ * the array fits in L2.  The array is allocated, zeroed (all ones for MIN)
+ * and freed by the call, on a stream of its own.  *gops receives operations
+ * per second / 1e9, best of three launches after one warm-up.
+ * Errors: INVALID_ARG (NULL gops, unknown kind, log2_words outside
+ * [10, 28], bad device), OOM, CUDA. */
+typedef enum {
+  MAITER_PROBE_RED_F32 = 0,  /* atomicAdd of a float, result unused (RED) */
+  MAITER_PROBE_RED_F64 = 1,  /* atomicAdd of a double, result unused */
+  MAITER_PROBE_MIN_U32 = 2,  /* atomicMin of a uint32, result unused */
+  MAITER_PROBE_LOAD_32 = 3   /* 4-byte load cached in L2 only */
+} maiter_probe_kind;
+
+maiter_status maiter_probe_random_rate(int device, int kind, int log2_words, double* gops);
+
 #ifdef __cplusplus
 }
 #endif

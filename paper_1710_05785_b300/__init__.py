@@ -36,6 +36,8 @@ SCHED_ALL, SCHED_THRESHOLD, SCHED_TOPFRAC, SCHED_LEARNED, SCHED_BUCKET = 0, 1, 2
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 8, 64, 641
 ENGINE_SYNC, ENGINE_ASYNC = 0, 1
 FLAG_PROFILE_KERNELS, FLAG_INJECT_STALL = 1, 2
+# maiter_probe_kind
+PROBE_RED_F32, PROBE_RED_F64, PROBE_MIN_U32, PROBE_LOAD_32 = 0, 1, 2, 3
 
 INF32 = 0xFFFFFFFF
 
@@ -132,6 +134,9 @@ def lib():
         L.maiter_batch_destroy.argtypes = [P]
         L.maiter_device_info.argtypes = [ctypes.c_int, ctypes.c_char_p, i32, ctypes.POINTER(i32)]
         L.maiter_device_info.restype = i32
+        L.maiter_probe_random_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_double)]
+        L.maiter_probe_random_rate.restype = i32
         L.maiter_mlp_create.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]
         L.maiter_mlp_create.restype = i32
         L.maiter_mlp_set_params.argtypes = [P, P]
@@ -522,6 +527,14 @@ def device_info(device: int = 0) -> tuple[str, int]:
     sms = ctypes.c_int32(0)
     _check(lib().maiter_device_info(device, buf, 256, ctypes.byref(sms)))
     return buf.value.decode(), sms.value
+
+
+def probe_random_rate(kind: int, log2_words: int, device: int = 0) -> float:
+    """Random-address operations per second / 1e9 that the device sustains
+    into an array of 2**log2_words elements (``maiter_probe_random_rate``)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().maiter_probe_random_rate(device, kind, log2_words, ctypes.byref(out)))
+    return out.value
 
 
 def version() -> str:

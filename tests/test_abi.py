@@ -106,3 +106,10 @@ def test_oracle_and_cuda_path_share_no_code():
         if f.endswith((".c", ".py")):
             text = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_1710_05785_b300" not in text and "csrc" not in text, f
+
+
+def test_probe_rejects_bad_arguments_before_any_device_work(mt):
+    for kind, lg in [(4, 20), (-1, 20), (mt.PROBE_RED_F32, 9), (mt.PROBE_LOAD_32, 29)]:
+        with pytest.raises(mt.MaiterError) as ei:
+            mt.probe_random_rate(kind, lg)
+        assert ei.value.status == mt.ERR_INVALID_ARG
