@@ -462,7 +462,7 @@ static maiter_status dense_run(maiter_batch* b, const maiter_batch_params* p,
     s.activations += static_cast<int64_t>(h.activations);
     s.edge_pushes += static_cast<int64_t>(h.pushes);
     s.residual = std::max(s.residual, h.residual);
-    s.kernel_launches += 2 + 2 * (static_cast<int64_t>(h.rounds) + 1);
+    s.kernel_launches += 2 + (profile ? 3 : 2) * (static_cast<int64_t>(h.rounds) + 1);
     if (h.status != 1) worst = h.status;
   }
   s.converged = worst == 1;

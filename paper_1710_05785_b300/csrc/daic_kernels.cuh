@@ -31,7 +31,12 @@ namespace maiter {
 constexpr int kBuckets = 3;
 constexpr int kChunk = 1024;   // edges per large-vertex work item (one CTA, 4 per thread)
 constexpr int kUnroll = 4;
-constexpr int kScanItems = 8;  // vertices per thread per k_scan tile
+// k_scan tiles: 4 vertices per thread, and at most 40 registers so that six
+// 256-thread CTAs fit an SM.  Measured on B300 against 2, 8 and 16 items and
+// against oversubscribed grids: the scan is one wave of short dependent
+// chains, and fewer items per thread shorten each chain.
+constexpr int kScanItems = 4;
+constexpr int kScanMinBlocks = 6;
 
 // Device-resident control block of one run.  Everything the round loop needs
 // to decide on its own lives here, so the loop never returns to the host.
@@ -155,7 +160,7 @@ __device__ __forceinline__ int warp_incl_scan(int x, int lane) {
 // ------------------------------------------------------------------ scan
 
 template <class Op, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
+__global__ void __launch_bounds__(BLOCK, kScanMinBlocks) k_scan(KArgs<Op> a) {
   static_assert(BLOCK % 32 == 0 && BLOCK <= 1024, "block");
   using D = typename Op::D;
   // Launched as a programmatic dependent of the kernel before it: wait until
@@ -173,12 +178,18 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
   constexpr int kItems = kScanItems;         // vertices per thread per tile
   constexpr int kTile = BLOCK * kItems;
 
+  // Per-thread, per-warp and per-block counts fit 32 bits: they are bounded
+  // by n or m, both below 2^31 (int32 row offsets).
   double rsum = 0.0;
-  unsigned long long nact = 0, npush = 0, npend = 0;
+  unsigned nact = 0, npush = 0, npend = 0;
   unsigned dmin = 0xFFFFFFFFu;               // min: smallest pending Delta seen (bits)
   const bool bucket = !Op::kIsSum && a.bucket;
-  __shared__ int s_woff[3][kWarps];          // per-warp exclusive offsets, per bucket
+  // per-warp exclusive offsets: [0] small and medium counts packed in the
+  // two 16-bit halves of one int (a tile holds kTile < 2^16 vertices), [1]
+  // large-vertex chunks
+  __shared__ int s_woff[2][kWarps];
   __shared__ unsigned s_base[3];             // the tile's base position, per bucket
+  static_assert(kTile < 65536, "packed small/medium counts");
 
   // Each block walks tiles of kTile consecutive vertices (item u of thread t
   // is vertex tile + u*BLOCK + t: coalesced).  A tile's selections are
@@ -239,17 +250,18 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
         cnt[1] += (b == 1);
         cnt[2] += (b == 2) ? (deg + kChunk - 1) / kChunk : 0;
         ++nact;
-        npush += static_cast<unsigned long long>(deg);
+        npush += static_cast<unsigned>(deg);
       }
     }
-    int incl[3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      incl[b] = warp_incl_scan(cnt[b], lane);
-      if (lane == 31) s_woff[b][wid] = incl[b];
+    const int c01 = cnt[0] | (cnt[1] << 16);
+    const int i01 = warp_incl_scan(c01, lane);
+    const int i2 = warp_incl_scan(cnt[2], lane);
+    if (lane == 31) {
+      s_woff[0][wid] = i01;
+      s_woff[1][wid] = i2;
     }
     __syncthreads();
-    if (threadIdx.x < 3) {
+    if (threadIdx.x < 2) {
       const int b = threadIdx.x;
       int run = 0;
       for (int w = 0; w < kWarps; ++w) {
@@ -257,13 +269,21 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
         s_woff[b][w] = run;
         run += t;
       }
-      s_base[b] = run ? atomicAdd(&ctl->cnt[ws][b], static_cast<unsigned>(run)) : 0u;
+      if (b == 0) {
+        const unsigned r0 = static_cast<unsigned>(run) & 0xFFFFu;
+        const unsigned r1 = static_cast<unsigned>(run) >> 16;
+        s_base[0] = r0 ? atomicAdd(&ctl->cnt[ws][0], r0) : 0u;
+        s_base[1] = r1 ? atomicAdd(&ctl->cnt[ws][1], r1) : 0u;
+      } else {
+        s_base[2] = run ? atomicAdd(&ctl->cnt[ws][2], static_cast<unsigned>(run)) : 0u;
+      }
     }
     __syncthreads();
+    const unsigned e01 = static_cast<unsigned>(s_woff[0][wid] + i01 - c01);
     unsigned pos[3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-      pos[b] = s_base[b] + static_cast<unsigned>(s_woff[b][wid] + incl[b] - cnt[b]);
+    pos[0] = s_base[0] + (e01 & 0xFFFFu);
+    pos[1] = s_base[1] + (e01 >> 16);
+    pos[2] = s_base[2] + static_cast<unsigned>(s_woff[1][wid] + i2 - cnt[2]);
 #pragma unroll
     for (int u = 0; u < kItems; ++u) {
       const int j = tile + u * BLOCK + static_cast<int>(threadIdx.x);
@@ -292,26 +312,25 @@ __global__ void __launch_bounds__(BLOCK) k_scan(KArgs<Op> a) {
   // Block reduction, one fire-and-forget atomic per block per counter; the
   // push reads the totals after this kernel ends.
   __shared__ double s_r[BLOCK / 32];
-  __shared__ unsigned long long s_a[BLOCK / 32], s_p[BLOCK / 32], s_q[BLOCK / 32];
-  __shared__ unsigned s_m[BLOCK / 32];
-  rsum = warp_sum(rsum);
-  nact = warp_sum(nact);
-  npush = warp_sum(npush);
-  npend = warp_sum(npend);
+  __shared__ unsigned s_a[BLOCK / 32], s_p[BLOCK / 32], s_q[BLOCK / 32], s_m[BLOCK / 32];
+  if constexpr (Op::kIsSum) rsum = warp_sum(rsum);
+  nact = __reduce_add_sync(0xffffffffu, nact);
+  npush = __reduce_add_sync(0xffffffffu, npush);
+  npend = __reduce_add_sync(0xffffffffu, npend);
   if (bucket) dmin = __reduce_min_sync(0xffffffffu, dmin);
   if (lane == 0) { s_r[wid] = rsum; s_a[wid] = nact; s_p[wid] = npush; s_q[wid] = npend; s_m[wid] = dmin; }
   __syncthreads();
   if (threadIdx.x == 0) {
     double r = 0.0;
-    unsigned long long x = 0, y = 0, z = 0;
+    unsigned x = 0, y = 0, z = 0;
     unsigned mn = 0xFFFFFFFFu;
     for (int i = 0; i < BLOCK / 32; ++i) {
       r += s_r[i]; x += s_a[i]; y += s_p[i]; z += s_q[i]; mn = min(mn, s_m[i]);
     }
     if (Op::kIsSum && r != 0.0) atomicAdd(&ctl->resid_acc[ws], r);
-    if (x) atomicAdd(&ctl->act_acc[ws], x);
-    if (y) atomicAdd(&ctl->push_acc[ws], y);
-    if (z) atomicAdd(&ctl->pend_acc[ws], z);
+    if (x) atomicAdd(&ctl->act_acc[ws], static_cast<unsigned long long>(x));
+    if (y) atomicAdd(&ctl->push_acc[ws], static_cast<unsigned long long>(y));
+    if (z) atomicAdd(&ctl->pend_acc[ws], static_cast<unsigned long long>(z));
     if (bucket && mn != 0xFFFFFFFFu) atomicMin(&ctl->minpend_acc[ws], mn);
     if (blockIdx.x == 0) ctl->push_set = ws;
   }
@@ -519,6 +538,21 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a,
 }
 
 // ------------------------------------------------------------- utilities
+
+// Holds the stream for about `ns` nanoseconds (by the global timer, and at
+// most kHoldIters sleeps in any case), so that the launches the host enqueues
+// behind it are queued before the GPU reaches them: per-kernel event pairs
+// recorded after the hold then time the kernels, not host launch latency.
+constexpr int kHoldIters = 100000;
+static __global__ void k_hold(unsigned long long ns) {
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (int i = 0; i < kHoldIters; ++i) {
+    __nanosleep(1000);
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 >= ns) break;
+  }
+}
 
 // Mixed precision: the end of the FP64-delta warm-up phase.  Rounds every
 // delta to FP32 once and re-arms the control block for the FP32 phase, which

@@ -569,9 +569,10 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   s.converged = h.status == 1;
   // every phase that ran ends with one scan that did not continue
   const int64_t phases = 1 + (h.phase > 0 ? 1 : 0);
-  // + 3 radix passes (TOPFRAC), + the scorer (LEARNED)
-  const int per_round = (p->sched == MAITER_SCHED_TOPFRAC) ? 5
-                        : (p->sched == MAITER_SCHED_LEARNED) ? 6 : 2;
+  // + 3 radix passes (TOPFRAC), + the scorer (LEARNED), + the hold that
+  // starts every round of the host-driven profiling loop
+  const int per_round = ((p->sched == MAITER_SCHED_TOPFRAC) ? 5
+                         : (p->sched == MAITER_SCHED_LEARNED) ? 6 : 2) + (profile ? 1 : 0);
   // graph mode runs whole passes of kRoundsPerPass rounds: the pass that
   // decides to stop completes its remaining rounds (which push nothing)
   constexpr int64_t kPass = Phase<OpSumF64>::kRoundsPerPass;

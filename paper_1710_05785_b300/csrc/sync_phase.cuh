@@ -16,6 +16,8 @@ inline int grid_for(const void* fn, int block, int num_sms, int per_sm_cap) {
 }
 
 constexpr int kBlock = 256;
+// per-round hold of the host-driven (profiling) loop
+constexpr unsigned long long kHoldNs = 40000;
 
 // Device buffers that a traced run fills, one row per (record, sampled vertex).
 struct TraceSink {
@@ -146,6 +148,9 @@ struct Phase {
   maiter_status host_loop(maiter_result* r, cudaStream_t st, cudaEvent_t* e, maiter_stats& s,
                           TraceSink* trace = nullptr) const {
     for (;;) {
+      // the round's launches queue up behind the hold (the host syncs on
+      // every round, so without it e[0] would fire while the GPU idles)
+      k_hold<<<1, 32, 0, st>>>(kHoldNs);
       MAITER_CUDA(cudaEventRecord(e[0], st));
       launch_select(st);
       k_scan<Op, kBlock><<<scan_grid, kBlock, 0, st>>>(a);
