@@ -581,7 +581,9 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
               : kPass * ((static_cast<int64_t>(h.rounds) + phases + kPass - 1) / kPass);
   s.kernel_launches += per_round * rounds_run + (plan.mixed ? 1 : 0);
   s.status = h.status == 1 ? MAITER_OK : MAITER_ERR_NOT_CONVERGED;
-  if (h.status != 1) {
+  if (h.status == 3) {
+    set_error("a large-vertex chunk list outgrew its capacity (residual %g)", h.residual);
+  } else if (h.status != 1) {
     set_error("round cap of %lld reached before the termination test held (residual %g)",
               (long long)c.max_rounds, h.residual);
   }
