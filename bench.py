@@ -195,7 +195,9 @@ def run_pagerank(args, wl):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev).cuda_stream
-    cfg = PR_WORKLOADS[wl]
+    cfg = dict(PR_WORKLOADS[wl])
+    if args.scale:
+        cfg["scale"] = args.scale   # a smaller case of the same kernels (profiling)
     g = graphgen.rmat(cfg["scale"], cfg["ef"])
     G = mt.Graph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev), device=local)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
@@ -211,6 +213,8 @@ def run_pagerank(args, wl):
         # queue latency per update, see the scale-13 line); left out here
         del variants["f64_async"]
     head = "plain_f64_sync" if cfg["op"] == "f64" else "mixed_sync"
+    if args.head_only:
+        variants = {head: variants[head]}
     results = {}
     res = {}
 
@@ -230,7 +234,7 @@ def run_pagerank(args, wl):
         results[name] = dict(time_to_tolerance_ms=t, rounds=st[-1]["rounds"],
                              edge_pushes=st[-1]["edge_pushes"], residual=st[-1]["residual"],
                              kernel_launches=st[-1]["kernel_launches"], stats=st[-1])
-    plain_t = results["plain_f64_sync"]["time_to_tolerance_ms"]
+    plain_t = results.get("plain_f64_sync", {}).get("time_to_tolerance_ms")
     hs = results[head]
     ms = hs["time_to_tolerance_ms"]
     prof = mt.run(G, eps=eps, damping=D_PR, stream=stream, flags=mt.FLAG_PROFILE_KERNELS,
@@ -253,7 +257,7 @@ def run_pagerank(args, wl):
                    "n": g.n, "m": g.m, "eps": eps, "headline": head,
                    "l2": f"{L2_FLUSH_BYTES >> 20} MiB write before every run"},
         "time_to_tolerance_ms": ms,
-        "vs_plain_form": plain_t / ms,
+        "vs_plain_form": plain_t / ms if plain_t else None,
         "variants": {k: {kk: vv for kk, vv in v.items() if kk != "stats"} for k, v in results.items()},
         "gteps_work": hs["edge_pushes"] / (ms * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "kernel": "k_push<OpSum>", "achieved": achieved,
@@ -279,7 +283,7 @@ def run_pagerank(args, wl):
             oracle.linear_power(g, coef, c, tol=0.0, max_iter=1)
             it += 1
         per_iter = (time.perf_counter() - t0) / it
-        rounds = results["plain_f64_sync"]["rounds"]
+        rounds = results.get("plain_f64_sync", results[head])["rounds"]
         line["cpu_baseline"] = {
             "value": g.m / (per_iter * rounds) / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
             "sample": f"{it} synchronous iterations of the oracle over the full graph "
@@ -654,6 +658,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--scale", type=int, default=0,
+                    help="PageRank workloads: R-MAT scale instead of the configuration's "
+                         "(a smaller case of the same kernels, for profiling)")
+    ap.add_argument("--head-only", action="store_true",
+                    help="PageRank workloads: time only the headline variant")
     ap.add_argument("--workload", default="sssp-rmat20",
                     choices=["sssp-rmat20", "batch", "learned"] + sorted(PR_WORKLOADS)
                     + ROW_WORKLOADS,
