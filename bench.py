@@ -705,15 +705,19 @@ def main():
     G = mt.Graph(rp_d, col_d, w_d, device=local)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
-    res = [None]
-    stats = []
+    # One step: the 8 sources one after another, chained inside one graph
+    # launch (maiter_run_batch, dense mode 2: each query is a round-engine run
+    # of its own, started when the one before it has stopped).
+    queries = [dict(op=mt.OP_MIN_U32, graph=0, seeds=[s]) for s in sources]
+    bat = [None]
+    stats, qrounds = [], []
 
     def step(record=False):
-        for s in sources:
-            res[0] = mt.run(G, mt.OP_MIN_U32, source=s, result=res[0],
-                            stream=stream.cuda_stream)
-            if record:
-                stats.append(res[0].stats())
+        bat[0] = mt.run_batch([G], queries, stream=stream.cuda_stream,
+                              mode=mt.BATCH_DENSE_CHAINED, batch=bat[0])
+        if record:
+            stats.append(bat[0].stats())
+            qrounds.append(bat[0].query_rounds())
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -774,6 +778,31 @@ def main():
     }
     variants = {"plain_sync": {"ms_per_8_sources": ms_per_step,
                                "edge_pushes": int(sum(s["edge_pushes"] for s in stats) / args.steps)}}
+    # the same 8 sources as 8 maiter_run calls (a host round trip after each
+    # run), and as one batch whose 8 runs go side by side (mode 0)
+    tts = []
+    for name in ("separate_runs", "batch8_side_by_side"):
+        best = None
+        rv = None
+        for rep in range(3):
+            flush.fill_(rep)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if name == "separate_runs":
+                for s in sources:
+                    rv = mt.run(G, mt.OP_MIN_U32, source=s, result=rv, stream=stream.cuda_stream)
+                    if rep == 2:
+                        tts.append(rv.stats()["elapsed_ms"])
+            else:
+                rv = mt.run_batch([G], queries, stream=stream.cuda_stream, mode=mt.BATCH_DENSE,
+                                  batch=rv)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                t = e0.elapsed_time(e1)
+                best = t if best is None else min(best, t)
+        rv.close()
+        variants[name] = {"ms_per_8_sources": best, "vs_plain": ms_per_step / best}
     for name, kw in variant_kw.items():
         rv = None
         best, pushes = None, 0
@@ -793,8 +822,8 @@ def main():
 
     # end to end through the C ABI from pinned host buffers, per step: upload
     # the CSR into the graph's buffers (maiter_graph_update; the buffers and
-    # the result are allocated once, before the timed steps), run the 8
-    # sources, read every distance vector back
+    # the batch are allocated once, before the timed steps), run the 8
+    # sources chained in one launch, read every distance vector back
     rp_h = torch.from_numpy(g.row_ptr).pin_memory()
     col_h = torch.from_numpy(g.col).pin_memory()
     w_h = torch.from_numpy(g.w.view(np.int32)).pin_memory()
@@ -803,14 +832,15 @@ def main():
     d2h = NSRC * g.n * 4
     e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
     Gh = mt.Graph(rp_h, col_h, w_h, device=local)
-    rr = mt.run(Gh, mt.OP_MIN_U32, source=sources[0], stream=stream.cuda_stream)
+    rr = mt.run_batch([Gh], queries, stream=stream.cuda_stream, mode=mt.BATCH_DENSE_CHAINED)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         Gh.update(rp_h, col_h, w_h, stream=stream.cuda_stream)
-        for s in sources:
-            rr = mt.run(Gh, mt.OP_MIN_U32, source=s, result=rr, stream=stream.cuda_stream)
-            rr.state(out_h)
+        rr = mt.run_batch([Gh], queries, stream=stream.cuda_stream,
+                          mode=mt.BATCH_DENSE_CHAINED, batch=rr)
+        for i in range(len(sources)):
+            rr.state(i, out_h)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / max(e2e_steps, 1)
     rr.close()
@@ -818,7 +848,6 @@ def main():
     e2e_value = NSRC * g.m * world / e2e_s / 1e9 if e2e_steps else None
 
     launches = sum(s["kernel_launches"] for s in stats) + args.steps  # + the L2 flush fill
-    tts = [s["elapsed_ms"] for s in stats]
     line = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -826,12 +855,12 @@ def main():
         "dtype": "u32", "data": "synthetic",
         "config": {"workload": f"sssp-rmat{SCALE}-ef{EF}-{NSRC}src", "n": g.n, "m": g.m,
                    "sources_per_rank": NSRC, "weights": "u32 uniform [1,255]",
-                   "engine": "sync (CUDA graph, device-side WHILE)", "sched": "all pending",
+                   "engine": "sync (CUDA graph, device-side WHILE); the 8 runs chained in one graph launch (maiter_run_batch mode 2)", "sched": "all pending",
                    "l2": f"{L2_FLUSH_BYTES >> 20} MiB write between steps (outside the events)",
                    "parallelism": f"independent sources x{world}"},
         "time_to_solution_ms": {"mean": float(np.mean(tts)), "max": float(np.max(tts))},
         "gteps_work": float(sum(s["edge_pushes"] for s in stats) / (total_ms * 1e-3) / 1e9),
-        "rounds_per_source": float(np.mean([s["rounds"] for s in stats])),
+        "rounds_per_source": float(np.mean(np.concatenate(qrounds))),
         "roofline": {"bound": "hbm", "kernel": "k_push<OpMinU32>", "achieved": achieved,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,

@@ -383,7 +383,10 @@ typedef struct maiter_batch_params {
                               exact termination sum |Delta| < eps_q - and one
                               independent branch of the graph, so queries run
                               side by side; 1 = sparse frontiers of (query,
-                              vertex) items as described above */
+                              vertex) items as described above; 2 = dense with
+                              the branches chained: the queries run one after
+                              another, in order, inside one graph launch (no
+                              host round trip between them) */
   int32_t reserved;        /* must be 0 */
 } maiter_batch_params;
 

@@ -36,6 +36,8 @@ SCHED_ALL, SCHED_THRESHOLD, SCHED_TOPFRAC, SCHED_LEARNED, SCHED_BUCKET = 0, 1, 2
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 8, 64, 641
 ENGINE_SYNC, ENGINE_ASYNC = 0, 1
 FLAG_PROFILE_KERNELS, FLAG_INJECT_STALL = 1, 2
+# maiter_batch_params.mode
+BATCH_DENSE, BATCH_SPARSE, BATCH_DENSE_CHAINED = 0, 1, 2
 # maiter_probe_kind
 PROBE_RED_F32, PROBE_RED_F64, PROBE_MIN_U32, PROBE_LOAD_32 = 0, 1, 2, 3
 

@@ -133,7 +133,8 @@ static Phase<Op> dense_phase(const maiter_batch* b, int q, const maiter_batch_pa
 
 template <class V, class D>
 static maiter_status dense_add_init(cudaGraph_t graph, const maiter_batch* b, int q, V vfill,
-                                    D dfill, D seedval, const DevCtl& init, cudaGraphNode_t* last) {
+                                    D dfill, D seedval, const DevCtl& init, cudaGraphNode_t* last,
+                                    const cudaGraphNode_t* after) {
   maiter_result* r = b->qres[q];
   const maiter_graph* g = b->graphs[b->hq[q].graph];
   V* v = static_cast<V*>(r->v);
@@ -148,7 +149,7 @@ static maiter_status dense_add_init(cudaGraph_t graph, const maiter_batch* b, in
   k1.blockDim = dim3(256);
   k1.kernelParams = a1;
   cudaGraphNode_t n1, n2;
-  MAITER_CUDA(cudaGraphAddKernelNode(&n1, graph, nullptr, 0, &k1));
+  MAITER_CUDA(cudaGraphAddKernelNode(&n1, graph, after, after ? 1 : 0, &k1));
   const int* seeds = b->d_qseeds + b->seed_off[q];
   int ns = b->seed_cnt[q];
   D sv = seedval;
@@ -177,21 +178,26 @@ static maiter_status dense_build(maiter_batch* b, const maiter_batch_params* p,
   if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
   if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
   MAITER_CUDA(cudaGraphCreate(&b->graph, 0));
+  // mode 2 chains the branches: query q starts when query q - 1 has stopped
+  cudaGraphNode_t prev = nullptr;
   for (int q = 0; q < b->nq; ++q) {
     const BQuery& Q = b->hq[q];
     const DevCtl init = dense_ctl(Q, p, eps[q]);
+    const cudaGraphNode_t* after = (p->mode == 2 && prev) ? &prev : nullptr;
     cudaGraphNode_t last, wnode;
     cudaGraphConditionalHandle h;
     MAITER_CUDA(cudaGraphConditionalHandleCreate(&h, b->graph, 1, cudaGraphCondAssignDefault));
     maiter_status s;
     if (Q.op == 0) {
-      s = dense_add_init<double, double>(b->graph, b, q, 0.0, 0.0, Q.init, init, &last);
+      s = dense_add_init<double, double>(b->graph, b, q, 0.0, 0.0, Q.init, init, &last, after);
       if (s == MAITER_OK) s = dense_phase<OpSumF64>(b, q, p).add_to(b->graph, &last, 1, h, &wnode);
     } else {
-      s = dense_add_init<uint32_t, uint32_t>(b->graph, b, q, kInfU32, kInfU32, 0u, init, &last);
+      s = dense_add_init<uint32_t, uint32_t>(b->graph, b, q, kInfU32, kInfU32, 0u, init, &last,
+                                             after);
       if (s == MAITER_OK) s = dense_phase<OpMinU32>(b, q, p).add_to(b->graph, &last, 1, h, &wnode);
     }
     if (s != MAITER_OK) return s;
+    prev = wnode;
   }
   MAITER_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
   return MAITER_OK;
@@ -280,7 +286,7 @@ static maiter_status batch_setup(maiter_batch* b, const maiter_graph* const* gra
   }
   b->n_sum = off[0];
   b->n_min = off[1];
-  if (b->mode == 0) return dense_setup(b, qs);
+  if (b->mode != 1) return dense_setup(b, qs);
   // large-vertex counts per graph at this cut-off
   std::vector<unsigned> nlarge(ng, 0);
   {
@@ -407,6 +413,7 @@ static maiter_status dense_run(maiter_batch* b, const maiter_batch_params* p,
   }
   mix(static_cast<uint64_t>(p->max_rounds));
   mix(static_cast<uint64_t>(p->push_blocks_per_sm));
+  mix(static_cast<uint64_t>(p->mode));
   const bool profile = (p->flags & MAITER_FLAG_PROFILE_KERNELS) != 0;
   if (!profile && (!b->exec || b->exec_grid != static_cast<int>(sig & 0x7fffffff))) {
     maiter_status s = dense_build(b, p, eps);
@@ -596,7 +603,8 @@ maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_gr
   MAITER_REQUIRE(p->cut_large >= 0 && p->chunk >= 0 && (p->chunk == 0 || p->chunk >= 32),
                  "cut_large >= 0 and chunk = 0 or >= 32");
   MAITER_REQUIRE((p->flags & ~MAITER_FLAG_PROFILE_KERNELS) == 0, "unknown flags 0x%x", p->flags);
-  MAITER_REQUIRE((p->mode == 0 || p->mode == 1) && p->reserved == 0, "mode must be 0 or 1");
+  MAITER_REQUIRE((p->mode == 0 || p->mode == 1 || p->mode == 2) && p->reserved == 0,
+                 "mode must be 0, 1 or 2");
   for (int q = 0; q < num_queries; ++q) {
     const maiter_query& Q = queries[q];
     MAITER_REQUIRE(Q.graph >= 0 && Q.graph < num_graphs, "query %d: graph %d out of range", q, Q.graph);
@@ -626,7 +634,7 @@ maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_gr
     for (int q = 0; q < num_queries && same; ++q) {
       const maiter_query& Q = queries[q];
       same = b->hq[q].graph == Q.graph && b->hq[q].op == (Q.op == MAITER_OP_MIN_U32 ? 1 : 0);
-      if (same && b->mode == 0) same = b->seed_cnt[q] == Q.num_seeds;
+      if (same && b->mode != 1) same = b->seed_cnt[q] == Q.num_seeds;
     }
   }
   if (!same) {
@@ -642,7 +650,7 @@ maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_gr
       if (fresh) maiter_batch_destroy(b);
       return s;
     }
-  } else if (b->mode == 0) {
+  } else if (b->mode != 1) {
     // dense, same shape: refresh damping / seed values and the seed ids
     std::vector<int> flat;
     for (int q = 0; q < num_queries; ++q) {
@@ -673,7 +681,7 @@ maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_gr
     MAITER_CUDA(cudaMemcpy(b->d_queries, b->hq.data(), sizeof(BQuery) * num_queries,
                            cudaMemcpyHostToDevice));
   }
-  maiter_status s = b->mode == 0 ? dense_run(b, p, queries) : batch_run(b, p);
+  maiter_status s = b->mode != 1 ? dense_run(b, p, queries) : batch_run(b, p);
   if (s == MAITER_OK || s == MAITER_ERR_NOT_CONVERGED) {
     *out = b;
   } else if (fresh) {
@@ -691,7 +699,7 @@ maiter_status maiter_batch_get_state(const maiter_batch* b, int32_t query, void*
   DeviceGuard guard(b->device);
   const BQuery& q = b->hq[query];
   const size_t bytes = (q.op == 0 ? sizeof(double) : sizeof(uint32_t)) * count;
-  if (b->mode == 0)
+  if (b->mode != 1)
     MAITER_CUDA(cudaMemcpy(out, b->qres[query]->v, bytes, cudaMemcpyDefault));
   else if (q.op == 0)
     MAITER_CUDA(cudaMemcpy(out, b->v_sum + q.off, bytes, cudaMemcpyDefault));
@@ -711,7 +719,7 @@ maiter_status maiter_batch_query_rounds(const maiter_batch* b, int32_t* out, int
   set_error("%s", "");
   MAITER_REQUIRE(b && out && count == b->nq, "need num_queries entries");
   DeviceGuard guard(b->device);
-  if (b->mode == 0) {
+  if (b->mode != 1) {
     // dense: the rounds each query's own loop ran (its control block)
     for (int q = 0; q < count; ++q) out[q] = static_cast<int32_t>(b->h_ctls[q].rounds);
     return MAITER_OK;

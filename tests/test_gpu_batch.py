@@ -50,7 +50,7 @@ def check(mt, graphs, queries, b):
             assert oracle.relative_error(v, vstar) <= 1e-6, qi
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batch_mixed_queries_uneven_graphs(mt, mode):
     graphs, queries = make_batch([8, 10, 11, 12], n_ppr=6, n_sssp=3)
     G = [mt.Graph.from_csr(g) for g in graphs]
@@ -63,7 +63,7 @@ def test_batch_mixed_queries_uneven_graphs(mt, mode):
     assert (qr >= 0).all() and qr.max() <= st["rounds"] and (qr > 0).sum() > len(queries) // 2
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batch_reuse_gives_the_same_answer(mt, mode):
     graphs, queries = make_batch([9, 11], n_ppr=4, n_sssp=2, seed=3)
     G = [mt.Graph.from_csr(g) for g in graphs]
@@ -78,7 +78,7 @@ def test_batch_reuse_gives_the_same_answer(mt, mode):
             assert oracle.relative_error(b.state(i), first[i]) <= 1e-6
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batch_multi_source_sssp_and_hub_chunks(mt, mode):
     # a star hub (chunked path) plus an R-MAT graph; a two-seed SSSP query
     n = 6000
@@ -127,3 +127,20 @@ def test_batch_rejects_bad_queries(mt):
         mt.run_batch(G, [dict(op=1, graph=0, seeds=[0])])
     with pytest.raises(mt.MaiterError):
         mt.run_batch(G, [dict(op=0, graph=1, seeds=[0], eps=1e-6)])
+
+
+def test_chained_mode_runs_queries_one_after_another(mt):
+    # mode 2: the same answers as separate maiter_run calls, query by query,
+    # and a reused chained batch switches to mode 0 and back without mixing
+    g = graphgen.rmat(12, 16, weights=True)
+    G = mt.Graph.from_csr(g)
+    src = [int(s) for s in graphgen.sssp_sources(g, 5)]
+    queries = [dict(op=2, graph=0, seeds=[s]) for s in src]
+    b = mt.run_batch([G], queries, mode=2)
+    for i, s in enumerate(src):
+        np.testing.assert_array_equal(b.state(i), mt.run(G, mt.OP_MIN_U32, source=s).state())
+    b0 = mt.run_batch([G], queries, mode=0)
+    b2 = mt.run_batch([G], queries, mode=2, batch=b)
+    for i in range(len(src)):
+        np.testing.assert_array_equal(b2.state(i), b0.state(i))
+    assert b2.stats()["converged"] == 1
