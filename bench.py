@@ -833,7 +833,7 @@ def main():
     w_h = torch.from_numpy(g.w.view(np.int32)).pin_memory()
     h2d = rp_h.numel() * 8 + col_h.numel() * 4 + w_h.numel() * 4
     d2h = NSRC * g.n * 4
-    e2e_steps = 0 if args.no_e2e else 2 * max(1, min(args.steps, 3))
+    e2e_steps = 0 if args.no_e2e else 2 * max(1, min(args.steps, 5))
     slots = []
     for _ in range(2):
         s_k = torch.cuda.Stream(dev)
