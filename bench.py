@@ -71,6 +71,29 @@ def random_access(mt, kind, n, device, edge_ops, push_ms, what):
             "unit": "G edge pushes/s vs G ops/s"}
 
 
+def rank_sources(g, rank, world):
+    """This rank's NSRC sources: the first NSRC * world seeded sources of the
+    graph, cut into consecutive slices in rank order (independent problems,
+    so ranks share nothing but the timing)."""
+    all_src = graphgen.sssp_sources(g, NSRC * world)
+    return [int(s) for s in all_src[rank * NSRC:(rank + 1) * NSRC]]
+
+
+def max_over_ranks(x, dist, device):
+    """The slowest rank's value (the job ends when its last rank does)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(ms_per_step, m, world):
+    """Whole-job GTEPS: every rank's NSRC sources over the slowest rank's time."""
+    return NSRC * m * world / (ms_per_step * 1e-3) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -697,8 +720,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     g = graphgen.rmat(SCALE, EF, weights=True)
-    all_src = graphgen.sssp_sources(g, NSRC * world)
-    sources = [int(s) for s in all_src[rank * NSRC:(rank + 1) * NSRC]]
+    sources = rank_sources(g, rank, world)
     rp_d = torch.from_numpy(g.row_ptr).to(dev)
     col_d = torch.from_numpy(g.col).to(dev)
     w_d = torch.from_numpy(g.w.view(np.int32)).to(dev)
@@ -740,14 +762,9 @@ def main():
     if dist:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     ms_per_step = total_ms / args.steps
-    edges_per_step = NSRC * g.m * world
-    value = edges_per_step / (ms_per_step * 1e-3) / 1e9
+    value = weak_value(ms_per_step, g.m, world)
 
     # kernel-level roofline: the same 8 runs with per-kernel events
     prof = []
