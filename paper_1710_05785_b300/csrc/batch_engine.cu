@@ -469,7 +469,12 @@ static maiter_status dense_run(maiter_batch* b, const maiter_batch_params* p,
     s.activations += static_cast<int64_t>(h.activations);
     s.edge_pushes += static_cast<int64_t>(h.pushes);
     s.residual = std::max(s.residual, h.residual);
-    s.kernel_launches += 2 + (profile ? 3 : 2) * (static_cast<int64_t>(h.rounds) + 1);
+    // init + seed, then per round a scan and a push (and the profiling
+    // loop's hold); the graph's WHILE body runs whole passes of
+    // kRoundsPerPass rounds, the last of them ending in the stopping round
+    const int64_t ran = static_cast<int64_t>(h.rounds) + 1;
+    constexpr int64_t kPass = Phase<OpMinU32>::kRoundsPerPass;
+    s.kernel_launches += 2 + (profile ? 3 * ran : 2 * kPass * ((ran + kPass - 1) / kPass));
     if (h.status != 1) worst = h.status;
   }
   s.converged = worst == 1;
