@@ -54,7 +54,9 @@ struct OpSum {
                                              double damping) {
     const D d = atomic_take(delta + j);
     if (d == D(0)) return D(0);
-    v[j] += static_cast<double>(d);
+    // v is read and written once a round: streamed (evict-first), so it does
+    // not push the Delta lines the pushes' atomics need out of L2
+    __stcs(v + j, __ldcs(v + j) + static_cast<double>(d));
     if (deg == 0) return D(0);
     const double c = coef ? static_cast<double>(coef[j]) : damping / static_cast<double>(deg);
     return static_cast<D>(c * static_cast<double>(d));
@@ -71,7 +73,7 @@ struct OpSum {
   __device__ static __forceinline__ Msg finish(int j, int deg, D d, V* v, const C* coef,
                                                double damping, bool first_chunk) {
     if (d == D(0)) return D(0);
-    if (first_chunk) v[j] += static_cast<double>(d);
+    if (first_chunk) __stcs(v + j, __ldcs(v + j) + static_cast<double>(d));
     if (deg == 0) return D(0);
     const double c = coef ? static_cast<double>(coef[j]) : damping / static_cast<double>(deg);
     return static_cast<D>(c * static_cast<double>(d));
