@@ -194,9 +194,9 @@ def run_reference(args):
 
 
 PR_WORKLOADS = {
-    # configuration 1: FP64 PageRank to sum |Delta| < 1e-8
+    # FP64 PageRank on R-MAT scale 13, to sum |Delta| < 1e-8
     "pagerank-rmat13": dict(scale=13, ef=8, op="f64", eps=1e-8),
-    # configuration 3: FP32 deltas / FP64 state and residual, scale 24; eps = 4e-8
+    # mixed precision at R-MAT scale 24: FP32 deltas / FP64 state and residual; eps = 4e-8
     # bounds the per-entry relative error by 25 * eps = 1e-6 (v* >= 1 - d)
     "pagerank-mixed-rmat24": dict(scale=24, ef=16, op="mixed", eps=4e-8),
 }
@@ -320,7 +320,7 @@ BATCH_SCALES = [16, 17, 18, 19, 20, 21, 22, 22]   # the last scale-22 graph on a
 
 
 def batch_workload(scales=BATCH_SCALES, ppr_per_graph=64, sssp_per_graph=16, ef=16, d=0.8):
-    """Configuration 4: 512 personalised-PageRank queries (seed sets of 1-64
+    """The batch workload: 512 personalised-PageRank queries (seed sets of 1-64
     vertices, sizes log-uniform) and 128 SSSP sources over 8 R-MAT graphs."""
     graphs, queries = [], []
     for gi, s in enumerate(scales):
@@ -335,7 +335,7 @@ def batch_workload(scales=BATCH_SCALES, ppr_per_graph=64, sssp_per_graph=16, ef=
 
 
 def run_batch_bench(args):
-    """One step = every query of configuration 4 to its own termination, in
+    """One step = every query of the batch workload to its own termination, in
     one CUDA-graph launch; value = sum over queries of m / step time."""
     import torch
     import paper_1710_05785_b300 as mt
@@ -405,7 +405,7 @@ def run_batch_bench(args):
 
 
 def run_learned_bench(args):
-    """Configuration 5: scorers trained on traces of scale-20 runs (PageRank
+    """Learned scheduling: scorers trained on traces of scale-20 runs (PageRank
     with d = 0.8, and SSSP), applied to PageRank at scale 24 and SSSP at scale
     22 (edge factor 16); messages and time to the same tolerance against the
     plain form (all pending vertices) and top-q by |Delta|."""
@@ -717,14 +717,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--scale", type=int, default=0,
-                    help="PageRank workloads: R-MAT scale instead of the configuration's "
+                    help="PageRank workloads: R-MAT scale instead of the workload's "
                          "(a smaller case of the same kernels, for profiling)")
     ap.add_argument("--head-only", action="store_true",
                     help="PageRank workloads: time only the headline variant")
     ap.add_argument("--workload", default="sssp-rmat20",
                     choices=["sssp-rmat20", "batch", "learned"] + sorted(PR_WORKLOADS)
                     + ROW_WORKLOADS,
-                    help="sssp-rmat20 (default; configuration 2) or a PageRank configuration")
+                    help="sssp-rmat20 (default: SSSP on R-MAT scale 20, 8 sources) or another workload")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
