@@ -94,6 +94,28 @@ def weak_value(ms_per_step, m, world):
     return NSRC * m * world / (ms_per_step * 1e-3) / 1e9
 
 
+def run_in_threads(fns):
+    """Runs each callable on a thread of its own and waits for all of them;
+    an exception on any thread is raised here (a failed step must not leave
+    a throughput figure behind)."""
+    import threading
+    errors = []
+
+    def wrap(fn):
+        try:
+            fn()
+        except BaseException as e:  # noqa: BLE001 - re-raised on the caller's thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=wrap, args=(fn,)) for fn in fns]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if errors:
+        raise errors[0]
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -664,12 +686,7 @@ def run_row(args, name):
         e2e_step(slots[0])
     e2e_serial_s = (time.perf_counter() - t0) / per_slot
     t0 = time.perf_counter()
-    workers = [threading.Thread(target=lambda sl=sl: [e2e_step(sl) for _ in range(per_slot)])
-               for sl in slots]
-    for t in workers:
-        t.start()
-    for t in workers:
-        t.join()
+    run_in_threads([lambda sl=sl: [e2e_step(sl) for _ in range(per_slot)] for sl in slots])
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / (2 * per_slot)
     for sl in slots:
@@ -914,12 +931,7 @@ def main():
         e2e_step(slots[0])
     e2e_serial_s = (time.perf_counter() - t0) / max(e2e_steps // 2, 1)
     t0 = time.perf_counter()
-    workers = [threading.Thread(target=e2e_worker, args=(slots[k], e2e_steps // 2))
-               for k in range(2)]
-    for t in workers:
-        t.start()
-    for t in workers:
-        t.join()
+    run_in_threads([lambda k=k: e2e_worker(slots[k], e2e_steps // 2) for k in range(2)])
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / max(e2e_steps, 1)
     for sl in slots:

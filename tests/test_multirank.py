@@ -63,3 +63,15 @@ def test_two_gloo_ranks_shard_sources_and_take_the_slowest_time():
         np.testing.assert_allclose(value, bench.NSRC * g.m * world / 2.5e-3 / 1e9)
         # one rank alone runs the first NSRC of the same seeded list
         assert single == expect[:bench.NSRC]
+
+
+def test_thread_errors_reach_the_caller():
+    import bench
+    done = []
+    bench.run_in_threads([lambda: done.append(1), lambda: done.append(2)])
+    assert sorted(done) == [1, 2]
+
+    def boom():
+        raise RuntimeError("step failed")
+    with pytest.raises(RuntimeError, match="step failed"):
+        bench.run_in_threads([lambda: None, boom])
