@@ -281,7 +281,7 @@ void maiter_result_destroy(maiter_result* r);
  * NULL) receives the number of rounds.
  *
  * Working memory: the frontier lists and the control block live in one
- * fixed device array inside the library, 12 MiB + 256 B, which every GPU that
+ * fixed device array inside the library, 12 MiB + 512 B, which every GPU that
  * loads the library holds until the process exits.  Hence n is limited to
  * 1,048,576 (2^20) vertices; larger n returns MAITER_ERR_INVALID_ARG with a
  * message.  The first call on a device looks up that array's device address
