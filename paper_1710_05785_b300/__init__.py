@@ -414,7 +414,10 @@ def run_batch(graphs, queries, *, max_rounds: int = 1000000, stream=None, cut_la
               batch: Batch | None = None) -> Batch:
     """``maiter_run_batch``.  ``queries`` is a list of dicts with keys op
     (OP_SUM_F64 or OP_MIN_U32), graph (index), seeds (ids), and for PageRank
-    damping and eps."""
+    damping and eps.  ``mode``: BATCH_DENSE (each query a round-engine run,
+    all side by side in one graph launch), BATCH_SPARSE ((query, vertex)
+    frontiers) or BATCH_DENSE_CHAINED (the dense runs one after another, in
+    order, in one graph launch)."""
     G = (ctypes.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
     Q = (QuerySpec * len(queries))()
     keep = []
