@@ -133,8 +133,7 @@ static Phase<Op> dense_phase(const maiter_batch* b, int q, const maiter_batch_pa
 
 template <class V, class D>
 static maiter_status dense_add_init(cudaGraph_t graph, const maiter_batch* b, int q, V vfill,
-                                    D dfill, D seedval, const DevCtl& init, cudaGraphNode_t* last,
-                                    const cudaGraphNode_t* after) {
+                                    D dfill, D seedval, const DevCtl& init, cudaGraphNode_t* last) {
   maiter_result* r = b->qres[q];
   const maiter_graph* g = b->graphs[b->hq[q].graph];
   V* v = static_cast<V*>(r->v);
@@ -149,7 +148,7 @@ static maiter_status dense_add_init(cudaGraph_t graph, const maiter_batch* b, in
   k1.blockDim = dim3(256);
   k1.kernelParams = a1;
   cudaGraphNode_t n1, n2;
-  MAITER_CUDA(cudaGraphAddKernelNode(&n1, graph, after, after ? 1 : 0, &k1));
+  MAITER_CUDA(cudaGraphAddKernelNode(&n1, graph, nullptr, 0, &k1));
   const int* seeds = b->d_qseeds + b->seed_off[q];
   int ns = b->seed_cnt[q];
   D sv = seedval;
@@ -178,23 +177,27 @@ static maiter_status dense_build(maiter_batch* b, const maiter_batch_params* p,
   if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
   if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
   MAITER_CUDA(cudaGraphCreate(&b->graph, 0));
-  // mode 2 chains the branches: query q starts when query q - 1 has stopped
+  // mode 2 chains the branches: query q's rounds start when query q - 1 has
+  // stopped (its initialisation, which touches only its own buffers, may run
+  // earlier)
   cudaGraphNode_t prev = nullptr;
   for (int q = 0; q < b->nq; ++q) {
     const BQuery& Q = b->hq[q];
     const DevCtl init = dense_ctl(Q, p, eps[q]);
-    const cudaGraphNode_t* after = (p->mode == 2 && prev) ? &prev : nullptr;
-    cudaGraphNode_t last, wnode;
+    cudaGraphNode_t deps[2], wnode;
+    const size_t ndeps = (p->mode == 2 && prev) ? 2 : 1;
+    deps[1] = prev;
     cudaGraphConditionalHandle h;
     MAITER_CUDA(cudaGraphConditionalHandleCreate(&h, b->graph, 1, cudaGraphCondAssignDefault));
     maiter_status s;
     if (Q.op == 0) {
-      s = dense_add_init<double, double>(b->graph, b, q, 0.0, 0.0, Q.init, init, &last, after);
-      if (s == MAITER_OK) s = dense_phase<OpSumF64>(b, q, p).add_to(b->graph, &last, 1, h, &wnode);
+      s = dense_add_init<double, double>(b->graph, b, q, 0.0, 0.0, Q.init, init, &deps[0]);
+      if (s == MAITER_OK)
+        s = dense_phase<OpSumF64>(b, q, p).add_to(b->graph, deps, ndeps, h, &wnode);
     } else {
-      s = dense_add_init<uint32_t, uint32_t>(b->graph, b, q, kInfU32, kInfU32, 0u, init, &last,
-                                             after);
-      if (s == MAITER_OK) s = dense_phase<OpMinU32>(b, q, p).add_to(b->graph, &last, 1, h, &wnode);
+      s = dense_add_init<uint32_t, uint32_t>(b->graph, b, q, kInfU32, kInfU32, 0u, init, &deps[0]);
+      if (s == MAITER_OK)
+        s = dense_phase<OpMinU32>(b, q, p).add_to(b->graph, deps, ndeps, h, &wnode);
     }
     if (s != MAITER_OK) return s;
     prev = wnode;
