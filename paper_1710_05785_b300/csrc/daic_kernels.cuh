@@ -169,6 +169,9 @@ __global__ void __launch_bounds__(BLOCK, kScanMinBlocks) k_scan(KArgs<Op> a) {
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();
   DevCtl* ctl = a.ctl;
+  // A round that follows the stopping one in the same pass of the graph
+  // loop: nothing to select (the push after it returns as well).
+  if (ctl->status != 0) return;
   const unsigned ws = ctl->scan_set;
   const double tau = ctl->tau;
   const unsigned key_thr = a.topq ? a.topq->key_thr : 0u;
@@ -369,8 +372,11 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a,
   // needs in one round trip (both sets, then picks) and decides; all CTAs
   // reach the same decision, and CTA 0 records it.
   __shared__ int s_cnt[3];
-  __shared__ unsigned s_cont, s_round, s_overflow;
+  __shared__ unsigned s_cont, s_round, s_overflow, s_stopped;
   if (threadIdx.x == 0) {
+    // A round after the stopping one in the same pass: its scan returned at
+    // once (selected and took nothing), so nothing is decided or given back.
+    const bool stopped = ctl->status != 0;
     const unsigned ps = ctl->push_set;
     const uint4 c0 = *reinterpret_cast<const uint4*>(ctl->cnt[0]);
     const uint4 c1 = *reinterpret_cast<const uint4*>(ctl->cnt[1]);
@@ -404,7 +410,8 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a,
     else if (converged) status = 1;
     else if (static_cast<long long>(rounds) >= max_rounds) status = 2;
     const unsigned cont = status == 0;
-    if (blockIdx.x == 0) {
+    s_stopped = stopped;
+    if (blockIdx.x == 0 && !stopped) {
       const unsigned ns = ps ^ 1u;
       ctl->residual = resid;
       ctl->rounds_in[ns] = rounds + cont;
@@ -446,6 +453,7 @@ __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK) k_push(KArgs<Op> a,
     s_round = static_cast<unsigned>(rounds + 1);
   }
   __syncthreads();
+  if (s_stopped) return;
   const int cS = s_cnt[0], cM = s_cnt[1], cL = s_cnt[2];
   const unsigned round = s_round;
   if (!s_cont) {
