@@ -236,9 +236,9 @@ def test_invalid_arguments_are_rejected(mt):
         mt.run(G, mt.OP_SUM_F64, eps=-1.0)
 
 
-@pytest.mark.parametrize("cap", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("cap", [1, 2, 3, 4, 5, 6, 7])
 def test_round_cap_in_either_position_of_a_pass(mt, cap):
-    # the graph loop runs two rounds per pass; a cap that falls on either of
+    # the graph loop runs three rounds per pass; a cap that falls on any of
     # them stops after exactly `cap` pushes with a valid DAIC state that resumes
     g = graphgen.rmat(11, 8, weights=True)
     G = mt.Graph.from_csr(g)
