@@ -2,6 +2,8 @@
 // and the dense batch (batch_engine.cu): launch shapes, trace sinks, and the
 // Phase that adds / drives WHILE(cond) { k_push ; [select] ; k_scan }.
 #pragma once
+#include <algorithm>
+
 #include "internal.h"
 
 namespace maiter {
@@ -16,6 +18,7 @@ inline int grid_for(const void* fn, int block, int num_sms, int per_sm_cap) {
 }
 
 constexpr int kBlock = 256;
+constexpr long long kPushEdgesPerCta = 2048;
 // per-round hold of the host-driven (profiling) loop
 constexpr unsigned long long kHoldNs = 40000;
 
@@ -72,6 +75,13 @@ struct Phase {
                          tu.push_blocks_per_sm);
     scan_grid = grid_for(reinterpret_cast<const void*>(&k_scan<Op, kBlock>), kBlock, g->num_sms,
                          tu.scan_blocks_per_sm);
+    // Small graphs: one push CTA per kPushEdgesPerCta edges (at least one per
+    // SM) instead of a full grid of CTAs that would only take the decision
+    // and leave (PageRank on 65K edges: 1.49 -> 1.41 ms).
+    {
+      const long long want = std::max<long long>(g->num_sms, g->m / kPushEdgesPerCta);
+      if (want < push_grid) push_grid = static_cast<int>(want);
+    }
     const int tile = kBlock * kScanItems;
     const int need = static_cast<int>((g->n + tile - 1) / tile);
     if (need < scan_grid) scan_grid = need > 0 ? need : 1;
