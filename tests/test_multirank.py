@@ -75,3 +75,20 @@ def test_thread_errors_reach_the_caller():
         raise RuntimeError("step failed")
     with pytest.raises(RuntimeError, match="step failed"):
         bench.run_in_threads([lambda: None, boom])
+
+
+def test_clock_summary_reports_median_clock_and_throttle_reasons():
+    import bench
+    c = bench.ClockSampler(0)
+    # index, sm, max sm, power, active mask, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap
+    c.lines = ["0, 2032, 2032, 700.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 1980, 2032, 1090.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2010, 2032, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line"]
+    s = c.summary()
+    assert s["sm_mhz"] == 2010.0 and s["sm_max_mhz"] == 2032.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    c.lines = ["0, 1500, 2032, 500.0, 0x8, Active, Not Active, Active, Not Active"]
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c.lines = []
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
