@@ -1,6 +1,6 @@
 // Host-side pieces of the round engine shared by single runs (maiter_api.cu)
 // and the dense batch (batch_engine.cu): launch shapes, trace sinks, and the
-// Phase that adds / drives WHILE(cond) { k_push ; [select] ; k_scan }.
+// Phase that adds / drives WHILE(cond) { ([select] ; k_scan ; k_push) x kRoundsPerPass }.
 #pragma once
 #include <algorithm>
 
@@ -34,7 +34,7 @@ struct TraceSink {
   unsigned* la = nullptr;
 };
 
-// One phase of the round loop, WHILE(cond) { k_push ; k_scan }, for one
+// One phase of the round loop, WHILE(cond) { [select] ; k_scan ; k_push }, for one
 // operator: its kernel arguments and launch shapes.
 template <class Op>
 struct Phase {
