@@ -217,10 +217,16 @@ typedef struct maiter_stats {
 } maiter_stats;
 
 /* Fills *p with defaults: PageRank-style sum in FP64, d = 0.8, sched ALL,
- * eps = 1e-8, threshold = 0, top_frac = 0.01, source = -1, max_rounds 1e6. */
+ * eps = 1e-8, threshold = 0, top_frac = 0.01, source = -1, max_rounds 1e6.
+ * Paper: the PageRank IterateKernel of Section 5.2 (v = 0, Delta = 1 - d,
+ * + as accumulate, d / outdeg as send) and the 1 % queue of Section 5.1. */
 void maiter_params_default(maiter_run_params* p);
 
-/* Uploads and validates a CSR of out-edges (layout above) on `device`.
+/* Paper: the Partitioner of Section 5.2, which fills each state-table
+ * entry's data field (Section 5.1) with the vertex's adjacency list.  Here
+ * the caller's CSR is the single partition and row j's targets are entry j's
+ * data field.
+ * Uploads and validates a CSR of out-edges (layout above) on `device`.
  * w may be NULL (no weights; min runs then fail with INVALID_ARG).
  * On success *out owns device copies; free with maiter_graph_destroy.
  * Errors: INVALID_ARG (sizes, ordering, col range), OOM, CUDA. */
@@ -228,7 +234,9 @@ maiter_status maiter_graph_create(int64_t n, int64_t m, const int64_t* row_ptr,
                                   const int32_t* col, const uint32_t* w, int device,
                                   maiter_graph** out);
 
-/* Replaces the contents of g with another CSR of the same n and m (and
+/* Paper: the Partitioner of Section 5.2 again (the data field of every
+ * state-table entry, Section 5.1), for a new input of the same shape.
+ * Replaces the contents of g with another CSR of the same n and m (and
  * weights iff g has them), from host or device arrays, stream-ordered on
  * `stream` (NULL = default stream; pinned host arrays copy asynchronously),
  * then validates it like maiter_graph_create and returns after validation.
@@ -241,9 +249,14 @@ maiter_status maiter_graph_create(int64_t n, int64_t m, const int64_t* row_ptr,
 maiter_status maiter_graph_update(maiter_graph* g, const int64_t* row_ptr, const int32_t* col,
                                   const uint32_t* w, void* stream);
 
+/* Frees the device copy of the CSR (the state table's data fields,
+ * Section 5.1); NULL is ignored.  Every run on g must have returned. */
 void maiter_graph_destroy(maiter_graph* g);
 
-/* Runs a DAIC to termination (Eq. 5 updates, Section 3.5 schedules).
+/* Paper: the IterateKernel (init = v0 / delta0, accumulate = op, send = g)
+ * and TermChecker (eps) of Section 5.2, executed as the asynchronous DAIC of
+ * Section 3.2 (Eq. 5) under the scheduling of Section 3.5 / Section 5.1.
+ * Runs a DAIC to termination (Eq. 5 updates, Section 3.5 schedules).
  * If *out is NULL a new result is allocated; otherwise *out must be a result
  * earlier returned for this graph and is reused without allocation (its
  * previous state is overwritten).  On OK, NOT_CONVERGED and TIMEOUT, *out
@@ -255,53 +268,74 @@ void maiter_graph_destroy(maiter_graph* g);
 maiter_status maiter_run(const maiter_graph* g, const maiter_run_params* p,
                          maiter_result** out);
 
-/* Copies the n states v into `out` (host or device): double for sums, uint32
- * for min.  count must equal n. */
+/* Paper: the dump of the state table's v fields when the terminator stops
+ * the run (Section 5.1, Iteration Termination).
+ * Copies the n states v into `out` (host or device): double for sums, uint32
+ * for min, float for MIN_F32, int32 for max.  count must equal n.
+ * Errors: INVALID_ARG (NULL, count), CUDA. */
 maiter_status maiter_get_state(const maiter_result* r, void* out, int64_t count);
 
-/* Copies the n pending deltas Delta into `out`: double (SUM_F64), float
- * (SUM_MIXED) or uint32 (min).  count must equal n. */
+/* Paper: the state table's Delta fields (Section 5.1); with the states they
+ * form the complete DAIC state (v, Delta) that a checkpoint saves (Section
+ * 5.1, Fault Tolerance) and that resumes a run as v0 / delta0.
+ * Copies the n pending deltas Delta into `out`: double (SUM_F64), float
+ * (SUM_MIXED) or uint32 (min).  count must equal n.
+ * Errors: INVALID_ARG (NULL, count), CUDA. */
 maiter_status maiter_get_delta(const maiter_result* r, void* out, int64_t count);
 
+/* Paper: the progress estimator / terminator of Section 5.1 (TermChecker,
+ * Section 5.2): the last residual sum_j |Delta_j| the device measured, the
+ * rounds, updates and messages of the run, and its device time.
+ * Errors: INVALID_ARG (NULL). */
 maiter_status maiter_get_stats(const maiter_result* r, maiter_stats* out);
 
+/* Frees a result's device state table (v, Delta: Section 5.1) and workspace;
+ * NULL is ignored.  May come before or after maiter_graph_destroy. */
 void maiter_result_destroy(maiter_result* r);
 
 /* SSSP (min, g(x) = x + w, all pending vertices per round) that allocates no
  * memory.  The paper has no counterpart: this entry point exists for callers
  * that hold device buffers but may not call cudaMalloc - for example a plugin
- * whose device memory belongs to a host framework's caching allocator, code
- * that may run while that framework is capturing a stream (allocation is not
- * allowed then), or a caller with a fixed memory budget.
+ * whose device memory belongs to a host framework's caching allocator (an
+ * allocation behind that allocator's back can fail or fragment its pool), or
+ * a caller with a fixed memory budget.
  *
- * Inputs (device pointers only): row_ptr[n+1] as INT32 offsets (row_ptr[0] =
- * 0, non-decreasing, row_ptr[n] = m), col[m], w[m]; source in [0, n).
- * Outputs (device, caller-owned): v_out[n] receives the distances (UINT32_MAX
- * if unreachable), delta_out[n] the final deltas.  *rounds_out (host, may be
- * NULL) receives the number of rounds.
+ * Inputs (device pointers on `device` only): row_ptr[n+1] as INT32 offsets
+ * (row_ptr[0] = 0, non-decreasing, row_ptr[n] = m), col[m], w[m]; source in
+ * [0, n).  Outputs (device, caller-owned): v_out[n] receives the distances
+ * (UINT32_MAX if unreachable), delta_out[n] the final deltas.  *rounds_out
+ * (host, may be NULL) receives the number of rounds.  A buffer that is not
+ * device memory of `device` (host memory, or another GPU's) is rejected with
+ * INVALID_ARG before anything is launched.
  *
  * Working memory: the frontier lists and the control block live in one
- * fixed device array inside the library, 12 MiB + 512 B, which every GPU that
+ * fixed device array inside the library, 8 MiB + 512 B, which every GPU that
  * loads the library holds until the process exits.  Hence n is limited to
  * 1,048,576 (2^20) vertices; larger n returns MAITER_ERR_INVALID_ARG with a
  * message.  The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress, with the device current); make that first call
- * before any stream capture.  All calls share the one array and it keeps the
- * previous call's contents (each call resets what must start at zero), so
- * calls that overlap on the GPU - on two streams, or from two threads - race
- * and must be serialised by the caller.
+ * (cudaGetSymbolAddress, with the device current).  All calls share the one
+ * array and it keeps the previous call's contents (each call resets what must
+ * start at zero), so calls that overlap on the GPU - on two streams, or from
+ * two threads - race and must be serialised by the caller.
  *
  * The round loop runs from the host: per round two kernel launches on
  * `stream` and a small device-to-host read of the control block (into a host
- * stack variable), so the call returns
- * when the distances are final.  Errors: INVALID_ARG (sizes, non-device
- * pointers, bad CSR), NOT_CONVERGED (max_rounds, <= 0 means 1,000,000), CUDA. */
+ * stack variable) that the host waits for, so the call returns when the
+ * distances are final.  `stream` (NULL = the default stream) must therefore
+ * not be capturing; a capturing stream, or the default stream while another
+ * stream captures, is rejected with INVALID_ARG before anything is launched.
+ * Errors: INVALID_ARG (sizes, pointers, stream, bad CSR), NOT_CONVERGED
+ * (max_rounds, <= 0 means 1,000,000; the state is readable), CUDA. */
 maiter_status maiter_sssp_noalloc(int64_t n, int64_t m, const int32_t* row_ptr,
                                   const int32_t* col, const uint32_t* w, int64_t source,
                                   uint32_t* v_out, uint32_t* delta_out, int64_t max_rounds,
                                   int device, void* stream, int64_t* rounds_out);
 
 /* -------------------------------------------------------- learned scorer
+ * Paper: the priority field of the state table and the priority queue that
+ * extracts the highest-priority entries each round (Section 5.1), motivated
+ * by Section 3.5 (priority |v (+) Delta - v|, Theorem 4).  The network that
+ * predicts a priority is this library's own; the paper has none.
  * A 2-layer network 8 -> 64 (ReLU) -> 1 scores pending vertices for
  * MAITER_SCHED_LEARNED.  Weights are BF16 on the device (an FP32 master copy
  * is kept for training); inputs are rounded to BF16; every product is
@@ -318,7 +352,8 @@ maiter_status maiter_sssp_noalloc(int64_t n, int64_t m, const int32_t* row_ptr,
 #define MAITER_MLP_HIDDEN 64
 #define MAITER_MLP_PARAMS 641
 
-/* Creates a network on `device` with seeded He-style random weights. */
+/* Creates a network on `device` with seeded He-style random weights.
+ * Errors: INVALID_ARG, OOM, CUDA (all mlp calls). */
 maiter_status maiter_mlp_create(int device, uint64_t seed, maiter_mlp** out);
 maiter_status maiter_mlp_set_params(maiter_mlp* m, const float* params);   /* 641 FP32 */
 maiter_status maiter_mlp_get_params(const maiter_mlp* m, float* params);
@@ -333,9 +368,11 @@ maiter_status maiter_mlp_gradients(const maiter_mlp* m, const float* x, const fl
 maiter_status maiter_mlp_train(maiter_mlp* m, const float* x, const float* y, int64_t n,
                                int32_t epochs, int32_t batch, float lr, uint64_t seed,
                                float* final_loss);
-void maiter_mlp_destroy(maiter_mlp* m);
+void maiter_mlp_destroy(maiter_mlp* m);   /* NULL is ignored */
 
-/* Activation trace of a round-engine run (SUM_F64 or MIN_U32; any schedule
+/* Paper: a run as maiter_run (Section 5.2) whose priority fields (Section
+ * 5.1) are sampled after every round - the training data of the scorer.
+ * Activation trace of a round-engine run (SUM_F64 or MIN_U32; any schedule
  * but LEARNED): after every push of the first max_records rounds, records for
  * each of the num_sample vertices in `sample` its 8 features, Delta, v and the
  * round of its last update (1-based, 0 = never), into host arrays of
@@ -392,7 +429,9 @@ typedef struct maiter_batch_params {
 
 void maiter_batch_params_default(maiter_batch_params* p);
 
-/* Runs every query to termination.  All graphs must live on one device.  If
+/* Paper: many IterateKernel runs (Section 5.2) of the Rooted PageRank and
+ * SSSP rows of Table 1, each with its own state table (Section 5.1).
+ * Runs every query to termination.  All graphs must live on one device.  If
  * *out is non-NULL and was returned for the same graphs, query graphs/ops and
  * tuning, it is reused without allocation; otherwise it is (re)built.
  * Errors: INVALID_ARG, OOM (also when a frontier outgrows its bounded
@@ -401,30 +440,35 @@ maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_gr
                                const maiter_query* queries, int32_t num_queries,
                                const maiter_batch_params* p, maiter_batch** out);
 
-/* Copies query `query`'s states (double for PPR, uint32 for SSSP; count = n
- * of its graph) into `out` (host or device). */
+/* Paper: the dump of one query's state table v fields (Section 5.1).
+ * Copies query `query`'s states (double for PPR, uint32 for SSSP; count = n
+ * of its graph) into `out` (host or device).  Errors: INVALID_ARG, CUDA. */
 maiter_status maiter_batch_get_state(const maiter_batch* b, int32_t query, void* out,
                                      int64_t count);
 
-/* Aggregate statistics of the last run (rounds, updates, pushes, time). */
+/* Paper: the progress estimator of Section 5.1, summed over the queries.
+ * Aggregate statistics of the last run (rounds, updates, pushes, time). */
 maiter_status maiter_batch_get_stats(const maiter_batch* b, maiter_stats* out);
 
-/* Per query: the last round in which it still had frontier items. */
+/* Per query (Section 5.1's per-run termination): the last round in which it
+ * still had frontier items.  count must equal the number of queries. */
 maiter_status maiter_batch_query_rounds(const maiter_batch* b, int32_t* out, int32_t count);
 
-void maiter_batch_destroy(maiter_batch* b);
+void maiter_batch_destroy(maiter_batch* b);   /* NULL is ignored */
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none).  No paper
+ * counterpart (error reporting of this boundary). */
 const char* maiter_last_error(void);
 
-/* Library version string. */
+/* Library version string (no paper counterpart). */
 const char* maiter_version(void);
 
 /* Name (NUL-terminated, truncated to len) and SM count of a device; used to
- * key tuning caches.  Errors: INVALID_ARG, CUDA. */
+ * key tuning caches (no paper counterpart).  Errors: INVALID_ARG, CUDA. */
 maiter_status maiter_device_info(int device, char* name, int32_t len, int32_t* num_sms);
 
-/* Diagnostic: the rate at which `device` serves 4- or 8-byte operations at
+/* Diagnostic with no paper counterpart (a hardware measurement).
+ * The rate at which `device` serves 4- or 8-byte operations at
  * random addresses of a device array of 2^log2_words elements (an integer
  * hash of (thread, iteration) picks each address; a grid of one wave of
  * 256-thread CTAs, 256 operations per thread).  The push kernels issue such

@@ -3,14 +3,13 @@
 //
 // Who needs it: code that runs inside a host process whose device memory is
 // owned by someone else - a plugin handed pre-allocated buffers by a framework
-// with its own caching allocator, a callback that may run while that
-// allocator is in the middle of a stream capture (where cudaMalloc is not
-// allowed), or an embedded caller with a fixed memory budget.  Such callers
-// can pass their graph and output buffers, but they cannot let the library
-// call cudaMalloc for its working memory.
+// with its own caching allocator (a cudaMalloc behind that allocator's back
+// can fail or fragment its pool), or an embedded caller with a fixed memory
+// budget.  Such callers can pass their graph and output buffers, but they
+// cannot let the library call cudaMalloc for its working memory.
 //
 // How: the same round kernels as maiter_run (k_scan / k_push for the min
-// operator), with their working memory - the three frontier lists and the
+// operator), with their working memory - the two frontier lists and the
 // control block - carved out of one file-scope device array of fixed size.
 // Every GPU that loads this library holds that array until the process exits.
 // The round loop is driven from the host, one short device-to-host read of the
@@ -25,12 +24,12 @@ namespace {
 
 constexpr int64_t kNoallocMaxN = int64_t(1) << 20;   // vertices
 constexpr size_t kCtlBytes = 512;
-constexpr int kNoallocLists = 3;   // small and medium lists, plus one spare list slot
+constexpr int kNoallocLists = 2;   // small and medium lists (no chunked large-vertex list)
 constexpr size_t kScratchBytes = kCtlBytes + sizeof(int) * kNoallocLists * size_t(kNoallocMaxN);
 // slot layout: [DevCtl | ... | validation flag (last 4 bytes)]
 static_assert(sizeof(DevCtl) + sizeof(unsigned) <= kCtlBytes, "control block must fit its slot");
 
-// The working memory: control block, then the three frontier lists.
+// The working memory: control block, then the two frontier lists.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -54,6 +53,19 @@ maiter_status scratch_address(int device, unsigned char** out) {
   }
   *out = static_cast<unsigned char*>(g_scratch_ptr[device]);
   return MAITER_OK;
+}
+
+// The device a caller buffer lives on: -1 when it is not device (or managed)
+// memory.
+int pointer_device(const void* p) {
+  if (!p) return -1;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return -1;
+  return at.device;
 }
 
 // Checks the CSR before any push reads through it.  flag bit 0: row offsets
@@ -112,12 +124,32 @@ extern "C" maiter_status maiter_sssp_noalloc(int64_t n, int64_t m, const int32_t
   MAITER_REQUIRE(row_ptr && v_out && delta_out && (m == 0 || (col && w)),
                  "NULL buffer");
   MAITER_REQUIRE(device >= 0 && device < kMaxDevices, "device %d out of range", device);
-  MAITER_REQUIRE(is_device_pointer(row_ptr) && is_device_pointer(v_out) &&
-                     is_device_pointer(delta_out) &&
-                     (m == 0 || (is_device_pointer(col) && is_device_pointer(w))),
-                 "maiter_sssp_noalloc takes device pointers only");
+  {
+    // Every buffer must be device memory of `device`: a buffer of another GPU
+    // would be read (and atomically written) across the interconnect, or fault.
+    const void* bufs[5] = {row_ptr, v_out, delta_out, col, w};
+    const char* names[5] = {"row_ptr", "v_out", "delta_out", "col", "w"};
+    for (int i = 0; i < (m == 0 ? 3 : 5); ++i) {
+      const int d = pointer_device(bufs[i]);
+      MAITER_REQUIRE(d >= 0, "maiter_sssp_noalloc takes device pointers only (%s is not)",
+                     names[i]);
+      MAITER_REQUIRE(d == device, "maiter_sssp_noalloc: %s lives on device %d, not on device %d",
+                     names[i], d, device);
+    }
+  }
   DeviceGuard guard(device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    // The round loop waits on the host after every round, which a capturing
+    // stream cannot do (and the attempt would invalidate the caller's capture).
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) cudaGetLastError();
+    MAITER_REQUIRE(e == cudaSuccess && cs == cudaStreamCaptureStatusNone,
+                   "maiter_sssp_noalloc: the stream is capturing (or the default stream "
+                   "while another stream captures); the call synchronises with the host "
+                   "every round, so it needs a stream that is not capturing");
+  }
 
   unsigned char* scratch = nullptr;
   maiter_status s = scratch_address(device, &scratch);
