@@ -186,11 +186,40 @@ def cpu_baseline(g, sources, budget_s=25.0):
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle, one bounded sample of the workload per step."""
+    """Reference arm: the CPU oracle on the host cores, one bounded sample of
+    the workload per step.  PageRank workloads: one synchronous iteration of
+    the oracle over the full graph per step, the iterations to tolerance
+    projected from the measured residual decay; SSSP: Dijkstra from one source
+    per step."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
+    if args.workload in PR_WORKLOADS:
+        cfg = dict(PR_WORKLOADS[args.workload])
+        if args.scale:
+            cfg["scale"] = args.scale
+        g = graphgen.rmat(cfg["scale"], cfg["ef"])
+        per_iter, n_tol, done = oracle_pagerank_sample(g, D_PR, cfg["eps"], iters=args.steps,
+                                                       warmup=args.warmup)
+        ms = per_iter * n_tol * 1e3
+        value = g.m / (ms * 1e-3) / 1e9
+        sample = (f"{done} synchronous iterations of the oracle over the full graph, one per "
+                  f"step ({per_iter:.2f} s each, one core); {n_tol} iterations to tolerance "
+                  f"projected from the measured residual decay")
+        line = {
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": pagerank_config(args.workload, cfg, g, 1),
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
     g = graphgen.rmat(SCALE, EF, weights=True)
     sources = graphgen.sssp_sources(g, NSRC)
     for k in range(args.warmup):
@@ -205,14 +234,21 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"sssp-rmat{SCALE}-ef{EF}", "sources_per_step": 1,
-                   "n": g.n, "m": g.m},
+        "config": sssp_config(g, 1),
         "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                          "sample": "Dijkstra from one source of the full graph per step"},
         "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def sssp_config(g, world):
+    return {"workload": f"sssp-rmat{SCALE}-ef{EF}-{NSRC}src: SSSP in DAIC form, weights u32 "
+                        f"uniform [1, 255], {NSRC} sources one after another, exact",
+            "n": g.n, "m": g.m, "sources_per_rank": NSRC,
+            "l2": f"{L2_FLUSH_BYTES >> 20} MiB write between steps (outside the events)",
+            "parallelism": f"independent sources x{world}"}
 
 
 PR_WORKLOADS = {
@@ -222,120 +258,295 @@ PR_WORKLOADS = {
     # bounds the per-entry relative error by 25 * eps = 1e-6 (v* >= 1 - d)
     "pagerank-mixed-rmat24": dict(scale=24, ef=16, op="mixed", eps=4e-8),
 }
-# algorithmic bytes of the PageRank push kernel (RMW = read + write):
-#   FP64:  4 B target + 16 B Delta_k RMW = 20 B per edge;
-#          8 B offsets + 16 B Delta_j exchange + 16 B v_j RMW = 40 B per vertex
-#   FP32 deltas: 4 + 8 = 12 B per edge; 8 + 8 + 16 = 32 B per vertex
+# algorithmic bytes of a PageRank message and of a vertex update (an atomic
+# or any read-modify-write counts as a read plus a write):
+#   FP64 deltas:  4 B target + 16 B Delta_k RMW = 20 B per message;
+#                 8 B offsets + 16 B Delta_j take + 16 B v_j RMW = 40 B per update
+#   FP32 deltas:  4 + 8 = 12 B per message; 8 + 8 + 16 = 32 B per update
 PR_BYTES = {"f64": (20, 40), "f32": (12, 32)}
 D_PR = 0.8
 
 
-def run_pagerank(args, wl):
-    """PageRank workloads: one step = one run from v0 = 0, Delta1 = 1 - d to the
-    tolerance; value = m / time-to-tolerance (GTEPS per solution)."""
+def pagerank_alg_bytes(st, mixed):
+    """Algorithmic bytes of a run's messages and updates (per the table above);
+    a mixed run's FP64 warm-up phase is counted at the FP64 rates."""
+    if not mixed:
+        return PR_BYTES["f64"][0] * st["edge_pushes"] + PR_BYTES["f64"][1] * st["activations"]
+    w_e, w_v = st["warm_edge_pushes"], st["warm_activations"]
+    return (PR_BYTES["f64"][0] * w_e + PR_BYTES["f64"][1] * w_v
+            + PR_BYTES["f32"][0] * (st["edge_pushes"] - w_e)
+            + PR_BYTES["f32"][1] * (st["activations"] - w_v))
+
+
+def oracle_pagerank_sample(g, d, eps, budget_s=None, iters=None, warmup=0):
+    """The oracle's synchronous iteration (Eq. 1) from v = 0 on the full graph,
+    one iteration being v <- v + r with r = c + P^T v - v (the oracle's
+    residual routine, one core), timed per iteration.  Runs `iters`
+    iterations (after `warmup` untimed ones) or as many as fit `budget_s`.
+    The iterations to ||r||_1 < eps are counted if reached, else projected
+    from the measured geometric decay of ||r||_1 over the last iterations.
+    Returns (seconds per iteration, iterations to tolerance, iterations run)."""
+    import oracle
+    coef = oracle.pagerank_coef(g, d)
+    c = oracle.pagerank_c(g.n, d)
+    v = np.zeros(g.n)
+    norms, times = [], []
+    t_start = time.perf_counter()
+    k = 0
+    while True:
+        t0 = time.perf_counter()
+        r = oracle.linear_residual(g, coef, c, v)
+        v += r
+        dt = time.perf_counter() - t0
+        if k >= warmup:
+            times.append(dt)
+        norms.append(float(np.abs(r).sum()))
+        k += 1
+        if norms[-1] < eps:
+            break
+        if iters is not None and k >= warmup + iters:
+            break
+        if budget_s is not None and time.perf_counter() - t_start > budget_s and k >= 3:
+            break
+    per_iter = float(np.median(times)) if times else dt
+    # iteration i computes r from v^i, so r is below eps once i = len - 1 holds;
+    # the run needs that many iterations plus the one that meets the test
+    if norms[-1] < eps:
+        n_tol = len(norms)
+    else:
+        span = min(4, len(norms) - 1)
+        rho = (norms[-1] / norms[-1 - span]) ** (1.0 / span)
+        n_tol = len(norms) + int(np.ceil(np.log(eps / norms[-1]) / np.log(rho)))
+    return per_iter, n_tol, len(times)
+
+
+def pagerank_cpu_baseline(g, d, eps, budget_s=15.0):
+    per_iter, n_tol, done = oracle_pagerank_sample(g, d, eps, budget_s=budget_s)
+    return {"value": g.m / (per_iter * n_tol) / 1e9, "unit": "GTEPS", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{done} synchronous iterations of the oracle (Eq. 1) over the full graph, "
+                      f"{per_iter:.2f} s each on one core; {n_tol} iterations to "
+                      f"sum |r| < {eps:g} projected from the measured decay of the residual"}
+
+
+def pagerank_config(wl, cfg, g, world):
+    """The workload as both arms of the bench name it."""
+    return {"workload": f"{wl}: PageRank in DAIC form, d = 0.8, v0 = 0, Delta1 = 0.2, R-MAT "
+                        f"scale {cfg['scale']} edge factor {cfg['ef']}, to sum |Delta| < "
+                        f"{cfg['eps']:g}",
+            "n": g.n, "m": g.m, "eps": cfg["eps"],
+            "l2": f"inputs larger than L2 (CSR {(4 * g.m + 4 * g.n) / 1e9:.2f} GB); the GPU arm "
+                  f"also writes {L2_FLUSH_BYTES >> 20} MiB before every run",
+            "parallelism": f"independent replicas x{world}"}
+
+
+def run_pagerank(args, wl, dist=None, nested=None):
+    """PageRank workloads: one step = one run from v0 = 0, Delta1 = 1 - d to
+    sum |Delta| < eps; value = m / time-to-tolerance (GTEPS per solution).
+    The headline engine is the binned one (mixed precision at scale 24);
+    beside it the plain form (FP64 round engine), the round engine in mixed
+    precision and top-q scheduling."""
     import torch
     import paper_1710_05785_b300 as mt
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev).cuda_stream
+    stream = torch.cuda.current_stream(dev)
     cfg = dict(PR_WORKLOADS[wl])
     if args.scale:
         cfg["scale"] = args.scale   # a smaller case of the same kernels (profiling)
+    mixed = cfg["op"] == "mixed"
     g = graphgen.rmat(cfg["scale"], cfg["ef"])
     G = mt.Graph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev), device=local)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     eps = cfg["eps"]
+    op_head = mt.OP_SUM_MIXED if mixed else mt.OP_SUM_F64
     variants = {
+        "binned_mixed" if mixed else "binned_f64": dict(op=op_head, engine=mt.ENGINE_BINNED),
+        "binned_f64" if mixed else "binned_mixed": dict(
+            op=mt.OP_SUM_F64 if mixed else mt.OP_SUM_MIXED, engine=mt.ENGINE_BINNED),
         "plain_f64_sync": dict(op=mt.OP_SUM_F64),
         "mixed_sync": dict(op=mt.OP_SUM_MIXED),
-        "f64_async": dict(op=mt.OP_SUM_F64, engine=mt.ENGINE_ASYNC),
         "f64_topq10_sync": dict(op=mt.OP_SUM_F64, sched=mt.SCHED_TOPFRAC, top_frac=0.1),
     }
-    if cfg["scale"] >= 20:
-        # the asynchronous engine needs minutes per run at this size (its
-        # queue latency per update, see the scale-13 line); left out here
-        del variants["f64_async"]
-    head = "plain_f64_sync" if cfg["op"] == "f64" else "mixed_sync"
+    if cfg["scale"] < 20:
+        variants["f64_async"] = dict(op=mt.OP_SUM_F64, engine=mt.ENGINE_ASYNC)
+    head = "binned_mixed" if mixed else "binned_f64"
     if args.head_only:
         variants = {head: variants[head]}
-    results = {}
     res = {}
 
-    def one(name, kw):
-        flush.fill_(1)
-        r = mt.run(G, eps=eps, damping=D_PR, stream=stream, result=res.get(name), **kw)
+    def one(name, kw, record=None):
+        r = mt.run(G, eps=eps, damping=D_PR, stream=stream.cuda_stream, result=res.get(name),
+                   **kw)
         res[name] = r
         return r.stats()
 
-    for name, kw in variants.items():
-        reps = args.steps if name == head else max(1, min(args.steps, 2))
-        for _ in range(max(args.warmup, 1) if name == head else 1):
-            one(name, kw)
+    # the headline: W warm-up runs, then K timed runs (device events on the
+    # launching stream, max over ranks), an L2 flush before each
+    for _ in range(max(args.warmup, 1)):
+        flush.fill_(1)
+        one(head, variants[head])
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stats = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(k)
+            ev[k][0].record(stream)
+            stats.append(one(head, variants[head]))
+            ev[k][1].record(stream)
         torch.cuda.synchronize()
-        st = [one(name, kw) for _ in range(reps)]
-        t = min(s["elapsed_ms"] for s in st) if name != head else float(np.mean([s["elapsed_ms"] for s in st]))
-        results[name] = dict(time_to_tolerance_ms=t, rounds=st[-1]["rounds"],
-                             edge_pushes=st[-1]["edge_pushes"], residual=st[-1]["residual"],
-                             kernel_launches=st[-1]["kernel_launches"], stats=st[-1])
-    plain_t = results.get("plain_f64_sync", {}).get("time_to_tolerance_ms")
-    hs = results[head]
-    ms = hs["time_to_tolerance_ms"]
-    prof = mt.run(G, eps=eps, damping=D_PR, stream=stream, flags=mt.FLAG_PROFILE_KERNELS,
-                  **variants[head]).stats()
-    if cfg["op"] == "f64":
-        alg = PR_BYTES["f64"][0] * prof["edge_pushes"] + PR_BYTES["f64"][1] * prof["activations"]
-    else:
-        w_e, w_v = prof["warm_edge_pushes"], prof["warm_activations"]
-        alg = (PR_BYTES["f64"][0] * w_e + PR_BYTES["f64"][1] * w_v
-               + PR_BYTES["f32"][0] * (prof["edge_pushes"] - w_e)
-               + PR_BYTES["f32"][1] * (prof["activations"] - w_v))
+    if dist:
+        dist.barrier()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, dev)
+    ms = total_ms / args.steps
+    hs = stats[-1]
+    if not all(s["converged"] == 1 and s["residual"] < eps for s in stats):
+        raise RuntimeError("a timed PageRank run did not reach its tolerance")
+    # the state of the last timed run against the residual bound (numpy)
+    v_head = res[head].state()
+    bound = linear_residual_bound(g, v_head, np.full(g.n, 1 - D_PR), D_PR)
+    if bound > 1e-6:
+        raise RuntimeError(f"PageRank result misses the 1e-6 bound: {bound:.3g}")
+    results = {head: dict(time_to_tolerance_ms=ms, rounds=hs["rounds"],
+                          edge_pushes=hs["edge_pushes"], residual=hs["residual"],
+                          kernel_launches=hs["kernel_launches"],
+                          error_bound=bound)}
+    for name, kw in variants.items():
+        if name == head:
+            continue
+        reps = 2
+        one(name, kw)
+        best = None
+        for _ in range(reps):
+            flush.fill_(1)
+            st = one(name, kw)
+            best = st if best is None or st["elapsed_ms"] < best["elapsed_ms"] else best
+        results[name] = dict(time_to_tolerance_ms=best["elapsed_ms"], rounds=best["rounds"],
+                             edge_pushes=best["edge_pushes"], residual=best["residual"],
+                             kernel_launches=best["kernel_launches"])
+        res[name].close()
+        del res[name]
+    plain_t = results["plain_f64_sync"]["time_to_tolerance_ms"] if "plain_f64_sync" in results else None
+    # kernel-level roofline: the headline run again with per-kernel events
+    prof = mt.run(G, eps=eps, damping=D_PR, stream=stream.cuda_stream,
+                  flags=mt.FLAG_PROFILE_KERNELS, **variants[head]).stats()
+    alg = pagerank_alg_bytes(prof, mixed)
     peaks, peak_kind = measured_peaks()
+    rounds_p = max(prof["push_launches"], 1)
     achieved = alg / (prof["push_ms"] * 1e-3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get(f"k_bin_pagerank_mixed_rmat{cfg['scale']}")
+    except (OSError, ValueError):
+        pass
+    slot_bytes = 12 if mixed else 20
+    roofline = {"bound": "hbm", "kernel": "k_bin_scatter + k_bin_gather (one round)",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_kind": f"{peak_kind} copy bandwidth",
+                "rounds": prof["push_launches"],
+                "round_ms": prof["push_ms"] / rounds_p,
+                "scatter_ms_per_round": prof["bin_scatter_ms"] / rounds_p,
+                "gather_ms_per_round": prof["bin_gather_ms"] / rounds_p,
+                "alg_bytes_per_round": alg / rounds_p,
+                "slots": prof["slots"],
+                "moved_bytes_per_round_fp32": slot_bytes * prof["slots"] + 36 * g.n,
+                "note": "achieved = algorithmic bytes of the messages and updates (12 B per "
+                        "FP32 message, 32 B per update; FP64 warm-up rounds at 20 / 40 B) / "
+                        "device time of the round's two kernels"}
+    e2e = None if args.no_e2e else pagerank_e2e(mt, g, G, eps, variants[head], dev, local, world,
+                                                 args)
     line = {
-        "metric": METRIC, "value": g.m / (ms * 1e-3) / 1e9, "unit": "GTEPS",
+        "metric": METRIC, "value": world * g.m / (ms * 1e-3) / 1e9, "unit": "GTEPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if cfg["op"] == "f64" else "f32/f64", "data": "synthetic",
-        "config": {"workload": f"{wl}: PageRank d=0.8, R-MAT scale {cfg['scale']} ef {cfg['ef']}",
-                   "n": g.n, "m": g.m, "eps": eps, "headline": head,
-                   "l2": f"{L2_FLUSH_BYTES >> 20} MiB write before every run"},
+        "dtype": "f32/f64" if mixed else "f64", "data": "synthetic",
+        "config": pagerank_config(wl, cfg, g, world),
+        "headline": head,
+        "engine": "binned (messages summed per receiver bin in shared memory; CUDA graph "
+                  "with a device-side WHILE)",
+        "precision": ("FP32 deltas and messages after an FP64 warm-up; FP64 state, sums and "
+                      "residual") if mixed else "FP64",
         "time_to_tolerance_ms": ms,
         "vs_plain_form": plain_t / ms if plain_t else None,
-        "variants": {k: {kk: vv for kk, vv in v.items() if kk != "stats"} for k, v in results.items()},
+        "error_bound": bound,
+        "variants": results,
         "gteps_work": hs["edge_pushes"] / (ms * 1e-3) / 1e9,
-        "roofline": {"bound": "hbm", "kernel": "k_push<OpSum>", "achieved": achieved,
-                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                     "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
-                     "push_launches": prof["push_launches"],
-                     "push_ms_per_launch": prof["push_ms"] / max(prof["push_launches"], 1),
-                     "scan_ms_per_launch": prof["scan_ms"] / max(prof["scan_launches"], 1),
-                     "alg_bytes_per_launch": alg / max(prof["push_launches"], 1),
-                     "random_access": random_access(
-                         mt, mt.PROBE_RED_F64 if cfg["op"] == "f64" else mt.PROBE_RED_F32, g.n,
-                         local, prof["edge_pushes"], prof["push_ms"],
-                         "f64 atomicAdd" if cfg["op"] == "f64" else "f32 atomicAdd")},
-        "gpu_launches": int(sum(v["kernel_launches"] for v in results.values())),
+        "roofline": roofline,
+        "e2e": e2e,
+        # every timed run's kernels, + one L2 flush fill per step
+        "gpu_launches": int(sum(x["kernel_launches"] for x in stats)) + args.steps,
+        "clocks": clk.summary(),
     }
-    if rank == 0 and not args.no_cpu_baseline:
-        import oracle
-        coef = oracle.pagerank_coef(g, D_PR)
-        c = oracle.pagerank_c(g.n, D_PR)
-        t0 = time.perf_counter()
-        it = 0
-        while time.perf_counter() - t0 < 15.0 and it < 200:
-            oracle.linear_power(g, coef, c, tol=0.0, max_iter=1)
-            it += 1
-        per_iter = (time.perf_counter() - t0) / it
-        rounds = results.get("plain_f64_sync", results[head])["rounds"]
-        line["cpu_baseline"] = {
-            "value": g.m / (per_iter * rounds) / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"{it} synchronous iterations of the oracle over the full graph "
-                      f"({per_iter * 1e3:.0f} ms each), projected to the {rounds} rounds the "
-                      f"plain GPU form needed"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = pagerank_cpu_baseline(g, D_PR, eps)
+    for r in res.values():
+        r.close()
+    G.close()
+    del G, flush
+    torch.cuda.empty_cache()
+    if nested is not None:
+        line.update(nested(dist))
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def pagerank_e2e(mt, g, G0, eps, kw, dev, local, world, args):
+    """End to end through the C ABI from pinned host buffers, per step: the CSR
+    uploaded into a graph's buffers (maiter_graph_update; the binned layout is
+    rebuilt from it), the run, and every state read back into pinned memory.
+    Two steps in flight, each on its own graph, result and stream driven by
+    its own host thread, with a lock that keeps the runs one after another."""
+    import threading
+    import torch
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    h2d = rp_h.numel() * 8 + col_h.numel() * 4
+    d2h = g.n * 8
+    slots = []
+    for _ in range(2):
+        s_k = torch.cuda.Stream(dev)
+        G_k = mt.Graph(rp_h, col_h, device=local)
+        r_k = mt.run(G_k, eps=eps, damping=D_PR, stream=s_k.cuda_stream, **kw)
+        slots.append({"G": G_k, "s": s_k, "r": r_k,
+                      "out": torch.empty(g.n, dtype=torch.float64).pin_memory()})
+    torch.cuda.synchronize()
+    lock = threading.Lock()
+
+    def e2e_step(sl):
+        sl["G"].update(rp_h, col_h, stream=sl["s"].cuda_stream)
+        with lock:
+            sl["r"] = mt.run(sl["G"], eps=eps, damping=D_PR, stream=sl["s"].cuda_stream,
+                             result=sl["r"], **kw)
+        sl["r"].state(sl["out"])
+
+    per = max(1, min(args.steps, 4))
+    t0 = time.perf_counter()
+    for _ in range(per):
+        e2e_step(slots[0])
+    serial_s = (time.perf_counter() - t0) / per
+    t0 = time.perf_counter()
+    run_in_threads([lambda sl=sl: [e2e_step(sl) for _ in range(per)] for sl in slots])
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / (2 * per)
+    bound = linear_residual_bound(g, slots[1]["out"].numpy(), np.full(g.n, 1 - D_PR), D_PR)
+    if bound > 1e-6:
+        raise RuntimeError(f"end-to-end PageRank result misses the 1e-6 bound: {bound:.3g}")
+    for sl in slots:
+        sl["r"].close()
+        sl["G"].close()
+    return {"value": world * g.m / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps_in_flight": 2,
+            "one_step_at_a_time": world * g.m / serial_s / 1e9,
+            "ms_per_step": e2e_s * 1e3}
 
 
 BATCH_SCALES = [16, 17, 18, 19, 20, 21, 22, 22]   # the last scale-22 graph on a second seed
@@ -381,13 +592,18 @@ def run_batch_bench(args):
             b = mt.run_batch(G, queries, batch=b, stream=stream, **cfg)
         reps = args.steps if name == "tuned" else 1
         times = []
-        for _ in range(reps):
-            b = mt.run_batch(G, queries, batch=b, stream=stream, **cfg)
-            times.append(b.stats()["elapsed_ms"])
+        with ClockSampler(local) as clk:
+            for _ in range(reps):
+                b = mt.run_batch(G, queries, batch=b, stream=stream, **cfg)
+                times.append(b.stats()["elapsed_ms"])
         st = b.stats()
         qr = b.query_rounds()
         out[name] = dict(ms=float(np.mean(times)), stats=st, qrounds=qr, cfg=cfg)
         if name == "tuned":
+            clocks = clk.summary()
+            bad = check_batch_sample(graphs, queries, b)
+            if bad:
+                raise RuntimeError(f"batch queries miss their answers: {bad[:5]}")
             prof = mt.run_batch(G, queries, batch=b, stream=stream,
                                 flags=mt.FLAG_PROFILE_KERNELS, **cfg).stats()
         b.close()
@@ -420,20 +636,147 @@ def run_batch_bench(args):
                      "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
                      "push_launches": prof["push_launches"],
                      "push_ms_per_launch": prof["push_ms"] / max(prof["push_launches"], 1)},
-        "gpu_launches": int(st["kernel_launches"]) * (args.steps + 1),
+        "gpu_launches": int(st["kernel_launches"]) * args.steps,
+        "checked": "2 SSSP (exact) and 4 PPR (residual bound <= 1e-6) queries per graph, "
+                   "from the last timed batch",
+        "clocks": clocks,
     }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_cpu_baseline(graphs, queries, edges)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def check_batch_sample(graphs, queries, b, sssp_per_graph=2, ppr_per_graph=4):
+    """The first few SSSP and PPR queries of every graph checked without the
+    oracle (exact distances; residual bound <= 1e-6).  Returns the failures."""
+    bad = []
+    seen = {}
+    for i, q in enumerate(queries):
+        key = (q["graph"], q["op"])
+        cap = sssp_per_graph if q["op"] == 2 else ppr_per_graph
+        if seen.get(key, 0) >= cap:
+            continue
+        seen[key] = seen.get(key, 0) + 1
+        g = graphs[q["graph"]]
+        v = b.state(i)
+        if q["op"] == 2:
+            if not sssp_is_exact(g, int(q["seeds"][0]), v):
+                bad.append(i)
+        else:
+            c = np.zeros(g.n)
+            c[np.asarray(q["seeds"])] = (1 - q["damping"]) / len(q["seeds"])
+            if linear_residual_bound(g, v, c, q["damping"]) > 1e-6:
+                bad.append(i)
+    return bad
+
+
+def batch_cpu_baseline(graphs, queries, edges, budget_s=20.0):
+    """The oracle on one core over a bounded sample of the batch: Dijkstra for
+    SSSP queries and the synchronous iteration to tolerance for PPR queries,
+    taken round-robin from the smallest graph up until the budget is spent;
+    value = the sampled queries' edges (m of their graph each) / time."""
+    import oracle
+    order = sorted(range(len(queries)), key=lambda i: (graphs[queries[i]["graph"]].n, i))
+    t0 = time.perf_counter()
+    done, sampled_edges = 0, 0
+    for i in order:
+        q = queries[i]
+        g = graphs[q["graph"]]
+        if q["op"] == 2:
+            oracle.dijkstra(g, int(q["seeds"][0]))
+        else:
+            oracle.pagerank(g, q["damping"], seeds=q["seeds"], tol=q["eps"])
+        done += 1
+        sampled_edges += g.m
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": sampled_edges / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{done} of the {len(queries)} queries, smallest graphs first "
+                      f"({dt:.1f} s; PPR by synchronous iteration to the query's eps)"}
+
+
+def train_scorers(mt, device=0, q=0.1, epochs=20, samples=8192, records=96):
+    """The learned workload's scorers: one trained on the activation trace of a
+    PageRank run (d = 0.8, top-q scheduling) on an R-MAT scale-20 graph, one
+    on an SSSP run's trace on another scale-20 graph; both trained on the GPU
+    by the library's own kernels.  Returns (pagerank net, sssp net, info)."""
+    import torch
+    from paper_1710_05785_b300 import learned
+
+    dev = torch.device("cuda", device)
+
+    def upload(g):
+        w = torch.from_numpy(g.w.view(np.int32)).to(dev) if g.w is not None else None
+        return mt.Graph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev), w,
+                        device=device)
+
+    t0 = time.perf_counter()
+    gtp = graphgen.rmat(20, 16, seed=graphgen.DEFAULT_SEED_BASE + 5020)
+    Gtp = upload(gtp)
+    Xp, yp = learned.collect(mt, Gtp, gtp.row_ptr, mt.OP_SUM_F64, samples=samples,
+                             records=records, top_frac=q, eps=1e-8)
+    net_pr, loss_pr = learned.train(mt, Xp, yp, epochs=epochs, device=device)
+    Gtp.close()
+    gts = graphgen.rmat(20, 16, seed=graphgen.DEFAULT_SEED_BASE + 6020, weights=True)
+    Gts = upload(gts)
+    Xs, ys = learned.collect(mt, Gts, gts.row_ptr, mt.OP_MIN_U32, samples=samples,
+                             records=records, top_frac=q,
+                             source=int(graphgen.sssp_sources(gts, 1)[0]))
+    net_ss, loss_ss = learned.train(mt, Xs, ys, epochs=epochs, device=device)
+    Gts.close()
+    info = {"seconds": time.perf_counter() - t0, "pagerank_examples": int(len(yp)),
+            "pagerank_final_loss": loss_pr, "sssp_examples": int(len(ys)),
+            "sssp_final_loss": loss_ss}
+    return net_pr, net_ss, info
+
+
+# ------------------------------------------------ result checks (no oracle)
+# The bench checks what it timed with properties that pin the exact answer at
+# any size, in numpy: a failed check fails the run instead of leaving a figure.
+
+def sssp_is_exact(g, source, dist):
+    """Distances from `source` are exactly the shortest-path distances iff
+    dist[source] = 0, no edge can shorten a distance (dist[k] <= dist[j] + w),
+    and every other finite distance is attained by an edge (positive weights
+    make the tight edges lead back to the source)."""
+    INF = 0xFFFFFFFF
+    d = np.asarray(dist, dtype=np.uint64)
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    dj = d[src]
+    cand = np.where(dj == INF, np.uint64(INF), dj + g.w.astype(np.uint64))
+    k = g.col
+    if d[source] != 0 or np.any(d[k] > cand):
+        return False
+    best = np.full(g.n, np.uint64(INF) + np.uint64(1), dtype=np.uint64)
+    np.minimum.at(best, k, cand)
+    fin = (d != INF)
+    fin[source] = False
+    return bool(np.all(best[fin] == d[fin]))
+
+
+def linear_residual_bound(g, v, c, d):
+    """||v* - v||_1 <= ||c + d P^T v - v||_1 / (1 - d) for PageRank-type
+    fixed points (P the out-degree-normalised adjacency); returns that bound
+    divided by max v (the norm-wise relative error it admits)."""
+    deg = np.diff(g.row_ptr).astype(np.float64)
+    coef = np.divide(d, deg, out=np.zeros_like(deg), where=deg > 0)
+    send = np.repeat(coef * v, np.diff(g.row_ptr))
+    r = np.asarray(c, dtype=np.float64) - v
+    r += np.bincount(g.col, weights=send, minlength=g.n)
+    return float(np.abs(r).sum() / (1 - d) / max(float(np.max(v)), 1e-300))
 
 
 def run_learned_bench(args):
     """Learned scheduling: scorers trained on traces of scale-20 runs (PageRank
     with d = 0.8, and SSSP), applied to PageRank at scale 24 and SSSP at scale
     22 (edge factor 16); messages and time to the same tolerance against the
-    plain form (all pending vertices) and top-q by |Delta|."""
+    plain form (all pending vertices, FP64 round engine), top-q by |Delta| and
+    the binned engine.  Every timed result is checked (residual bound, exact
+    distances)."""
     import torch
     import paper_1710_05785_b300 as mt
-    from paper_1710_05785_b300 import learned
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -446,27 +789,17 @@ def run_learned_bench(args):
                         device=local)
 
     q = 0.1
-    t0 = time.perf_counter()
-    gtp = graphgen.rmat(20, 16, seed=graphgen.DEFAULT_SEED_BASE + 5020)
-    Gtp = upload(gtp)
-    Xp, yp = learned.collect(mt, Gtp, gtp.row_ptr, mt.OP_SUM_F64, samples=8192, records=96,
-                             top_frac=q, eps=1e-8)
-    net_pr, loss_pr = learned.train(mt, Xp, yp, epochs=20, device=local)
-    gts = graphgen.rmat(20, 16, seed=graphgen.DEFAULT_SEED_BASE + 6020, weights=True)
-    Gts = upload(gts)
-    Xs, ys = learned.collect(mt, Gts, gts.row_ptr, mt.OP_MIN_U32, samples=8192, records=96,
-                             top_frac=q, source=int(graphgen.sssp_sources(gts, 1)[0]))
-    net_ss, loss_ss = learned.train(mt, Xs, ys, epochs=20, device=local)
-    train_s = time.perf_counter() - t0
-    del Gtp, Gts
+    net_pr, net_ss, training = train_scorers(mt, device=local, q=q)
 
-    def measure(G, reps, **kw):
+    def measure(G, reps, check, **kw):
         r = mt.run(G, stream=stream, **kw)
         best = None
         for _ in range(reps):
             r = mt.run(G, stream=stream, result=r, **kw)
             st = r.stats()
             best = st if best is None or st["elapsed_ms"] < best["elapsed_ms"] else best
+        if not check(r):
+            raise RuntimeError(f"learned workload: a result misses its answer ({kw})")
         r.close()
         return {"time_to_tolerance_ms": best["elapsed_ms"], "edge_pushes": best["edge_pushes"],
                 "rounds": best["rounds"], "converged": best["converged"]}
@@ -474,28 +807,39 @@ def run_learned_bench(args):
     gp = graphgen.rmat(24, 16)
     Gp = upload(gp)
     eps = 4e-8
-    pr = {
-        "plain_f64": measure(Gp, 2, op=mt.OP_SUM_F64, eps=eps),
-        "topq_f64": measure(Gp, 1, op=mt.OP_SUM_F64, eps=eps, sched=mt.SCHED_TOPFRAC, top_frac=q),
-        "learned_f64": measure(Gp, 2, op=mt.OP_SUM_F64, eps=eps, sched=mt.SCHED_LEARNED,
-                               top_frac=q, scorer=net_pr),
-        "mixed": measure(Gp, 2, op=mt.OP_SUM_MIXED, eps=eps),
-        "learned_mixed": measure(Gp, 2, op=mt.OP_SUM_MIXED, eps=eps, sched=mt.SCHED_LEARNED,
-                                 top_frac=q, scorer=net_pr),
-    }
-    del Gp
-    gs = graphgen.rmat(22, 16, weights=True)
-    Gs = upload(gs)
-    srcs = [int(s) for s in graphgen.sssp_sources(gs, 4)]
-    ss = {}
-    for name, kw in [("plain", {}), ("topq", dict(sched=mt.SCHED_TOPFRAC, top_frac=0.05)),
-                     ("learned", dict(sched=mt.SCHED_LEARNED, top_frac=0.05, scorer=net_ss))]:
-        tot = {"time_to_tolerance_ms": 0.0, "edge_pushes": 0, "rounds": 0}
-        for s in srcs:
-            m = measure(Gs, 1, op=mt.OP_MIN_U32, source=s, **kw)
-            for k in tot:
-                tot[k] += m[k]
-        ss[name] = tot
+    c_pr = np.full(gp.n, 1 - D_PR)
+
+    def pr_ok(r):
+        return linear_residual_bound(gp, r.state(), c_pr, D_PR) <= 1e-6
+
+    with ClockSampler(local) as clk:
+        pr = {
+            "plain_f64": measure(Gp, 2, pr_ok, op=mt.OP_SUM_F64, eps=eps),
+            "topq_f64": measure(Gp, 1, pr_ok, op=mt.OP_SUM_F64, eps=eps, sched=mt.SCHED_TOPFRAC,
+                                top_frac=q),
+            "learned_f64": measure(Gp, 2, pr_ok, op=mt.OP_SUM_F64, eps=eps,
+                                   sched=mt.SCHED_LEARNED, top_frac=q, scorer=net_pr),
+            "mixed": measure(Gp, 2, pr_ok, op=mt.OP_SUM_MIXED, eps=eps),
+            "learned_mixed": measure(Gp, 2, pr_ok, op=mt.OP_SUM_MIXED, eps=eps,
+                                     sched=mt.SCHED_LEARNED, top_frac=q, scorer=net_pr),
+            "binned_mixed": measure(Gp, 2, pr_ok, op=mt.OP_SUM_MIXED, eps=eps,
+                                    engine=mt.ENGINE_BINNED),
+        }
+        Gp.close()
+        gs = graphgen.rmat(22, 16, weights=True)
+        Gs = upload(gs)
+        srcs = [int(s) for s in graphgen.sssp_sources(gs, 4)]
+        ss = {}
+        for name, kw in [("plain", {}), ("topq", dict(sched=mt.SCHED_TOPFRAC, top_frac=0.05)),
+                         ("learned", dict(sched=mt.SCHED_LEARNED, top_frac=0.05, scorer=net_ss))]:
+            tot = {"time_to_tolerance_ms": 0.0, "edge_pushes": 0, "rounds": 0}
+            for s in srcs:
+                m = measure(Gs, 1, lambda r, s=s: sssp_is_exact(gs, s, r.state()),
+                            op=mt.OP_MIN_U32, source=s, **kw)
+                for k in tot:
+                    tot[k] += m[k]
+            ss[name] = tot
+        Gs.close()
     head = min(("learned_f64", "learned_mixed"), key=lambda k: pr[k]["time_to_tolerance_ms"])
     ms = pr[head]["time_to_tolerance_ms"]
     line = {
@@ -505,13 +849,17 @@ def run_learned_bench(args):
         "dtype": "f64" if head == "learned_f64" else "f32/f64", "data": "synthetic",
         "config": {"workload": "learned scheduling: scorers trained on R-MAT scale-20 traces; "
                                "PageRank at scale 24 (eps 4e-8), SSSP at scale 22 (4 sources)",
-                   "top_frac": q, "headline": head},
+                   "top_frac": q, "headline": head,
+                   "l2": "inputs larger than L2 (scale-24 CSR 1.14 GB)"},
         "vs_plain_form": pr["plain_f64"]["time_to_tolerance_ms"] / ms,
         "pagerank_scale24": pr, "sssp_scale22_4_sources": ss,
-        "training": {"seconds": train_s, "pagerank_examples": int(len(yp)),
-                     "pagerank_final_loss": loss_pr, "sssp_examples": int(len(ys)),
-                     "sssp_final_loss": loss_ss},
+        "training": training,
+        "checked": "every timed result: PageRank by the residual bound (<= 1e-6 norm-wise), "
+                   "SSSP distances exact",
+        "clocks": clk.summary(),
     }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = pagerank_cpu_baseline(gp, D_PR, eps)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -733,41 +1081,59 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-sssp", action="store_true",
+                    help="default workload: leave out the nested SSSP record")
     ap.add_argument("--scale", type=int, default=0,
                     help="PageRank workloads: R-MAT scale instead of the workload's "
                          "(a smaller case of the same kernels, for profiling)")
     ap.add_argument("--head-only", action="store_true",
                     help="PageRank workloads: time only the headline variant")
-    ap.add_argument("--workload", default="sssp-rmat20",
+    ap.add_argument("--workload", default="pagerank-mixed-rmat24",
                     choices=["sssp-rmat20", "batch", "learned"] + sorted(PR_WORKLOADS)
                     + ROW_WORKLOADS,
-                    help="sssp-rmat20 (default: SSSP on R-MAT scale 20, 8 sources) or another workload")
+                    help="pagerank-mixed-rmat24 (default: PageRank, mixed precision, R-MAT "
+                         "scale 24, with the SSSP scale-20 record nested) or another workload")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.workload in PR_WORKLOADS:
-        run_pagerank(args, args.workload)
-        return
-    if args.workload == "batch":
-        run_batch_bench(args)
-        return
-    if args.workload == "learned":
-        run_learned_bench(args)
-        return
-    if args.workload in ROW_WORKLOADS:
-        run_row(args, args.workload)
-        return
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    try:
+        if args.workload in PR_WORKLOADS:
+            nested = None
+            if args.workload == "pagerank-mixed-rmat24" and not args.no_sssp and not args.scale:
+                def nested(d):
+                    return {"sssp_rmat20_8src": run_sssp(args, d, emit=False)}
+            run_pagerank(args, args.workload, dist, nested)
+        elif args.workload == "batch":
+            run_batch_bench(args)
+        elif args.workload == "learned":
+            run_learned_bench(args)
+        elif args.workload in ROW_WORKLOADS:
+            run_row(args, args.workload)
+        else:
+            run_sssp(args, dist, emit=True)
+    finally:
+        if dist:
+            dist.destroy_process_group()
 
+
+def run_sssp(args, dist, emit=True):
+    """SSSP on R-MAT scale 20 (edge factor 16, weights U[1, 255]), 8 sources one
+    after another, every run to the exact fixed point; one step = the 8
+    sources.  value = 8 m / step time (GTEPS).  Prints the line (emit) or
+    returns it as a record."""
     import torch
     import paper_1710_05785_b300 as mt
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
@@ -946,11 +1312,9 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"sssp-rmat{SCALE}-ef{EF}-{NSRC}src", "n": g.n, "m": g.m,
-                   "sources_per_rank": NSRC, "weights": "u32 uniform [1,255]",
-                   "engine": "sync (CUDA graph, device-side WHILE); the 8 runs chained in one graph launch (maiter_run_batch mode 2)", "sched": "all pending",
-                   "l2": f"{L2_FLUSH_BYTES >> 20} MiB write between steps (outside the events)",
-                   "parallelism": f"independent sources x{world}"},
+        "config": sssp_config(g, world),
+        "engine": "sync (CUDA graph, device-side WHILE); the 8 runs chained in one graph "
+                  "launch (maiter_run_batch mode 2)", "sched": "all pending",
         "time_to_solution_ms": {"mean": float(np.mean(tts)), "max": float(np.max(tts))},
         "gteps_work": float(sum(s["edge_pushes"] for s in stats) / (total_ms * 1e-3) / 1e9),
         "rounds_per_source": float(np.mean(np.concatenate(qrounds))),
@@ -975,12 +1339,17 @@ def main():
         "clocks": clk.summary(),
         "wall_s_timed": t_wall,
     }
+    # every source's distances of the last timed step, checked exactly
+    for i, s in enumerate(sources):
+        if not sssp_is_exact(g, s, bat[0].state(i)):
+            raise RuntimeError(f"SSSP distances from source {s} are not exact")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, sources)
-    if rank == 0:
+    bat[0].close()
+    G.close()
+    if emit and rank == 0:
         print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+    return line
 
 
 if __name__ == "__main__":

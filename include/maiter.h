@@ -122,7 +122,7 @@ typedef enum {
   MAITER_ENGINE_SYNC = 0,     /* round loop: frontier, then push; the loop and its
                                  termination test run on the device (CUDA graph
                                  with a conditional node), no host round trip */
-  MAITER_ENGINE_ASYNC = 1     /* persistent kernel over a device work queue: warps
+  MAITER_ENGINE_ASYNC = 1,    /* persistent kernel over a device work queue: warps
                                  take queued vertices, update them and re-queue
                                  receivers whose delta crosses the threshold (ALL:
                                  eps / (2n)), with no barrier between CTAs (Eq. 5,
@@ -130,6 +130,18 @@ typedef enum {
                                  reduction tests termination and re-seeds the queue
                                  (the periodic check of Section 5.1).  SUM_F64 and
                                  MIN_U32; schedules ALL and THRESHOLD. */
+  MAITER_ENGINE_BINNED = 2    /* rounds in which every vertex with a pending delta
+                                 sends (the synchronous DAIC of Section 3.2, schedule
+                                 ALL), for SUM_F64 / SUM_MIXED with g = SCALE_BY_SRC.
+                                 The messages of a round are written to bins of
+                                 16384 receivers (one slot per edge, in a layout the
+                                 library builds from the CSR on first use and after
+                                 maiter_graph_update) and each bin is summed in
+                                 shared memory in FP64, then folded: no atomic in
+                                 global memory per edge.  Needs n <= 2^28; memory
+                                 about 4 bytes per edge for the layout plus 8 per
+                                 edge for the messages of a result.  The loop and its
+                                 termination test run on the device as for SYNC. */
 } maiter_engine;
 
 /* Run flags (bit set). */
@@ -214,6 +226,12 @@ typedef struct maiter_stats {
   int64_t warm_rounds;
   int64_t warm_activations;
   int64_t warm_edge_pushes;
+  /* ENGINE_BINNED: padded edge slots of the layout (every round moves one
+     message per slot), and under MAITER_FLAG_PROFILE_KERNELS the summed
+     device time of its two round kernels (push_ms is their sum) */
+  int64_t slots;
+  double bin_scatter_ms;
+  double bin_gather_ms;
 } maiter_stats;
 
 /* Fills *p with defaults: PageRank-style sum in FP64, d = 0.8, sched ALL,

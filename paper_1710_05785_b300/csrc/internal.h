@@ -60,6 +60,10 @@ struct Tuning {
 
 }  // namespace maiter
 
+namespace maiter {
+struct BinLayout;   // binned engine: the edges by (sender cell, receiver bin)
+}
+
 struct maiter_graph {
   int device = 0;
   int64_t n = 0, m = 0;
@@ -73,6 +77,7 @@ struct maiter_graph {
   unsigned* flag = nullptr;    // validation flags (kept after the first update)
   bool invalid = false;        // the last update failed validation: no runs
   int num_sms = 0;
+  maiter::BinLayout* bins = nullptr;   // binned engine layout (built on first use)
 };
 
 struct maiter_result {
@@ -108,6 +113,11 @@ struct maiter_result {
   cudaGraph_t agraph = nullptr;
   cudaGraphExec_t aexec = nullptr;
   uint64_t aexec_key = 0;
+  // binned engine (allocated on its first use)
+  void* bin_msg_v = nullptr;           // n messages c_j Delta_j (8 bytes each)
+  void* bin_cmsg = nullptr;            // n coefficients c_j (8 bytes each)
+  void* bin_msg_e = nullptr;           // one message per padded edge slot (8 bytes each)
+  size_t bin_msg_e_cap = 0;
   maiter_stats stats{};
 };
 
@@ -121,4 +131,10 @@ int mlp_device(const maiter_mlp* m);
 maiter_status run_async(const maiter_graph* g, const maiter_run_params* p, maiter_result* r,
                         cudaStream_t st);
 void free_async(maiter_result* r);
+// Binned engine (binned_engine.cu): dense rounds of + with messages summed per
+// receiver bin in shared memory; v and Delta are initialised.
+maiter_status run_binned(const maiter_graph* g, const maiter_run_params* p, maiter_result* r,
+                         cudaStream_t st);
+void free_bins(maiter_graph* g);
+void invalidate_bins(maiter_graph* g);
 }  // namespace maiter

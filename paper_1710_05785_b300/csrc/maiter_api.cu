@@ -124,6 +124,7 @@ void maiter_graph_destroy(maiter_graph* g) {
   cudaFree(g->rp64);
   cudaFree(g->flag);
   cudaFree(g->indeg);
+  free_bins(g);
   delete g;
 }
 
@@ -228,6 +229,7 @@ maiter_status maiter_graph_update(maiter_graph* g, const int64_t* row_ptr, const
   cudaFree(g->indeg);
   g->indeg = nullptr;
   g->wf32 = 0;
+  invalidate_bins(g);
   if (h_flag & 1u) {
     set_error("row_ptr must start at 0, be non-decreasing and end at m = %lld", (long long)m);
     return MAITER_ERR_INVALID_ARG;
@@ -257,6 +259,9 @@ void maiter_result_destroy(maiter_result* r) {
   cudaFree(r->topq);
   cudaFree(r->keys);
   cudaFree(r->last_act);
+  cudaFree(r->bin_msg_v);
+  cudaFree(r->bin_cmsg);
+  cudaFree(r->bin_msg_e);
   free_async(r);
   if (r->h_ctl) cudaFreeHost(r->h_ctl);
   if (r->ev0) cudaEventDestroy(r->ev0);
@@ -687,7 +692,9 @@ static maiter_status run_op(const maiter_graph* g, const maiter_run_params* p, m
     r->stats.kernel_launches = init_launches;
     return MAITER_OK;
   }
-  s = (p->engine == MAITER_ENGINE_ASYNC) ? run_async(g, p, r, st) : run_sync(g, p, r, st, trace);
+  s = (p->engine == MAITER_ENGINE_ASYNC)    ? run_async(g, p, r, st)
+      : (p->engine == MAITER_ENGINE_BINNED) ? run_binned(g, p, r, st)
+                                            : run_sync(g, p, r, st, trace);
   r->stats.kernel_launches += init_launches;
   return s;
 }
@@ -733,8 +740,15 @@ static maiter_status run_impl(const maiter_graph* g, const maiter_run_params* p,
     }
     MAITER_REQUIRE(p->top_frac > 0.0 && p->top_frac <= 1.0, "top_frac must lie in (0, 1]");
   }
-  MAITER_REQUIRE(p->engine == MAITER_ENGINE_SYNC || p->engine == MAITER_ENGINE_ASYNC,
+  MAITER_REQUIRE(p->engine == MAITER_ENGINE_SYNC || p->engine == MAITER_ENGINE_ASYNC ||
+                     p->engine == MAITER_ENGINE_BINNED,
                  "unknown engine %d", p->engine);
+  if (p->engine == MAITER_ENGINE_BINNED &&
+      (!is_sum || p->g != MAITER_G_SCALE_BY_SRC || p->sched != MAITER_SCHED_ALL || trace ||
+       (p->flags & MAITER_FLAG_INJECT_STALL))) {
+    set_error("the binned engine runs sums with g = SCALE_BY_SRC and schedule ALL");
+    return MAITER_ERR_UNSUPPORTED;
+  }
   MAITER_REQUIRE(p->timeout_ms >= 0, "timeout_ms must be >= 0");
   MAITER_REQUIRE(p->cut_warp >= 0 && p->cut_cta >= 0 && p->push_blocks_per_sm >= 0 &&
                      p->reserved1 == 0,

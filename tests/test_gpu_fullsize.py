@@ -6,15 +6,13 @@ in FP64) satisfies (I - dP^T)(v* - v) = r, hence
     max_j |v*_j - v_j| <= ||v* - v||_1 <= ||r||_1 / (1 - d),
 and since v only grows towards v* (Section 3.5), max_j v_j <= max_j v*_j.
 
-The FP64 run is bounded directly this way.  For the mixed-precision run the
-L1 bound is loose (it sums FP32 rounding over every vertex), so its max error
-is bounded through the FP64 run:
-    max|v_mixed - v*| <= max|v_mixed - v_f64| + ||r_f64||_1 / (1 - d)."""
+The FP64 run is bounded directly this way.  For the mixed-precision runs
+and the binned engine's runs the L1 bound is loose (it sums FP32 rounding
+over every vertex), so their max error is bounded through the FP64 run:
+    max|v_other - v*| <= max|v_other - v_f64| + ||r_f64||_1 / (1 - d)."""
 import numpy as np
 import pytest
 
-import graphgen
-import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -32,19 +30,17 @@ def mt():
 
 
 @pytest.fixture(scope="module")
-def runs(mt):
-    g = graphgen.rmat(24, 16)
-    dev = torch.device("cuda", 0)
-    G = mt.Graph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev))
-    out = {}
-    for name in ["OP_SUM_F64", "OP_SUM_MIXED"]:
-        r = mt.run(G, getattr(mt, name), damping=D, eps=4e-8)
+def runs(mt, pagerank24):
+    G = pagerank24["G"]
+    out = {"OP_SUM_F64": pagerank24["v"], "bound_f64": pagerank24["bound"]}
+    for name, kw in [("OP_SUM_MIXED", dict(op=mt.OP_SUM_MIXED)),
+                     ("binned_f64", dict(op=mt.OP_SUM_F64, engine=mt.ENGINE_BINNED)),
+                     ("binned_mixed", dict(op=mt.OP_SUM_MIXED, engine=mt.ENGINE_BINNED))]:
+        op = kw.pop("op")
+        r = mt.run(G, op, damping=D, eps=4e-8, **kw)
         assert r.stats()["converged"] == 1
         out[name] = r.state()
         r.close()
-    coef = oracle.pagerank_coef(g, D)
-    c = oracle.pagerank_c(g.n, D)
-    out["bound_f64"] = np.abs(oracle.linear_residual(g, coef, c, out["OP_SUM_F64"])).sum() / (1 - D)
     return out
 
 
@@ -58,3 +54,10 @@ def test_pagerank_scale24_mixed_within_1e6(runs):
     vm, vf = runs["OP_SUM_MIXED"], runs["OP_SUM_F64"]
     err = np.abs(vm - vf).max() + runs["bound_f64"]
     assert err <= 1e-6 * vf.max(), (err, vf.max())
+
+
+@pytest.mark.parametrize("name", ["binned_f64", "binned_mixed"])
+def test_pagerank_scale24_binned_within_1e6(runs, name):
+    vb, vf = runs[name], runs["OP_SUM_F64"]
+    err = np.abs(vb - vf).max() + runs["bound_f64"]
+    assert err <= 1e-6 * vf.max(), (name, err, vf.max())
