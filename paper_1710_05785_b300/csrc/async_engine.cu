@@ -6,7 +6,7 @@
 
 namespace maiter {
 
-constexpr int kAsyncBlock = 256;
+constexpr int kAsyncBlock = 512;
 
 void free_async(maiter_result* r) {
   if (r->aexec) cudaGraphExecDestroy(r->aexec);
@@ -111,7 +111,9 @@ struct AsyncPlan {
 template <class Op>
 static maiter_status run_async_op(const maiter_graph* g, const maiter_run_params* p,
                                   maiter_result* r, cudaStream_t st) {
-  const void* coef = p->coef ? r->coef : nullptr;
+  // r->coef holds the caller's coefficients, or c_j = damping / outdeg(j)
+  // tabulated for this run (no FP64 divide per update)
+  const void* coef = (p->coef || Op::kIsSum) ? r->coef : nullptr;
   AsyncPlan<Op> plan;
   plan.setup(g, r, coef, p->damping);
   const bool profile = (p->flags & MAITER_FLAG_PROFILE_KERNELS) != 0;

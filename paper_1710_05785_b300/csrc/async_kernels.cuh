@@ -1,21 +1,27 @@
 // Persistent asynchronous DAIC (Section 3.2, Eq. 5; Section 5.1).
 //
-// One launch processes vertices from a device work queue until the queue is
-// quiescent.  No CTA ever waits for another at a barrier: warps claim batches
-// of queued vertices, update them, and re-enqueue receivers whose delta just
-// became worth an update, exactly as Maiter's update thread takes vertices
-// from its priority queue while the receive thread accumulates messages.
+// One launch processes vertices until the work is quiescent.  No CTA ever
+// waits for another at a barrier: each CTA keeps its own work list in shared
+// memory, updates the vertices on it, and puts the receivers whose delta just
+// became worth an update on its next list - Maiter's update thread taking
+// vertices from its queue while the receive thread accumulates messages, one
+// of them per SM.
 //
-// Queue: a ring of int32 vertex ids (empty slot = -1), monotonic 64-bit head
-// (next to claim) and tail (next to reserve), a per-vertex in-queue flag so a
-// vertex is queued at most once, and `pending` = vertices reserved in the
-// queue or being processed.  pending == 0 means quiescence: nothing queued and
-// nothing in flight, so no message can still create work.
+// Per edge the scatter is a fire-and-forget atomic (no returned value); the
+// receiver is re-activated from a read of its delta just before: for + when
+// that read was at or below the threshold tau and the read plus the message
+// is above it, for min when the message improves the read distance and the
+// receiver's state.  A per-vertex in-queue flag (exchanged only for those
+// candidates) keeps a vertex on at most one list.  A stale read can miss an
+// activation; the exact check between launches (k_async_seed) then finds the
+// vertex still pending and seeds it again, so nothing is lost.
 //
-// Termination of the run (the paper's periodic check, Section 5.1) is an
-// exact reduction between launches (k_async_seed): it measures sum |Delta|
-// (or the pending count for min) with no update in flight, decides, and seeds
-// the next launch with every vertex above the activation threshold.
+// A global ring of vertex ids (empty slot = -1; monotonic 64-bit head and
+// tail) carries the seeds of a launch, the overflow of full local lists and
+// the work busy CTAs hand to idle ones.  `busy` counts the CTAs that hold
+// work: a CTA raises it before it claims from the ring and lowers it only
+// when its lists are empty, after any hand-over, so "ring empty and no CTA
+// busy, ring still empty" proves quiescence.
 //
 // Every spin is bounded: a wait that sees no progress for timeout_ns on the
 // global timer records status 4 (timeout) or 5 (queue slot never freed) and
@@ -29,12 +35,11 @@
 
 namespace maiter {
 
-// The three hot counters sit on cache lines of their own: idle warps poll
-// them and every claim and enqueue hits them.
+// The hot counters sit on cache lines of their own.
 struct AsyncCtl {
-  alignas(128) unsigned long long head;   // next queue index to claim
-  alignas(128) unsigned long long tail;   // next queue index to reserve
-  alignas(128) long long pending;         // reserved + in-flight vertices
+  alignas(128) unsigned long long head;   // next ring index to claim
+  alignas(128) unsigned long long tail;   // next ring index to reserve
+  alignas(128) long long busy;            // CTAs holding work (+ an injected phantom)
   alignas(128) unsigned int ticket;       // last-block election in k_async_seed
   int status;                    // 0 running, 1 converged, 2 epoch cap, 4 timeout, 5 queue full
   double resid_acc;
@@ -48,7 +53,7 @@ struct AsyncCtl {
   double eps;
   long long max_epochs;
   unsigned long long timeout_ns; // longest wait without progress
-  int inject_stall;              // testing: one phantom pending item per launch
+  int inject_stall;              // testing: a phantom busy CTA per launch
   int pad;
 };
 
@@ -73,21 +78,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Warp-aggregated enqueue of the lanes with `want` (their flags already
-// acquired).  Reserves slots and pending counts first, then writes each id
-// into its slot once the slot is empty (bounded wait).
+// Warp-aggregated append of the lanes with `want` to the global ring:
+// reserves slots, then writes each id once its slot is empty (bounded wait).
 template <class Op>
-__device__ __forceinline__ void enqueue_warp(const AArgs<Op>& a, bool want, int k, int lane) {
+__device__ __forceinline__ void ring_put_warp(const AArgs<Op>& a, bool want, int k, int lane) {
   const unsigned mask = __ballot_sync(0xffffffffu, want);
   if (!mask) return;
-  const int cnt = __popc(mask);
+  const int leader = __ffs(mask) - 1;
   unsigned long long base = 0;
-  if (lane == 0) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(&a.ctl->pending),
-              static_cast<unsigned long long>(cnt));
-    base = atomicAdd(&a.ctl->tail, static_cast<unsigned long long>(cnt));
-  }
-  base = __shfl_sync(0xffffffffu, base, 0);
+  if (lane == leader)
+    base = atomicAdd(&a.ctl->tail, static_cast<unsigned long long>(__popc(mask)));
+  base = __shfl_sync(0xffffffffu, base, leader);
   if (want) {
     const unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
     volatile int* slot = a.queue + (idx % a.cap);
@@ -102,184 +103,286 @@ __device__ __forceinline__ void enqueue_warp(const AArgs<Op>& a, bool want, int 
       }
     }
     *slot = k;
+    __threadfence();   // the id is in the ring before this CTA can report itself idle
   }
 }
 
-// Claims up to kClaim queued indices for the calling warp (processed 32 at a
-// time): returns the first index and the count (0 when nothing is claimable
-// right now).  Large claims keep the rate of compare-and-swap on head low.
-constexpr int kClaim = 128;
-__device__ __forceinline__ int claim_warp(AsyncCtl* ctl, unsigned long long* first, int lane) {
-  int got = 0;
-  unsigned long long h = 0;
-  if (lane == 0) {
-    volatile AsyncCtl* vc = ctl;
-    for (int tries = 0; tries < 64; ++tries) {
-      h = vc->head;
-      const unsigned long long t = vc->tail;
-      if (h >= t) break;
-      const unsigned long long take =
-          (t - h) < static_cast<unsigned long long>(kClaim) ? (t - h) : kClaim;
-      if (atomicCAS(&ctl->head, h, h + take) == h) {
-        got = static_cast<int>(take);
-        break;
-      }
-      __nanosleep(32 + (tries & 7) * 16);
+constexpr int kAsyncList = 4096;   // ids per shared-memory work list
+constexpr int kAsyncBig = 64;      // high-degree items a CTA scatters together
+constexpr int kAsyncBigDeg = 1024; // out-degree from which an item is scattered by the CTA
+constexpr int kAsyncClaim = 2048;  // ids claimed from the ring at once
+constexpr int kAsyncShare = 512;   // a list longer than this hands half to the ring when it is empty
+
+template <class Op, int BLOCK>
+struct AsyncShared {
+  int cur[kAsyncList];
+  int nxt[kAsyncList];
+  int big_j[kAsyncBig];
+  typename Op::Msg big_m[kAsyncBig];
+  int ncur, nnxt, nbig;
+  int quit, got, share;
+  unsigned long long first;
+};
+
+// Per edge: the scatter (fire-and-forget) and the re-activation test from the
+// receiver's delta read just before it.  Returns the receiver to activate or -1.
+template <class Op>
+__device__ __forceinline__ int async_edge(const AArgs<Op>& a, int64_t e, typename Op::Msg m,
+                                          double tau) {
+  using D = typename Op::D;
+  const typename Op::Edge ed = Op::load(a.edges, e);
+  const int k = ed.k;
+  bool want = false;
+  if constexpr (Op::kIsSum) {
+    const D old = __ldcg(a.delta + k);
+    atomicAdd(a.delta + k, m);
+    const double nw = fabs(static_cast<double>(old) + static_cast<double>(m));
+    want = fabs(static_cast<double>(old)) <= tau && nw > tau;
+  } else {
+    const uint32_t s = m + ed.w;
+    const uint32_t nd = (s < m) ? kInfU32 : s;
+    if (nd < __ldcg(a.delta + k)) {
+      atomicMin(a.delta + k, nd);
+      want = nd < __ldcg(a.v + k);
     }
   }
-  got = __shfl_sync(0xffffffffu, got, 0);
-  *first = __shfl_sync(0xffffffffu, h, 0);
-  return got;
+  if (want) want = atomicExch(a.inq + k, 1u) == 0u;
+  return want ? k : -1;
+}
+
+// Appends the lanes' ids (>= 0) to the next list; what does not fit goes to
+// the ring.
+template <class Op, int BLOCK>
+__device__ __forceinline__ void list_put_warp(const AArgs<Op>& a, AsyncShared<Op, BLOCK>& sh,
+                                              int k, int lane) {
+  const unsigned mask = __ballot_sync(0xffffffffu, k >= 0);
+  if (!mask) return;
+  const int leader = __ffs(mask) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&sh.nnxt, __popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  const int pos = base + __popc(mask & ((1u << lane) - 1u));
+  const bool fits = k >= 0 && pos < kAsyncList;
+  if (fits) sh.nxt[pos] = k;
+  ring_put_warp(a, k >= 0 && !fits, k, lane);
 }
 
 template <class Op, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_async(AArgs<Op> a) {
+__global__ void __launch_bounds__(BLOCK, 1) k_async(AArgs<Op> a) {
   using Msg = typename Op::Msg;
   using D = typename Op::D;
+  __shared__ AsyncShared<Op, BLOCK> sh;
   AsyncCtl* ctl = a.ctl;
   volatile AsyncCtl* vc = ctl;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int kWarps = BLOCK / 32;
   const double tau = ctl->tau;
   const unsigned long long timeout = ctl->timeout_ns;
   unsigned long long my_updates = 0, my_pushes = 0;
-  // idle-wait bookkeeping (lane 0): the wait restarts whenever work moves
-  unsigned long long idle_since = 0, seen_head = ~0ull;
-  long long seen_pending = -1;
-  unsigned backoff = 128;          // idle poll interval (ns), doubled up to 8 us
+  // thread 0's view of the CTA: holding work (counted in busy) or not, and
+  // the idle wait's bookkeeping (restarted whenever work moves anywhere)
+  bool busy = false;
+  unsigned long long idle_since = 0, seen_head = ~0ull, seen_tail = ~0ull;
+  long long seen_busy = -1;
+  unsigned backoff = 128;
+  if (threadIdx.x == 0) { sh.ncur = 0; sh.nnxt = 0; sh.nbig = 0; }
+  __syncthreads();
 
   for (;;) {
-    if (vc->status >= 4) break;
-    unsigned long long first;
-    const int got = claim_warp(ctl, &first, lane);
-    if (got == 0) {
-      // Nothing claimable: done if quiescent, else wait (bounded: timeout
-      // without any claim or completion anywhere in the grid).
-      int quit = 0;
-      if (lane == 0) {
-        const long long pend = vc->pending;
-        const unsigned long long h = vc->head;
-        if (pend == 0) {
-          quit = 1;
+    // ---- take work: the CTA's list, else a claim from the ring
+    if (threadIdx.x == 0) {
+      sh.quit = vc->status >= 4;
+      sh.got = 0;
+      if (!sh.quit && sh.ncur == 0) {
+        const unsigned long long t1 = vc->tail, h = vc->head;
+        if (h < t1) {
+          if (!busy) { atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->busy), 1ull); busy = true; }
+          unsigned long long hh = h;
+          for (int tries = 0; tries < 64; ++tries) {
+            hh = vc->head;
+            const unsigned long long t = vc->tail;
+            if (hh >= t) break;
+            const unsigned long long take =
+                (t - hh) < static_cast<unsigned long long>(kAsyncClaim) ? (t - hh) : kAsyncClaim;
+            if (atomicCAS(&ctl->head, hh, hh + take) == hh) {
+              sh.got = static_cast<int>(take);
+              sh.first = hh;
+              break;
+            }
+            __nanosleep(32 + (tries & 7) * 16);
+          }
+        }
+        if (sh.got == 0) {
+          if (busy) {
+            __threadfence();
+            atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->busy),
+                      static_cast<unsigned long long>(-1ll));
+            busy = false;
+          }
+          // quiescent: ring empty, no CTA busy, and the ring still empty
+          const unsigned long long ta = vc->tail, ha = vc->head;
+          __threadfence();
+          const long long b = vc->busy;
+          __threadfence();
+          const unsigned long long tb = vc->tail;
+          if (ha == ta && ta == tb && b == 0) {
+            sh.quit = 1;
+          } else {
+            const unsigned long long now = global_ns();
+            if (ha != seen_head || ta != seen_tail || b != seen_busy) {
+              seen_head = ha;
+              seen_tail = ta;
+              seen_busy = b;
+              idle_since = now;
+            } else if (now - idle_since > timeout) {
+              atomicMax(&ctl->status, 4);
+              sh.quit = 1;
+            }
+            if (!sh.quit) {
+              __nanosleep(backoff);
+              backoff = backoff < 8192u ? backoff * 2u : 8192u;
+            }
+          }
         } else {
-          const unsigned long long now = global_ns();
-          if (pend != seen_pending || h != seen_head) {
-            seen_pending = pend;
-            seen_head = h;
-            idle_since = now;
-          } else if (now - idle_since > timeout) {
-            atomicMax(&ctl->status, 4);
-            quit = 1;
-          }
-          if (!quit) {
-            __nanosleep(backoff);
-            backoff = backoff < 8192u ? backoff * 2u : 8192u;
-          }
+          backoff = 128;
+          seen_busy = -1;
         }
       }
-      if (__shfl_sync(0xffffffffu, quit, 0)) break;
-      continue;
     }
-    seen_pending = -1;
-    backoff = 128;
-    for (int sub = 0; sub < got; sub += 32) {
-    const int cnt = got - sub < 32 ? got - sub : 32;
-    const unsigned long long fsub = first + static_cast<unsigned long long>(sub);
-    // Read the claimed ids (a slot may still be in the middle of being written).
-    int j = -1;
-    if (lane < cnt) {
-      volatile int* slot = a.queue + ((fsub + lane) % a.cap);
-      int x = *slot;
-      if (x == -1) {
-        const unsigned long long t0 = global_ns();
-        while ((x = *slot) == -1) {
-          if (global_ns() - t0 > timeout) { atomicMax(&ctl->status, 4); break; }
-          __nanosleep(32);
+    __syncthreads();
+    if (sh.quit) break;
+    if (sh.ncur == 0 && sh.got == 0) continue;
+    if (sh.got > 0) {
+      // copy the claimed ids (a slot may still be in the middle of being written)
+      for (int i = threadIdx.x; i < sh.got; i += BLOCK) {
+        volatile int* slot = a.queue + ((sh.first + i) % a.cap);
+        int x = *slot;
+        if (x == -1) {
+          const unsigned long long t0 = global_ns();
+          while ((x = *slot) == -1) {
+            if (global_ns() - t0 > timeout) { atomicMax(&ctl->status, 4); break; }
+            __nanosleep(32);
+          }
         }
-      }
-      j = x;
-      if (j >= 0) {
         *slot = -1;
-        // Leave the queue before taking the delta, so a message that lands
-        // after the take re-enqueues the vertex instead of being stranded.
-        atomicExch(a.inq + j, 0u);
-        __threadfence();
+        sh.cur[i] = x;
       }
+      __syncthreads();
+      if (threadIdx.x == 0) sh.ncur = sh.got;
+      __syncthreads();
     }
-    // Update: take Delta_j, fold it into v_j (atomically: the vertex may be
-    // re-queued and updated by another warp meanwhile), form the message.
-    Msg m{};
-    int beg = 0, deg = 0;
-    if (j >= 0) {
-      beg = __ldg(a.rp + j);
-      deg = __ldg(a.rp + j + 1) - beg;
-      if constexpr (Op::kIsSum) {
-        const D d = atomic_take(a.delta + j);
-        if (d != D(0)) {
-          atomicAdd(a.v + j, static_cast<double>(d));
-          const double c = a.coef ? static_cast<double>(a.coef[j])
-                                  : (deg ? a.damping / static_cast<double>(deg) : 0.0);
-          m = static_cast<Msg>(c * static_cast<double>(d));
+    const int ncur = sh.ncur;
+
+    // ---- update the listed vertices, 32 per warp step
+    for (int base = wid * 32; base < ncur; base += kWarps * 32) {
+      const int i = base + lane;
+      int j = -1;
+      if (i < ncur) {
+        j = sh.cur[i];
+        if (j >= 0) {
+          // leave the queue before taking the delta, so a message that lands
+          // after the take re-activates the vertex instead of being stranded
+          atomicExch(a.inq + j, 0u);
+          __threadfence();
         }
-      } else {
-        const D d = __ldcg(a.delta + j);
-        const unsigned int old = atomicMin(a.v + j, d);
-        m = (d < old) ? d : kInfU32;
       }
-      if (!Op::live(m)) deg = 0;
-      else ++my_updates;
-    }
-    // Walk the batch's edges 32 at a time (prefix sum + owner search).
-    int incl = deg;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    const int excl = incl - deg;
-    my_pushes += deg;
-    for (int t0 = 0; t0 < total; t0 += 32) {
-      const int t = t0 + lane;
-      int owner = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int probe = __shfl_sync(0xffffffffu, incl, owner + step - 1);
-        if (probe <= t) owner += step;
-      }
-      const int ob = __shfl_sync(0xffffffffu, beg, owner);
-      const int oe = __shfl_sync(0xffffffffu, excl, owner);
-      const Msg om = __shfl_sync(0xffffffffu, m, owner);
-      bool want = false;
-      int k = 0;
-      if (t < total) {
-        const typename Op::Edge ed = Op::load(a.edges, static_cast<int64_t>(ob) + (t - oe));
-        k = ed.k;
+      Msg m{};
+      int beg = 0, deg = 0;
+      if (j >= 0) {
+        beg = __ldg(a.rp + j);
+        deg = __ldg(a.rp + j + 1) - beg;
         if constexpr (Op::kIsSum) {
-          const D old = atomicAdd(a.delta + k, om);
-          const double nw = fabs(static_cast<double>(old) + static_cast<double>(om));
-          // re-activate when the receiver's delta crosses the threshold
-          want = (fabs(static_cast<double>(old)) <= tau) && (nw > tau);
+          const D d = atomic_take(a.delta + j);
+          if (d != D(0)) {
+            // the vertex can be re-activated and updated on another SM meanwhile
+            atomicAdd(a.v + j, static_cast<double>(d));
+            if (deg) m = Op::message(j, deg, d, a.coef, a.damping);
+          }
         } else {
-          const uint32_t s = om + ed.w;
-          const uint32_t nd = (s < om) ? kInfU32 : s;
-          if (nd < __ldcg(a.delta + k)) {
-            const uint32_t old = atomicMin(a.delta + k, nd);
-            // re-activate when the receiver's distance can improve
-            want = nd < old && nd < __ldcg(a.v + k);
+          const D d = __ldcg(a.delta + j);
+          const unsigned int old = atomicMin(a.v + j, d);
+          m = (d < old) ? d : kInfU32;
+        }
+        if (!Op::live(m)) {
+          deg = 0;
+        } else {
+          ++my_updates;
+          my_pushes += deg;
+          if (deg >= kAsyncBigDeg) {
+            const int slot = atomicAdd(&sh.nbig, 1);
+            if (slot < kAsyncBig) {
+              sh.big_j[slot] = j;
+              sh.big_m[slot] = m;
+              deg = 0;   // the whole CTA scatters it below
+            }
           }
         }
-        if (want) want = atomicExch(a.inq + k, 1u) == 0u;
       }
-      enqueue_warp(a, want, k, lane);
+      // walk the edges of the step's vertices 32 at a time (prefix sum + owner search)
+      int incl = deg;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      const int excl = incl - deg;
+      for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int probe = __shfl_sync(0xffffffffu, incl, owner + step - 1);
+          if (probe <= t) owner += step;
+        }
+        const int ob = __shfl_sync(0xffffffffu, beg, owner);
+        const int oe = __shfl_sync(0xffffffffu, excl, owner);
+        const Msg om = __shfl_sync(0xffffffffu, m, owner);
+        const int k = t < total ? async_edge(a, static_cast<int64_t>(ob) + (t - oe), om, tau) : -1;
+        list_put_warp(a, sh, k, lane);
+      }
     }
-    }  // sub-batches
-    // The batch is done: its pushes (and the enqueues they caused) are visible.
-    __threadfence();
-    if (lane == 0) {
-      atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->pending),
-                static_cast<unsigned long long>(-static_cast<long long>(got)));
+    __syncthreads();
+    // ---- high-degree vertices: every thread of the CTA takes edges
+    const int nbig = min(sh.nbig, kAsyncBig);
+    for (int b = 0; b < nbig; ++b) {
+      const int j = sh.big_j[b];
+      const Msg m = sh.big_m[b];
+      const int beg = __ldg(a.rp + j), end = __ldg(a.rp + j + 1);
+      for (int e0 = beg; e0 < end; e0 += BLOCK) {
+        const int e = e0 + static_cast<int>(threadIdx.x);
+        const int k = e < end ? async_edge(a, static_cast<int64_t>(e), m, tau) : -1;
+        list_put_warp(a, sh, k, lane);
+      }
     }
+    __syncthreads();
+    // ---- the next list becomes the current one; a long list hands half of
+    // its ids to the ring when the ring is empty, so idle CTAs get work
+    if (threadIdx.x == 0) sh.share = min(sh.nnxt, kAsyncList) > kAsyncShare && vc->head >= vc->tail;
+    __syncthreads();
+    int nn = min(sh.nnxt, kAsyncList);
+    if (sh.share) {
+      const int keep = nn / 2;
+      for (int i0 = keep; i0 < nn; i0 += BLOCK) {
+        const int i = i0 + static_cast<int>(threadIdx.x);
+        ring_put_warp(a, i < nn, i < nn ? sh.nxt[i] : 0, lane);
+      }
+      nn = keep;
+    }
+    for (int i = threadIdx.x; i < nn; i += BLOCK) sh.cur[i] = sh.nxt[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      sh.ncur = nn;
+      sh.nnxt = 0;
+      sh.nbig = 0;
+    }
+    __syncthreads();
   }
+  // leaving with work would break the quiescence count; only a timeout or a
+  // full ring gets here with busy still held (the launch is failed then)
+  if (threadIdx.x == 0 && busy)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->busy),
+              static_cast<unsigned long long>(-1ll));
   my_updates = [&] {
     unsigned long long x = my_updates;
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -298,7 +401,7 @@ __global__ void __launch_bounds__(BLOCK) k_async(AArgs<Op> a) {
 
 // Exact termination check between launches, and the seed of the next one:
 // sum |Delta| (or the pending count) over all vertices, then every vertex above
-// the threshold enters the queue.  The last block decides (residual < eps,
+// the threshold enters the ring.  The last block decides (residual < eps,
 // epoch cap, or an error status from the last launch) and sets the WHILE
 // condition.
 template <class Op, int BLOCK>
@@ -331,7 +434,7 @@ __global__ void __launch_bounds__(BLOCK) k_async_seed(AArgs<Op> a, cudaGraphCond
     sel = sel && !stop_now;
     if (sel) sel = atomicExch(a.inq + j, 1u) == 0u;
     nsel += sel;
-    enqueue_warp(a, sel, j, lane);
+    ring_put_warp(a, sel, j, lane);
   }
   __shared__ double s_r[BLOCK / 32];
   __shared__ unsigned long long s_p[BLOCK / 32], s_s[BLOCK / 32];
@@ -362,7 +465,7 @@ __global__ void __launch_bounds__(BLOCK) k_async_seed(AArgs<Op> a, cudaGraphCond
   ctl->residual = resid;
   unsigned cont = 0;
   if (stop_now) {
-    // a launch reported a timeout or a full queue: keep its status
+    // a launch reported a timeout or a full ring: keep its status
   } else if (Op::kIsSum ? (resid < vc->eps || pend == 0) : (pend == 0)) {
     ctl->status = 1;
   } else if (static_cast<long long>(vc->epochs) >= vc->max_epochs) {
@@ -377,9 +480,9 @@ __global__ void __launch_bounds__(BLOCK) k_async_seed(AArgs<Op> a, cudaGraphCond
   ctl->pend_acc = 0;
   ctl->sel_acc = 0;
   ctl->ticket = 0;
-  // Testing hook: a phantom pending item that nothing will ever complete, so
-  // the next launch's idle warps wait until their timeout and report it.
-  if (cont && vc->inject_stall) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->pending), 1ull);
+  // Testing hook: a phantom busy CTA that never finishes, so the next
+  // launch's idle CTAs wait until their timeout and report it.
+  if (cont && vc->inject_stall) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->busy), 1ull);
   __threadfence();
   if (use_cond) cudaGraphSetConditional(cond, cont);
 }

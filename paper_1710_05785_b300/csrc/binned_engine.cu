@@ -1,10 +1,8 @@
 // Host side of the binned engine (MAITER_ENGINE_BINNED): the static layout
 // of a graph's edges by (sender cell, receiver bin), built on the device on
 // first use and after every maiter_graph_update, and the run - a CUDA graph
-// prime ; WHILE { (scatter ; gather) x 3 }, with the loop condition set by the
-// scatter's CTA 0 (no host round trip per round).  A mixed-precision run
-// starts with the round engine's FP64-delta warm-up (WHILE { scan ; push }),
-// then primes the binned FP32 phase from its deltas.
+// prime ; WHILE { (scatter ; gather) x 3 } per precision phase, with the loop
+// condition set by the scatter's CTA 0 (no host round trip per round).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -83,15 +81,12 @@ maiter_status set_smem_limits() {
   MAITER_CUDA(cudaFuncSetAttribute(k_bin_scatter<float>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    kCellSize * 4));
-  MAITER_CUDA(cudaFuncSetAttribute(k_bin_gather<double, double, double, double>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kBinSize * 8));
-  MAITER_CUDA(cudaFuncSetAttribute(k_bin_gather<double, double, float, double>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kBinSize * 8));
-  MAITER_CUDA(cudaFuncSetAttribute(k_bin_gather<float, float, float, float>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kBinSize * 4));
+  MAITER_CUDA(cudaFuncSetAttribute(k_bin_gather<double, double, double>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSize * 8));
+  MAITER_CUDA(cudaFuncSetAttribute(k_bin_gather<double, double, float>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSize * 8));
+  MAITER_CUDA(cudaFuncSetAttribute(k_bin_gather<float, float, float>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kBinSize * 8));
   done = true;
   return MAITER_OK;
 }
@@ -264,9 +259,8 @@ maiter_status ensure_bins(const maiter_graph* cg, cudaStream_t st) {
 
 namespace {
 
-// One precision phase: prime, then WHILE { (scatter ; gather) x kRounds };
-// AT is the precision of the per-bin sums in shared memory.
-template <class DT, class MT, class CT, class AT>
+// One precision phase: prime, then WHILE { (scatter ; gather) x kRounds }.
+template <class DT, class MT, class CT>
 struct BinPhase {
   BinArgs a{};
   int scatter_grid = 1, gather_grid = 1, prime_grid = 1;
@@ -290,11 +284,11 @@ struct BinPhase {
     cfg.attrs = attr;
     cfg.numAttrs = chained ? 1 : 0;
     cudaLaunchKernelEx(&cfg, k_bin_scatter<MT>, a, h, use_cond);
-    cfg.blockDim = dim3(GatherShape<AT>::kBlock);
+    cfg.blockDim = dim3(kBinGatherBlock);
     cfg.gridDim = dim3(gather_grid);
-    cfg.dynamicSmemBytes = kBinSize * sizeof(AT);
+    cfg.dynamicSmemBytes = kBinSize * sizeof(unsigned long long);
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_bin_gather<DT, MT, CT, AT>, a);
+    cudaLaunchKernelEx(&cfg, k_bin_gather<DT, MT, CT>, a);
   }
   maiter_status add_to(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps,
                        cudaGraphConditionalHandle h, cudaGraphNode_t* node) const {
@@ -327,8 +321,8 @@ struct BinPhase {
       k_bin_scatter<MT><<<scatter_grid, kBinScatterBlock, kCellSize * sizeof(MT), st>>>(
           a, cudaGraphConditionalHandle{}, 0);
       MAITER_CUDA(cudaEventRecord(e[1], st));
-      k_bin_gather<DT, MT, CT, AT><<<gather_grid, GatherShape<AT>::kBlock,
-                                     kBinSize * sizeof(AT), st>>>(a);
+      k_bin_gather<DT, MT, CT><<<gather_grid, kBinGatherBlock,
+                                 kBinSize * sizeof(unsigned long long), st>>>(a);
       MAITER_CUDA(cudaEventRecord(e[2], st));
       MAITER_CUDA(cudaGetLastError());
       MAITER_CUDA(cudaMemcpyAsync(r->h_ctl, r->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st));
@@ -345,8 +339,8 @@ struct BinPhase {
   }
 };
 
-template <class DT, class MT, class CT, class AT>
-void setup_phase(BinPhase<DT, MT, CT, AT>& ph, const maiter_graph* g, maiter_result* r, void* delta,
+template <class DT, class MT, class CT>
+void setup_phase(BinPhase<DT, MT, CT>& ph, const maiter_graph* g, maiter_result* r, void* delta,
                  const void* coef, double damping) {
   const BinLayout* L = g->bins;
   BinArgs& a = ph.a;
@@ -373,8 +367,7 @@ void setup_phase(BinPhase<DT, MT, CT, AT>& ph, const maiter_graph* g, maiter_res
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_scatter<MT>, kBinScatterBlock,
                                                 kCellSize * sizeof(MT));
   ph.scatter_grid = std::max(1, std::min(L->nchunks, g->num_sms * std::max(per_sm, 1)));
-  ph.gather_grid =
-      std::max(1, std::min(L->nbins, g->num_sms * GatherShape<AT>::kMinBlocks));
+  ph.gather_grid = std::max(1, std::min(L->nbins, g->num_sms));
   ph.prime_grid = std::max(1, std::min(static_cast<int>((g->n + 255) / 256), g->num_sms * 4));
 }
 
@@ -402,15 +395,11 @@ maiter_status run_binned(const maiter_graph* g, const maiter_run_params* p, mait
     }
   }
   const void* coef = p->coef ? r->coef : nullptr;
-  BinPhase<double, double, double, double> f64;
-  BinPhase<float, float, float, float> f32;
-  // Mixed precision: the FP64-delta warm-up runs on the round engine, whose
-  // FP64 sums are atomics in L2; the binned engine's per-bin FP64 sums would
-  // be shared-memory FP64 arithmetic, slow on this part.  The FP32 phase,
-  // most of the rounds, is binned.
-  Phase<OpSumWarm> warm;
+  BinPhase<double, double, double> f64;
+  BinPhase<double, double, float> warm;
+  BinPhase<float, float, float> f32;
   if (mixed) {
-    warm.setup(g, r, r->delta_wide, coef, p->damping, Tuning{}, false);
+    setup_phase(warm, g, r, r->delta_wide, coef, p->damping);
     setup_phase(f32, g, r, r->delta, coef, p->damping);
   } else {
     setup_phase(f64, g, r, r->delta, coef, p->damping);
@@ -458,7 +447,9 @@ maiter_status run_binned(const maiter_graph* g, const maiter_run_params* p, mait
     cudaGraphNode_t n0, n1;
     maiter_status s;
     if (mixed) {
-      s = warm.add_to(r->graph, nullptr, 0, h1, &n1);
+      s = prime_node(warm, nullptr, h1, 0, nullptr, 0, &n0);
+      if (s != MAITER_OK) return s;
+      s = warm.add_to(r->graph, &n0, 1, h1, &n1);
       if (s != MAITER_OK) return s;
       cudaGraphConditionalHandle h2;
       MAITER_CUDA(cudaGraphConditionalHandleCreate(&h2, r->graph, 0, 0));
@@ -491,6 +482,7 @@ maiter_status run_binned(const maiter_graph* g, const maiter_run_params* p, mait
     MAITER_CUDA(cudaEventRecord(r->ev0, st));
     maiter_status ls;
     if (mixed) {
+      warm.launch_prime(st, nullptr, cudaGraphConditionalHandle{}, 0);
       ls = warm.host_loop(r, st, e, s);
       if (ls == MAITER_OK) {
         f32.launch_prime(st, static_cast<const double*>(r->delta_wide),
@@ -534,10 +526,10 @@ maiter_status run_binned(const maiter_graph* g, const maiter_run_params* p, mait
   // prime per phase, then whole passes of kRounds rounds (2 kernels each);
   // the pass that stops completes its remaining rounds, which return at once
   const int64_t phases = 1 + (h.phase > 0 ? 1 : 0);
-  constexpr int64_t kPass = BinPhase<double, double, double, double>::kRounds;
+  constexpr int64_t kPass = BinPhase<double, double, double>::kRounds;
   const int64_t decided = static_cast<int64_t>(h.rounds) + phases;
   const int64_t rounds_run = profile ? decided : kPass * ((decided + kPass - 1) / kPass);
-  s.kernel_launches = (mixed ? phases - 1 : phases) + 2 * rounds_run + (profile ? decided : 0);
+  s.kernel_launches = phases + 2 * rounds_run + (profile ? decided : 0);
   s.status = h.status == 1 ? MAITER_OK : MAITER_ERR_NOT_CONVERGED;
   if (h.status != 1)
     set_error("round cap of %lld reached before the termination test held (residual %g)",

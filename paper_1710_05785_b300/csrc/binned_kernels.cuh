@@ -29,11 +29,18 @@
 //            memory and write msg_e[slot] = msg_v[sender of slot] for every
 //            slot - a sequential read of src_local and a sequential write;
 //   k_bin_gather - for every bin: sum the messages of its segments into a
-//            shared-memory array (one slot read, one shared atomic each), then
+//            shared-memory array of 64-bit fixed-point integers (one slot
+//            read, one integer atomic per run of equal receivers), then
 //            for every receiver k of the bin: fold the delta the messages came
 //            from into v_k (v_k <- v_k + Delta_k), store the new delta (the
 //            sum), and its message c_k Delta_k for the next round; the FP64
 //            residual sum |Delta| of the new deltas feeds the next decision.
+// The sums are exact integers: every message is scaled by 2^s, s chosen per
+// round so that the round's total message mass E = sum_j deg_j |m_j| (which
+// bounds every receiver's sum) stays below 2^62; each message loses only the
+// bits below 2^-s (truncation), far below its own FP32 / FP64 ulp.  Integer
+// atomics on shared memory are native; floating-point ones are
+// compare-and-swap loops on this part.
 // Between kernels (v, Delta) is always a complete DAIC state: before the
 // gather the messages in msg_e are a function of the pending deltas, which
 // are still in Delta; after it they have been delivered and folded.
@@ -53,7 +60,6 @@ constexpr int kPieceEdges = 65536;             // edges per chunk at most
 constexpr int kPad = 8;                        // segment padding (entries)
 constexpr unsigned short kPadSrc = 0xFFFF;     // src_local of a padding slot
 constexpr int kBinScatterBlock = 512;
-constexpr int kBinGatherBlock = 1024;
 constexpr int kBinMaxBins = 16384;             // n <= 2^28
 
 struct BinArgs {
@@ -75,9 +81,9 @@ struct BinArgs {
   const int* __restrict__ T;             // (nbins + 1) x nchunks segment starts
   const uint4* __restrict__ src8;        // src_local, 8 per uint4
   const uint4* __restrict__ dst8;        // dst_local, 8 per uint4
-  const int* __restrict__ step_base;     // nbins + 1: first step descriptor of each bin
-  const unsigned* __restrict__ steps;    // per bin, its segments' 32-slot steps:
-                                         // (first slot / 8) << 2 | (slots / 8 - 1)
+  const int* __restrict__ step_base;     // nbins + 1: first group of each bin
+  const unsigned* __restrict__ steps;    // per bin, its segments' 8-slot groups
+                                         // (first slot / 8)
   DevCtl* ctl;
 };
 
@@ -87,28 +93,62 @@ __device__ __forceinline__ double bin_coef(const BinArgs& a, int j, int deg) {
                 : a.damping / static_cast<double>(deg);
 }
 
-// Block-wide sum of (resid, act, push) into set `ws` of the control block,
-// one atomic per block per total.
+// Block-wide sum of (resid, act, push, mass) into set `ws` of the control
+// block, one atomic per block per total.
 template <int BLOCK>
 __device__ __forceinline__ void bin_block_totals(DevCtl* ctl, unsigned ws, double resid,
                                                  unsigned long long act,
-                                                 unsigned long long push) {
-  __shared__ double s_r[BLOCK / 32];
+                                                 unsigned long long push, double mass) {
+  __shared__ double s_r[BLOCK / 32], s_m[BLOCK / 32];
   __shared__ unsigned long long s_a[BLOCK / 32], s_p[BLOCK / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   resid = warp_sum(resid);
+  mass = warp_sum(mass);
   act = warp_sum(act);
   push = warp_sum(push);
-  if (lane == 0) { s_r[wid] = resid; s_a[wid] = act; s_p[wid] = push; }
+  if (lane == 0) { s_r[wid] = resid; s_m[wid] = mass; s_a[wid] = act; s_p[wid] = push; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double r = 0.0;
+    double r = 0.0, ms = 0.0;
     unsigned long long x = 0, y = 0;
-    for (int i = 0; i < BLOCK / 32; ++i) { r += s_r[i]; x += s_a[i]; y += s_p[i]; }
+    for (int i = 0; i < BLOCK / 32; ++i) { r += s_r[i]; ms += s_m[i]; x += s_a[i]; y += s_p[i]; }
     if (r != 0.0) atomicAdd(&ctl->resid_acc[ws], r);
+    if (ms != 0.0) atomicAdd(&ctl->mass_acc[ws], ms);
     if (x) atomicAdd(&ctl->act_acc[ws], x);
     if (y) atomicAdd(&ctl->push_acc[ws], y);
   }
+}
+
+// Fixed point: x * 2^s as a 64-bit integer, truncated toward zero.  The
+// scaling multiplies by exact powers of two (split in two factors so that
+// each fits the type's exponent range), then one conversion; the caller
+// guarantees |x| 2^s < 2^62.
+struct BinScale {
+  float f1, f2;      // 2^s = f1 f2 (FP32 messages)
+  double d;          // 2^s (FP64 messages)
+};
+__device__ __forceinline__ long long bin_fix(float x, const BinScale& sc) {
+  return __float2ll_rz((x * sc.f1) * sc.f2);
+}
+__device__ __forceinline__ long long bin_fix(double x, const BinScale& sc) {
+  return __double2ll_rz(x * sc.d);
+}
+
+// The round's scale: E < 2^e (frexp), s = 62 - e, so E 2^s < 2^62; s is
+// kept within [-250, 250] (sums below 2^-250 are zero to any precision used).
+__device__ __forceinline__ int bin_scale(double mass) {
+  if (!(mass > 0.0)) return 0;
+  int e = 0;
+  frexp(mass, &e);
+  return max(-250, min(250, 62 - e));
+}
+__device__ __forceinline__ BinScale bin_scale_factors(int s) {
+  BinScale r;
+  const int h = s / 2;
+  r.f1 = ldexpf(1.0f, h);
+  r.f2 = ldexpf(1.0f, s - h);
+  r.d = ldexp(1.0, s);
+  return r;
 }
 
 // Primes a phase: msg_v[j] = c_j Delta_j for every vertex and the totals of
@@ -125,7 +165,7 @@ __global__ void __launch_bounds__(256) k_bin_prime(BinArgs a, const double* __re
   const unsigned ws = ctl->scan_set;
   DT* delta = static_cast<DT*>(a.delta);
   MT* msg = static_cast<MT*>(a.msg_v);
-  double resid = 0.0;
+  double resid = 0.0, mass = 0.0;
   unsigned long long act = 0, push = 0;
   for (int j = blockIdx.x * 256 + threadIdx.x; j < a.n; j += gridDim.x * 256) {
     DT d;
@@ -140,12 +180,14 @@ __global__ void __launch_bounds__(256) k_bin_prime(BinArgs a, const double* __re
     // divide per vertex and round would cost more than the round's sums)
     const MT cj = deg > 0 ? static_cast<MT>(bin_coef<CT>(a, j, deg)) : MT(0);
     static_cast<MT*>(a.cmsg)[j] = cj;
-    msg[j] = (d != DT(0)) ? cj * static_cast<MT>(d) : MT(0);
+    const MT m = (d != DT(0)) ? cj * static_cast<MT>(d) : MT(0);
+    msg[j] = m;
     resid += fabs(static_cast<double>(d));
+    mass += static_cast<double>(deg) * fabs(static_cast<double>(m));
     act += (d != DT(0));
     push += (d != DT(0)) ? static_cast<unsigned long long>(deg) : 0ull;
   }
-  bin_block_totals<256>(ctl, ws, resid, act, push);
+  bin_block_totals<256>(ctl, ws, resid, act, push, mass);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->push_set = ws;
     if (wide) {
@@ -201,6 +243,7 @@ __device__ __forceinline__ int bin_decide(DevCtl* ctl, cudaGraphConditionalHandl
       ctl->status = status;
     }
     ctl->resid_acc[ns] = 0.0;
+    ctl->mass_acc[ns] = 0.0;
     ctl->act_acc[ns] = ctl->push_acc[ns] = ctl->pend_acc[ns] = 0;
     ctl->cnt[ns][0] = 0;                 // the gather's bin ticket
     ctl->scan_set = ns;
@@ -290,71 +333,66 @@ __global__ void __launch_bounds__(kBinScatterBlock) k_bin_scatter(BinArgs a,
   }
 }
 
-// Adds one step of a segment (32 consecutive slots, lane i holding slot i)
-// into the bin's shared-memory sums.  A run is a maximal group of adjacent
-// lanes with the same receiver; segments are sorted by receiver, so all
-// messages of a step to one receiver form one run.  When every lane is its
-// own run, each lane adds its message; otherwise a segmented inclusive scan
-// leaves each run's sum in its last lane, which adds it with one atomic.
-// Zero messages (padding, senders without a pending delta) add nothing.
-template <class AT>
-__device__ __forceinline__ void bin_warp_add(AT* acc, unsigned key, AT x, int lane) {
-  const unsigned prevk = __shfl_up_sync(0xffffffffu, key, 1);
-  const bool head = lane == 0 || prevk != key;
-  if (__all_sync(0xffffffffu, head)) {
-    if (x != AT(0) && key < kBinSize) atomicAdd(acc + key, x);
-    return;
-  }
-  // rs = first lane of this lane's run (max-scan of the run heads)
-  int rs = head ? lane : 0;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const int r2 = __shfl_up_sync(0xffffffffu, rs, off);
-    if (lane >= off && r2 > rs) rs = r2;
-  }
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const AT y = __shfl_up_sync(0xffffffffu, x, off);
-    if (lane - off >= rs) x += y;
-  }
-  const bool next_head = __shfl_down_sync(0xffffffffu, head ? 1 : 0, 1) != 0;
-  if ((lane == 31 || next_head) && x != AT(0) && key < kBinSize) atomicAdd(acc + key, x);
+constexpr int kBinGatherBlock = 1024;   // one CTA per SM: 128 KB of 64-bit sums
+
+// acc[k] += x on a shared-memory word, as a reduction with no return value,
+// addressed in the shared window (a generic-address atomic is slower).
+__device__ __forceinline__ void bin_red(unsigned long long* acc, unsigned k, long long x) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(acc + k));
+  asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(a), "l"(x) : "memory");
 }
 
-constexpr int kGatherUnroll = 4;   // steps whose loads a warp has in flight
-
-// Gather block shape: FP32 sums (64 KB of shared memory per bin) run three
-// 512-thread CTAs per SM; FP64 sums (128 KB) one 1024-thread CTA.
-template <class AT> struct GatherShape;
-template <> struct GatherShape<float> { static constexpr int kBlock = 512, kMinBlocks = 3; };
-template <> struct GatherShape<double> { static constexpr int kBlock = 1024, kMinBlocks = 1; };
+// The 8 slots of one group into the bin's sums: receivers of a sorted
+// segment ascend, so equal receivers are adjacent and each run of them is
+// added with one integer atomic.  Padding slots carry receivers >= kBinSize
+// and zero messages: skipped.
+template <class MT>
+__device__ __forceinline__ void bin_group_add(unsigned long long* acc, const uint4& d,
+                                              const Msg8<MT>& m, const BinScale& s) {
+  const unsigned short* k = reinterpret_cast<const unsigned short*>(&d);
+  unsigned rk = k[0];
+  long long run = bin_fix(msg8_get(m, 0), s);
+#pragma unroll
+  for (int i = 1; i < 8; ++i) {
+    const unsigned ki = k[i];
+    const long long xi = bin_fix(msg8_get(m, i), s);
+    if (ki == rk) {
+      run += xi;
+    } else {
+      if (run != 0 && rk < kBinSize) bin_red(acc, rk, run);
+      rk = ki;
+      run = xi;
+    }
+  }
+  if (run != 0 && rk < kBinSize) bin_red(acc, rk, run);
+}
 
 // Gather: per bin, sum the messages of its segments in shared memory, then
 // fold the old deltas into v, store the new deltas and their messages, and
 // accumulate the totals of the new deltas for the next decision.  A bin's
-// segments are cut into steps of at most 32 slots (descriptors built with
-// the layout); warps take 32 descriptors at a time and walk them with
-// kGatherUnroll steps' loads in flight, one slot per lane.
-template <class DT, class MT, class CT, class AT>
-__global__ void __launch_bounds__(GatherShape<AT>::kBlock, GatherShape<AT>::kMinBlocks)
-    k_bin_gather(BinArgs a) {
-  constexpr int BLOCK = GatherShape<AT>::kBlock;
+// segments are listed as 8-slot groups (built with the layout); each thread
+// takes groups, two at a time, with one 16-byte load of receivers and the
+// messages' vector loads per group.
+template <class DT, class MT, class CT>
+__global__ void __launch_bounds__(kBinGatherBlock, 1) k_bin_gather(BinArgs a) {
+  constexpr int BLOCK = kBinGatherBlock;
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();
   DevCtl* ctl = a.ctl;
   if (ctl->status != 0) return;   // after the stopping round of this pass
   const unsigned ws = ctl->scan_set;
+  // the messages of this round came from the deltas the set ws ^ 1 measured
+  const int s_round = bin_scale(ctl->mass_acc[ws ^ 1u]);
+  const BinScale sc = bin_scale_factors(s_round);
+  const double unscale = ldexp(1.0, -s_round);
   extern __shared__ __align__(16) unsigned char bin_smem[];
-  AT* acc = reinterpret_cast<AT*>(bin_smem);
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(bin_smem);
   __shared__ int s_bin;
-  for (int k = threadIdx.x; k < kBinSize; k += BLOCK) acc[k] = AT(0);
+  for (int k = threadIdx.x; k < kBinSize; k += BLOCK) acc[k] = 0ull;
   DT* delta = static_cast<DT*>(a.delta);
   MT* msg_v = static_cast<MT*>(a.msg_v);
   const MT* msg_e = static_cast<const MT*>(a.msg_e);
-  const unsigned short* dst = reinterpret_cast<const unsigned short*>(a.dst8);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  constexpr int kWarps = BLOCK / 32;
-  double resid = 0.0;
+  double resid = 0.0, mass = 0.0;
   unsigned long long act = 0, push = 0;
   for (;;) {
     if (threadIdx.x == 0) s_bin = static_cast<int>(atomicAdd(&ctl->cnt[ws][0], 1u));
@@ -362,48 +400,45 @@ __global__ void __launch_bounds__(GatherShape<AT>::kBlock, GatherShape<AT>::kMin
     const int b = s_bin;
     if (b >= a.nbins) break;
     const int q0 = __ldg(a.step_base + b), q1 = __ldg(a.step_base + b + 1);
-    for (int qb = q0 + wid * 32; qb < q1; qb += kWarps * 32) {
-      const unsigned my = (qb + lane < q1) ? __ldg(a.steps + qb + lane) : 0u;
-      const int nq = min(32, q1 - qb);
-      for (int u0 = 0; u0 < nq; u0 += kGatherUnroll) {
-        unsigned key[kGatherUnroll];
-        MT val[kGatherUnroll];
-#pragma unroll
-        for (int u = 0; u < kGatherUnroll; ++u) {
-          const unsigned d = __shfl_sync(0xffffffffu, my, (u0 + u) & 31);
-          const int start = static_cast<int>(d >> 2) * kPad;
-          const int len = static_cast<int>((d & 3u) + 1u) * kPad;
-          const bool ok = u0 + u < nq && lane < len;
-          key[u] = ok ? static_cast<unsigned>(__ldcs(dst + start + lane)) : 0u;
-          val[u] = ok ? __ldcs(msg_e + start + lane) : MT(0);
-        }
-#pragma unroll
-        for (int u = 0; u < kGatherUnroll; ++u)
-          if (u0 + u < nq) bin_warp_add<AT>(acc, key[u], static_cast<AT>(val[u]), lane);
-      }
+    int q = q0 + threadIdx.x;
+    for (; q + BLOCK < q1; q += 2 * BLOCK) {
+      const unsigned g0 = __ldg(a.steps + q), g1 = __ldg(a.steps + q + BLOCK);
+      const uint4 d0 = __ldcs(a.dst8 + g0), d1 = __ldcs(a.dst8 + g1);
+      const Msg8<MT> m0 = load_msg8(msg_e + static_cast<int64_t>(g0) * kPad);
+      const Msg8<MT> m1 = load_msg8(msg_e + static_cast<int64_t>(g1) * kPad);
+      bin_group_add<MT>(acc, d0, m0, sc);
+      bin_group_add<MT>(acc, d1, m1, sc);
+    }
+    if (q < q1) {
+      const unsigned g0 = __ldg(a.steps + q);
+      const uint4 d0 = __ldcs(a.dst8 + g0);
+      const Msg8<MT> m0 = load_msg8(msg_e + static_cast<int64_t>(g0) * kPad);
+      bin_group_add<MT>(acc, d0, m0, sc);
     }
     __syncthreads();
     const int j0 = b << kBinShift;
     const int cnt = min(kBinSize, a.n - j0);
     for (int k = threadIdx.x; k < cnt; k += BLOCK) {
       const int j = j0 + k;
-      const AT x = acc[k];
-      acc[k] = AT(0);
-      const DT dnew = static_cast<DT>(x);
+      const long long x = static_cast<long long>(acc[k]);
+      acc[k] = 0ull;
+      const DT dnew = static_cast<DT>(static_cast<double>(x) * unscale);
       const DT dold = delta[j];
       if (dold != DT(0)) __stcs(a.v + j, __ldcs(a.v + j) + static_cast<double>(dold));
       delta[j] = dnew;
       const int deg = __ldg(a.rp + j + 1) - __ldg(a.rp + j);
-      msg_v[j] = (dnew != DT(0)) ? __ldg(static_cast<const MT*>(a.cmsg) + j) * static_cast<MT>(dnew)
-                                 : MT(0);
+      const MT m = (dnew != DT(0)) ? __ldg(static_cast<const MT*>(a.cmsg) + j) * static_cast<MT>(dnew)
+                                   : MT(0);
+      msg_v[j] = m;
       resid += fabs(static_cast<double>(dnew));
+      mass += static_cast<double>(deg) * fabs(static_cast<double>(m));
       act += (dnew != DT(0));
       push += (dnew != DT(0)) ? static_cast<unsigned long long>(deg) : 0ull;
     }
     // acc is zero again once every thread is past the fold; the next
     // iteration's __syncthreads orders that before its sums
   }
-  bin_block_totals<BLOCK>(ctl, ws, resid, act, push);
+  bin_block_totals<BLOCK>(ctl, ws, resid, act, push, mass);
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->push_set = ws;
 }
 
@@ -591,8 +626,9 @@ __global__ void __launch_bounds__(kSortBlock) k_bin_sort(const int* __restrict__
 
 constexpr int kStepBlock = 1024;
 
-// Per bin: the number of 32-slot steps of its segments (pass 0), then their
-// descriptors from the bin's first step on (pass 1).  One CTA per bin.
+// Per bin: the number of 8-slot groups of its segments (pass 0), then the
+// groups' first slots / 8 from the bin's first entry on (pass 1).  One CTA per
+// bin.
 template <int PASS>
 __global__ void __launch_bounds__(kStepBlock) k_bin_steps(const int* __restrict__ T, int nchunks,
                                                           int nbins, int* __restrict__ count,
@@ -605,7 +641,7 @@ __global__ void __launch_bounds__(kStepBlock) k_bin_steps(const int* __restrict_
     const int* Te = Tb + nchunks;
     const int c0 = threadIdx.x * per, c1 = min(nchunks, c0 + per);
     int run = 0;
-    for (int c = c0; c < c1; ++c) run += (Te[c] - Tb[c] + 31) >> 5;
+    for (int c = c0; c < c1; ++c) run += (Te[c] - Tb[c]) / kPad;
     if (PASS == 0) {
       s_part[threadIdx.x] = run;
       __syncthreads();
@@ -625,12 +661,8 @@ __global__ void __launch_bounds__(kStepBlock) k_bin_steps(const int* __restrict_
     }
     __syncthreads();
     int q = step_base[b] + s_part[threadIdx.x];
-    for (int c = c0; c < c1; ++c) {
-      for (int s0 = Tb[c]; s0 < Te[c]; s0 += 32) {
-        const int len = min(32, Te[c] - s0);
-        steps[q++] = (static_cast<unsigned>(s0 / kPad) << 2) | static_cast<unsigned>(len / kPad - 1);
-      }
-    }
+    for (int c = c0; c < c1; ++c)
+      for (int s0 = Tb[c]; s0 < Te[c]; s0 += kPad) steps[q++] = static_cast<unsigned>(s0 / kPad);
     __syncthreads();
   }
 }

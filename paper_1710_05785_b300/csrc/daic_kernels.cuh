@@ -57,6 +57,8 @@ struct DevCtl {
   unsigned long long push_acc[2];  // [set] sum of out-degrees of selected vertices
   unsigned long long pend_acc[2];  // [set] pending vertices (Delta != 0 / Delta < v)
   unsigned int minpend_acc[2];     // [set] min: smallest pending Delta (BUCKET scheduling)
+  double mass_acc[2];              // [set] binned engine: sum of deg_j |message_j| (bounds
+                                   // every receiver's sum; sets the fixed-point scale)
   // Decision inputs that change from round to round, per set: the push
   // reading set s writes set s ^ 1, so no CTA reads a word another CTA of the
   // same launch writes.

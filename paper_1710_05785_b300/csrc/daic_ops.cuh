@@ -33,7 +33,8 @@ __device__ __forceinline__ float atomic_take(float* p) { return atomicExch(p, 0.
 
 // ------------------------------------------------------------------ + (sum)
 // State v in FP64; delta in DT (double or float); coefficients in CT.  The
-// message c_j * Delta_j is formed in FP64 and rounded once to DT.
+// message c_j * Delta_j is an FP32 product when both are FP32, else formed in
+// FP64 and rounded once to DT.
 template <class DT, class CT>
 struct OpSum {
   using V = double;
@@ -58,6 +59,15 @@ struct OpSum {
     // not push the Delta lines the pushes' atomics need out of L2
     __stcs(v + j, __ldcs(v + j) + static_cast<double>(d));
     if (deg == 0) return D(0);
+    return message(j, deg, d, coef, damping);
+  }
+  // c_j Delta_j: in FP32 when delta and coefficient are FP32, else formed in
+  // FP64 and rounded once to D.
+  __device__ static __forceinline__ Msg message(int j, int deg, D d, const C* coef,
+                                                double damping) {
+    if constexpr (sizeof(D) == 4 && sizeof(C) == 4) {
+      if (coef) return coef[j] * d;
+    }
     const double c = coef ? static_cast<double>(coef[j]) : damping / static_cast<double>(deg);
     return static_cast<D>(c * static_cast<double>(d));
   }
@@ -75,8 +85,7 @@ struct OpSum {
     if (d == D(0)) return D(0);
     if (first_chunk) __stcs(v + j, __ldcs(v + j) + static_cast<double>(d));
     if (deg == 0) return D(0);
-    const double c = coef ? static_cast<double>(coef[j]) : damping / static_cast<double>(deg);
-    return static_cast<D>(c * static_cast<double>(d));
+    return message(j, deg, d, coef, damping);
   }
 
   __device__ static __forceinline__ bool live(Msg m) { return m != Msg(0); }

@@ -279,6 +279,25 @@ static size_t state_bytes(int op) { return is_order_op(op) ? 4 : 8; }
 static size_t delta_bytes(int op) { return op == MAITER_OP_SUM_F64 ? 8 : 4; }
 static size_t coef_bytes(int op) { return op == MAITER_OP_SUM_F64 ? 8 : 4; }
 
+// Round-engine and asynchronous sums with g = c_j x and no caller
+// coefficients: c_j = damping / outdeg(j) is tabulated once per run
+// (k_degree_coef).
+static bool derived_coef(const maiter_run_params* p) {
+  return !p->coef && (p->engine == MAITER_ENGINE_SYNC || p->engine == MAITER_ENGINE_ASYNC) &&
+         p->g == MAITER_G_SCALE_BY_SRC &&
+         (p->op == MAITER_OP_SUM_F64 || p->op == MAITER_OP_SUM_MIXED);
+}
+
+template <class C>
+static __global__ void k_degree_coef(const int* __restrict__ rp, int64_t n, double damping,
+                                     C* __restrict__ coef) {
+  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n;
+       j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int deg = rp[j + 1] - rp[j];
+    coef[j] = deg > 0 ? static_cast<C>(damping / static_cast<double>(deg)) : C(0);
+  }
+}
+
 maiter_status alloc_result(const maiter_graph* g, int op, maiter_result** out) {
   maiter_result* r = new (std::nothrow) maiter_result();
   MAITER_REQUIRE(r, "host allocation failed");
@@ -373,7 +392,7 @@ static maiter_status ensure_indegree(const maiter_graph* g) {
 static maiter_status setup_plan(const maiter_graph* g, const maiter_run_params* p,
                                 maiter_result* r, const Tuning& tu, RunPlan* plan,
                                 bool track = false) {
-  const void* coef = p->coef ? r->coef : nullptr;
+  const void* coef = (p->coef || derived_coef(p)) ? r->coef : nullptr;
   const bool learned = p->sched == MAITER_SCHED_LEARNED;
   const bool topq = p->sched == MAITER_SCHED_TOPFRAC || learned;
   if (topq && !r->topq) {
@@ -685,6 +704,19 @@ static maiter_status run_op(const maiter_graph* g, const maiter_run_params* p, m
   } else if (p->coef && g->n > 0) {
     if (!r->coef) MAITER_CUDA(cudaMalloc(&r->coef, coef_bytes(r->op) * g->n));
     MAITER_CUDA(cudaMemcpyAsync(r->coef, p->coef, coef_bytes(r->op) * g->n, cudaMemcpyDefault, st));
+  } else if (derived_coef(p) && g->n > 0) {
+    // c_j = damping / outdeg(j) once per run: the update then reads c_j
+    // instead of dividing in FP64 at every vertex update (FP64 arithmetic is
+    // slow on this part)
+    if (!r->coef) MAITER_CUDA(cudaMalloc(&r->coef, coef_bytes(r->op) * g->n));
+    if (r->op == MAITER_OP_SUM_F64)
+      k_degree_coef<double><<<conversion_grid(g), 256, 0, st>>>(g->rp, g->n, p->damping,
+                                                                static_cast<double*>(r->coef));
+    else
+      k_degree_coef<float><<<conversion_grid(g), 256, 0, st>>>(g->rp, g->n, p->damping,
+                                                               static_cast<float*>(r->coef));
+    MAITER_CUDA(cudaGetLastError());
+    ++init_launches;
   }
   if (g->n == 0) {
     r->stats = maiter_stats{};

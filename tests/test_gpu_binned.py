@@ -167,3 +167,18 @@ def test_binned_refuses_what_it_does_not_serve(mt):
     with pytest.raises(mt.MaiterError) as e:
         mt.run(G, mt.OP_SUM_F64, edge_coef=np.ones(g.m), engine=mt.ENGINE_BINNED)
     assert e.value.status == mt.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("opname", ["OP_SUM_F64", "OP_SUM_MIXED"])
+def test_binned_runs_are_bitwise_reproducible(mt, opname):
+    # the per-bin sums are exact integers, so the order of the atomic adds
+    # cannot change a result: two runs agree bit for bit
+    g = graphgen.rmat(15, 16)
+    G = mt.Graph.from_csr(g)
+    op = getattr(mt, opname)
+    a = binned(mt, G, op, damping=D, eps=1e-9)
+    va, da = a.state(), a.delta()
+    b = binned(mt, G, op, damping=D, eps=1e-9)
+    np.testing.assert_array_equal(va, b.state())
+    np.testing.assert_array_equal(da, b.delta())
+    assert a.stats()["rounds"] == b.stats()["rounds"]

@@ -35,7 +35,9 @@ def runs(mt, pagerank24):
     out = {"OP_SUM_F64": pagerank24["v"], "bound_f64": pagerank24["bound"]}
     for name, kw in [("OP_SUM_MIXED", dict(op=mt.OP_SUM_MIXED)),
                      ("binned_f64", dict(op=mt.OP_SUM_F64, engine=mt.ENGINE_BINNED)),
-                     ("binned_mixed", dict(op=mt.OP_SUM_MIXED, engine=mt.ENGINE_BINNED))]:
+                     ("binned_mixed", dict(op=mt.OP_SUM_MIXED, engine=mt.ENGINE_BINNED)),
+                     ("binned_f32", dict(op=mt.OP_SUM_MIXED, engine=mt.ENGINE_BINNED,
+                                         mixed_switch=1.0))]:
         op = kw.pop("op")
         r = mt.run(G, op, damping=D, eps=4e-8, **kw)
         assert r.stats()["converged"] == 1
@@ -56,7 +58,7 @@ def test_pagerank_scale24_mixed_within_1e6(runs):
     assert err <= 1e-6 * vf.max(), (err, vf.max())
 
 
-@pytest.mark.parametrize("name", ["binned_f64", "binned_mixed"])
+@pytest.mark.parametrize("name", ["binned_f64", "binned_mixed", "binned_f32"])
 def test_pagerank_scale24_binned_within_1e6(runs, name):
     vb, vf = runs[name], runs["OP_SUM_F64"]
     err = np.abs(vb - vf).max() + runs["bound_f64"]
