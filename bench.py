@@ -729,7 +729,7 @@ def batch_cpu_baseline(graphs, queries, edges, budget_s=20.0):
                       f"({dt:.1f} s; PPR by synchronous iteration to the query's eps)"}
 
 
-def train_scorers(mt, device=0, q=0.1, epochs=20, samples=8192, records=96):
+def train_scorers(mt, device=0, q=0.1, epochs=20, samples=8192, records=320):
     """The learned workload's scorers: one trained on the activation trace of a
     PageRank run (d = 0.8, top-q scheduling) on an R-MAT scale-20 graph, one
     on an SSSP run's trace on another scale-20 graph; both trained on the GPU

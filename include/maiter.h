@@ -102,11 +102,14 @@ typedef enum {
   MAITER_SCHED_TOPFRAC = 2,   /* the top_frac fraction of pending vertices by
                                  priority, ties included (priority queue of
                                  Section 5.1) */
-  MAITER_SCHED_LEARNED = 3,   /* the top_frac fraction of pending vertices by the
-                                 score of a learned network (params.scorer, a
-                                 maiter_mlp); every 8th round activates every
-                                 pending vertex, so none can starve (Theorem 3
-                                 needs every vertex updated again eventually) */
+  MAITER_SCHED_LEARNED = 3,   /* about the top_frac fraction of pending vertices
+                                 by the score of a learned network (params.scorer,
+                                 a maiter_mlp): the threshold is the score ranked
+                                 top_frac among 4096 vertices drawn by a hash of
+                                 the round (extraction by sampling, Section 5.1);
+                                 every 8th round activates every pending vertex,
+                                 so none can starve (Theorem 3 needs every vertex
+                                 updated again eventually) */
   MAITER_SCHED_BUCKET = 4     /* min only, distance-ordered (delta-stepping): the
                                  pending vertices with Delta_j < tau, where tau starts
                                  at the bucket width `threshold` and, whenever no

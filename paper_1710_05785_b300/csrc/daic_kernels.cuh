@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include "daic_ops.cuh"
+#include "mlp.cuh"
 
 namespace maiter {
 
@@ -84,8 +85,14 @@ struct DevCtl {
 
 // Top-fraction selection state (see topq_kernels.cuh).
 constexpr int kHistBins = 2048;
+// LEARNED: vertices drawn per round to fix the selection threshold.
+constexpr int kLearnedSample = 4096;
+
 struct TopqCtl {
   unsigned int hist[3][kHistBins];  // one histogram per radix pass (zeroed after use)
+  unsigned int sample[kLearnedSample];  // LEARNED: the keys of the round's draws
+  unsigned int sample_done;         // LEARNED: CTAs that have written their draws
+  unsigned int sample_pend;         // LEARNED: draws that hit a pending vertex
   unsigned int ticket[3];
   unsigned int prefix;              // key bits fixed by the passes so far
   unsigned int kth;                 // rank still to find within the prefix bucket
@@ -133,12 +140,63 @@ struct KArgs {
   unsigned int large_cap;        // capacity of large / large_d
   DevCtl* ctl;
   const TopqCtl* topq;           // non-null: select key >= topq->key_thr (TOPFRAC, LEARNED)
-  const unsigned* keys;          // non-null (LEARNED): per-vertex priority keys from the scorer
+  const MlpWeights* mlp;         // non-null (LEARNED): the scorer whose output is the key
+  const int* indeg;              // LEARNED / traces: in-degrees (a feature)
   unsigned* last_act;            // non-null: round of each vertex's last update (1-based)
   int cut_warp;                  // deg <  cut_warp : small bucket
   int cut_cta;                   // deg >= cut_cta  : large bucket (chunked)
   int bucket;                    // min: distance-ordered selection (Delta_j < tau)
 };
+
+// What the scorer reads of vertex j: its delta and state, out-degree, round
+// of last update and in-degree.  Loaded apart from the arithmetic so that a
+// thread can have the loads of several vertices in flight at once.
+template <class Op>
+struct LearnIn {
+  typename Op::D d;
+  typename Op::V v;
+  int deg;
+  int indeg;
+  unsigned la;
+};
+
+template <class Op>
+__device__ __forceinline__ LearnIn<Op> learn_in(const KArgs<Op>& a, int j) {
+  LearnIn<Op> in;
+  in.d = a.delta[j];
+  in.v = a.v[j];
+  in.deg = __ldg(a.rp + j + 1) - __ldg(a.rp + j);
+  in.indeg = a.indeg[j];
+  in.la = a.last_act ? a.last_act[j] : 0u;
+  return in;
+}
+
+// Scorer features (see vertex_features) of a vertex at round `round`.
+template <class Op>
+__device__ __forceinline__ void features_of(const KArgs<Op>& a, const LearnIn<Op>& in,
+                                            unsigned round, float* f) {
+  const unsigned age = in.la ? round + 1u - in.la : round + 1u;
+  const float n = u32_to_f32(static_cast<unsigned>(a.n));
+  if constexpr (Op::kIsSum) {
+    vertex_features<true>(abs_f32(in.d), abs_f32(in.v), true, true, in.indeg, in.deg, age, n, f);
+  } else {
+    vertex_features<false>(Op::fvalue(in.d), Op::fvalue(in.v), in.d != Op::kNone,
+                           in.v != Op::kNone, in.indeg, in.deg, age, n, f);
+  }
+}
+
+// LEARNED scheduling.  A pending vertex not updated for kMaxAge rounds gets
+// the largest key, so it is selected whatever the network says: no vertex
+// waits for ever, which the convergence of priority scheduling (Lemma 5,
+// Theorem 3) needs.  Otherwise its key is the scorer's estimate of the mass
+// an update of j moves per message (Section 3.5's priority |v (+) Delta - v|
+// weighed by the update's cost), scored a warp at a time (warp_score).
+constexpr unsigned kMaxAge = 16;
+constexpr unsigned kAgedKey = 0xFFFFFFFFu;
+
+__device__ __forceinline__ bool aged_out(unsigned la, unsigned round) {
+  return round + 1u - la >= kMaxAge;
+}
 
 __device__ __forceinline__ double warp_sum(double x) {
 #pragma unroll
@@ -161,10 +219,20 @@ __device__ __forceinline__ int warp_incl_scan(int x, int lane) {
 
 // ------------------------------------------------------------------ scan
 
-template <class Op, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, kScanMinBlocks) k_scan(KArgs<Op> a) {
+// kLearn (LEARNED scheduling): the key of every pending vertex is the
+// scorer's output, computed here in the tile pass (no key array, no second
+// pass over the vertices); the threshold comes from k_learned_threshold.
+template <class Op, int BLOCK, bool kLearn = false>
+__global__ void __launch_bounds__(BLOCK, kLearn ? 3 : kScanMinBlocks) k_scan(KArgs<Op> a) {
   static_assert(BLOCK % 32 == 0 && BLOCK <= 1024, "block");
   using D = typename Op::D;
+  // the scorer's weights do not change during a run: staged before the wait
+  // (unreferenced, so not allocated, without kLearn)
+  __shared__ MlpFrag s_w[1];
+  if constexpr (kLearn) {
+    stage_mlp(a.mlp, s_w);
+    __syncthreads();
+  }
   // Launched as a programmatic dependent of the kernel before it: wait until
   // that grid's writes are visible (a no-op after an ordinary launch), and let
   // the next kernel's CTAs be scheduled as this grid's CTAs retire.
@@ -177,6 +245,7 @@ __global__ void __launch_bounds__(BLOCK, kScanMinBlocks) k_scan(KArgs<Op> a) {
   const unsigned ws = ctl->scan_set;
   const double tau = ctl->tau;
   const unsigned key_thr = a.topq ? a.topq->key_thr : 0u;
+  const unsigned round = static_cast<unsigned>(ctl->rounds);
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   constexpr int kWarps = BLOCK / 32;
@@ -188,11 +257,15 @@ __global__ void __launch_bounds__(BLOCK, kScanMinBlocks) k_scan(KArgs<Op> a) {
   double rsum = 0.0;
   unsigned nact = 0, npush = 0, npend = 0;
   unsigned dmin = 0xFFFFFFFFu;               // min: smallest pending Delta seen (bits)
-  const bool bucket = !Op::kIsSum && a.bucket;
+  const bool bucket = !kLearn && !Op::kIsSum && a.bucket;   // BUCKET and LEARNED exclude each other
   // per-warp exclusive offsets: [0] small and medium counts packed in the
   // two 16-bit halves of one int (a tile holds kTile < 2^16 vertices), [1]
   // large-vertex chunks
   __shared__ int s_woff[2][kWarps];
+  // kLearn: each warp's pending vertices of the tile, compacted so that the
+  // scorer runs on converged lanes (a sparse frontier costs only its size)
+  __shared__ uint4 s_lf[kLearn ? kWarps : 1][32 * kItems];   // feature rows
+  __shared__ float s_ly[kLearn ? kWarps : 1][32 * kItems];   // their scores
   __shared__ unsigned s_base[3];             // the tile's base position, per bucket
   static_assert(kTile < 65536, "packed small/medium counts");
 
@@ -217,6 +290,55 @@ __global__ void __launch_bounds__(BLOCK, kScanMinBlocks) k_scan(KArgs<Op> a) {
       dd[u] = in ? a.delta[j] : kNone;
       vv[u] = Op::kIsSum ? typename Op::V(0) : (in ? a.v[j] : typename Op::V(Op::kNone));
     }
+    unsigned lkey[kItems];
+    if constexpr (kLearn) {
+      // the scorer's inputs of this thread's pending items (coalesced loads,
+      // all in flight before any is used)
+      bool pnd[kItems];
+      LearnIn<Op> in[kItems];
+#pragma unroll
+      for (int u = 0; u < kItems; ++u) {
+        const int j = tile + u * BLOCK + static_cast<int>(threadIdx.x);
+        pnd[u] = j < a.n && Op::pending(dd[u], vv[u]);
+        in[u].d = dd[u];
+        in[u].v = vv[u];
+        in[u].deg = 0;
+        in[u].indeg = 0;
+        in[u].la = 0u;
+        if (pnd[u]) {
+          if constexpr (Op::kIsSum) in[u].v = a.v[j];
+          in[u].deg = __ldg(a.rp + j + 1) - __ldg(a.rp + j);
+          in[u].indeg = a.indeg[j];
+          in[u].la = a.last_act[j];
+        }
+      }
+      // rows of the warp's scored vertices, compacted (a sparse frontier
+      // costs only its size)
+      int slot[kItems];
+      unsigned cnt_w = 0;
+      const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+      for (int u = 0; u < kItems; ++u) {
+        const bool aged = pnd[u] && aged_out(in[u].la, round);
+        const bool sc = pnd[u] && !aged;
+        const unsigned b = __ballot_sync(0xffffffffu, sc);
+        slot[u] = sc ? static_cast<int>(cnt_w + __popc(b & lt)) : -1;
+        if (sc) {
+          float f[kMlpIn];
+          features_of(a, in[u], round, f);
+          s_lf[wid][slot[u]] = pack_features(f);
+        }
+        lkey[u] = aged ? kAgedKey : 0u;
+        cnt_w += __popc(b);
+      }
+      __syncwarp();
+      warp_score(s_w[0], s_lf[wid], static_cast<int>(cnt_w), s_ly[wid]);
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < kItems; ++u)
+        if (slot[u] >= 0) lkey[u] = score_key(s_ly[wid][slot[u]]);
+      __syncwarp();   // s_lf / s_ly are refilled by the next tile
+    }
 #pragma unroll
     for (int u = 0; u < kItems; ++u) {
       const int j = tile + u * BLOCK + static_cast<int>(threadIdx.x);
@@ -232,7 +354,12 @@ __global__ void __launch_bounds__(BLOCK, kScanMinBlocks) k_scan(KArgs<Op> a) {
         s = pend && (!bucket || min_value<Op>(dd[u]) < tau);
         if (bucket && pend) dmin = min(dmin, static_cast<unsigned>(dd[u]));
       }
-      if (a.topq) s = pend && (a.keys ? a.keys[j] : priority_key<Op>(dd[u], vv[u])) >= key_thr;
+      if (a.topq) {
+        unsigned key;
+        if constexpr (kLearn) key = lkey[u];
+        else key = priority_key<Op>(dd[u], vv[u]);
+        s = pend && key >= key_thr;
+      }
       sel[u] = s;
     }
     int rb[kItems], re[kItems];

@@ -15,6 +15,15 @@
 
 namespace maiter {
 
+// u32 -> f32 without an I2F (B300 issues conversions on its narrow FP64
+// pipe), rounded to nearest like the conversion: each 16-bit half is exact
+// as (2^23 + half) - 2^23, and one fma joins them with a single rounding.
+__device__ __forceinline__ float u32_to_f32(unsigned x) {
+  const float hi = __uint_as_float(0x4B000000u | (x >> 16)) - 8388608.0f;
+  const float lo = __uint_as_float(0x4B000000u | (x & 0xFFFFu)) - 8388608.0f;
+  return fmaf(hi, 65536.0f, lo);
+}
+
 constexpr uint32_t kInfU32 = 0xFFFFFFFFu;
 
 // Vertex-update context shared by all operators.
@@ -167,6 +176,7 @@ struct OpMinU32 {
   static constexpr bool kIsMax = false;
   static constexpr uint32_t kNone = kInfU32;   // infinity: identity of min, nothing pending
   __device__ static __forceinline__ double value(uint32_t x) { return static_cast<double>(x); }
+  __device__ static __forceinline__ float fvalue(uint32_t x) { return u32_to_f32(x); }
 
   __device__ static __forceinline__ double priority(D d, V v) {
     return d < v ? static_cast<double>(v - d) : 0.0;
@@ -232,6 +242,7 @@ struct OpMinF32 {
   __device__ static __forceinline__ double value(uint32_t x) {
     return static_cast<double>(__uint_as_float(x));
   }
+  __device__ static __forceinline__ float fvalue(uint32_t x) { return __uint_as_float(x); }
 
   __device__ static __forceinline__ double priority(D d, V v) {
     return d < v ? value(v) - value(d) : 0.0;
@@ -288,6 +299,7 @@ struct OpMaxI32 {
   static constexpr bool kIsMax = true;
   static constexpr int32_t kNone = -1;   // identity of max over labels >= 0
   __device__ static __forceinline__ double value(int32_t x) { return static_cast<double>(x); }
+  __device__ static __forceinline__ float fvalue(int32_t x) { return static_cast<float>(x); }
 
   __device__ static __forceinline__ double priority(D d, V v) {
     return d > v ? static_cast<double>(d) - static_cast<double>(v) : 0.0;

@@ -96,7 +96,6 @@ struct maiter_result {
   unsigned large_cap = 0;              // n + m / kChunk + 1 entries
   maiter::DevCtl* ctl = nullptr;
   maiter::TopqCtl* topq = nullptr;     // top-fraction selection (allocated on first use)
-  unsigned* keys = nullptr;            // learned scheduling: per-vertex keys
   unsigned* last_act = nullptr;        // learned scheduling / traces: last update round
   maiter::DevCtl* h_ctl = nullptr;   // pinned mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -257,7 +257,6 @@ void maiter_result_destroy(maiter_result* r) {
   cudaFree(r->large_d);
   cudaFree(r->ctl);
   cudaFree(r->topq);
-  cudaFree(r->keys);
   cudaFree(r->last_act);
   cudaFree(r->bin_msg_v);
   cudaFree(r->bin_cmsg);
@@ -399,7 +398,6 @@ static maiter_status setup_plan(const maiter_graph* g, const maiter_run_params* 
     MAITER_CUDA(cudaMalloc(&r->topq, sizeof(TopqCtl)));
     MAITER_CUDA(cudaMemset(r->topq, 0, sizeof(TopqCtl)));
   }
-  if (learned && !r->keys) MAITER_CUDA(cudaMalloc(&r->keys, sizeof(unsigned) * (g->n > 0 ? g->n : 1)));
   if ((learned || track) && !r->last_act)
     MAITER_CUDA(cudaMalloc(&r->last_act, sizeof(unsigned) * (g->n > 0 ? g->n : 1)));
   if (learned || track) {
@@ -593,10 +591,10 @@ static maiter_status run_sync(const maiter_graph* g, const maiter_run_params* p,
   s.converged = h.status == 1;
   // every phase that ran ends with one scan that did not continue
   const int64_t phases = 1 + (h.phase > 0 ? 1 : 0);
-  // + 3 radix passes (TOPFRAC), + the scorer (LEARNED), + the hold that
-  // starts every round of the host-driven profiling loop
+  // + 3 radix passes (TOPFRAC), + the sampled threshold (LEARNED), + the
+  // hold that starts every round of the host-driven profiling loop
   const int per_round = ((p->sched == MAITER_SCHED_TOPFRAC) ? 5
-                         : (p->sched == MAITER_SCHED_LEARNED) ? 6 : 2) + (profile ? 1 : 0);
+                         : (p->sched == MAITER_SCHED_LEARNED) ? 3 : 2) + (profile ? 1 : 0);
   // graph mode runs whole passes of kRoundsPerPass rounds: the pass that
   // decides to stop completes its remaining rounds (which push nothing)
   constexpr int64_t kPass = Phase<OpSumF64>::kRoundsPerPass;

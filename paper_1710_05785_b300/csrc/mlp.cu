@@ -38,16 +38,29 @@ __global__ void k_mlp_round(const float* __restrict__ master, MlpWeights* w) {
 
 __global__ void k_mlp_forward(const MlpWeights* __restrict__ wg, const float* __restrict__ x,
                               int64_t n, float* __restrict__ out) {
-  __shared__ MlpWeights W;
-  for (int i = threadIdx.x; i < static_cast<int>(sizeof(MlpWeights) / 2); i += blockDim.x)
-    reinterpret_cast<unsigned short*>(&W)[i] = reinterpret_cast<const unsigned short*>(wg)[i];
+  // the scheduler's inference path: rows scored a warp (32 rows) at a time
+  // on the tensor cores
+  __shared__ MlpFrag W;
+  __shared__ uint4 s_rows[8][32];
+  __shared__ float s_out[8][32];
+  stage_mlp(wg, &W);
   __syncthreads();
-  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < n;
-       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    float f[kMlpIn];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t r0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + wid * 32; r0 < n; r0 += stride) {
+    const int64_t r = r0 + lane;
+    const int cnt = static_cast<int>(n - r0 < 32 ? n - r0 : 32);
+    if (r < n) {
+      float f[kMlpIn];
 #pragma unroll
-    for (int i = 0; i < kMlpIn; ++i) f[i] = bf16r(x[r * kMlpIn + i]);
-    out[r] = mlp_forward(W, f, nullptr);
+      for (int i = 0; i < kMlpIn; ++i) f[i] = bf16r(x[r * kMlpIn + i]);
+      s_rows[wid][lane] = pack_features(f);
+    }
+    __syncwarp();
+    warp_score(W, s_rows[wid], cnt, s_out[wid]);
+    __syncwarp();
+    if (r < n) out[r] = s_out[wid][lane];
+    __syncwarp();
   }
 }
 

@@ -40,17 +40,14 @@ template <class Op>
 struct Phase {
   KArgs<Op> a{};
   int push_grid = 1, scan_grid = 1, hist_grid = 1;
-  const MlpWeights* mlp = nullptr;    // LEARNED: scorer weights
-  const int* indeg = nullptr;         // LEARNED / traces: in-degrees
-  unsigned* keys = nullptr;           // LEARNED: key array written by k_score
+  bool learned = false;               // LEARNED: the scan scores (k_scan<.., true>)
 
   void setup(const maiter_graph* g, maiter_result* r, void* delta, const void* coef,
              double damping, const Tuning& tu, bool topq, const MlpWeights* scorer = nullptr,
              bool track = false) {
-    mlp = scorer;
-    indeg = g->indeg;
-    keys = scorer ? r->keys : nullptr;
-    a.keys = keys;
+    learned = scorer != nullptr;
+    a.mlp = scorer;
+    a.indeg = g->indeg;
     a.last_act = (scorer || track) ? r->last_act : nullptr;
     a.n = static_cast<int>(g->n);
     a.rp = g->rp;
@@ -73,8 +70,9 @@ struct Phase {
     a.cut_cta = tu.cut_cta;
     push_grid = grid_for(reinterpret_cast<const void*>(&k_push<Op, kBlock>), kBlock, g->num_sms,
                          tu.push_blocks_per_sm);
-    scan_grid = grid_for(reinterpret_cast<const void*>(&k_scan<Op, kBlock>), kBlock, g->num_sms,
-                         tu.scan_blocks_per_sm);
+    scan_grid = grid_for(learned ? reinterpret_cast<const void*>(&k_scan<Op, kBlock, true>)
+                                 : reinterpret_cast<const void*>(&k_scan<Op, kBlock>),
+                         kBlock, g->num_sms, tu.scan_blocks_per_sm);
     // Small graphs: one push CTA per kPushEdgesPerCta edges (at least one per
     // SM) instead of a full grid of CTAs that would only take the decision
     // and leave (PageRank on 65K edges: 1.49 -> 1.41 ms).
@@ -87,14 +85,33 @@ struct Phase {
     if (need < scan_grid) scan_grid = need > 0 ? need : 1;
   }
 
-  // TOPFRAC: the three radix-select passes that fix the round's key threshold.
-  void launch_select(cudaStream_t s) const {
+  // TOPFRAC: the three radix-select passes that fix the round's key threshold
+  // (exact); LEARNED: the sampled threshold (the scan scores every vertex),
+  // with `chained` a programmatic dependent of the push before it.
+  void launch_select(cudaStream_t s, bool chained = false) const {
     if (!a.topq) return;
     TopqCtl* tq = const_cast<TopqCtl*>(a.topq);
-    if (mlp) k_score<Op, kBlock><<<hist_grid, kBlock, 0, s>>>(a, mlp, indeg, keys);
+    if (learned) {
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(kLearnedBlocks);
+      cfg.blockDim = dim3(kLearnedBlock);
+      cfg.stream = s;
+      cfg.attrs = attr;
+      cfg.numAttrs = chained ? 1 : 0;
+      cudaLaunchKernelEx(&cfg, k_learned_threshold<Op>, a, tq);
+      return;
+    }
     k_topq_hist<Op, kBlock, 0><<<hist_grid, kBlock, 0, s>>>(a, tq);
     k_topq_hist<Op, kBlock, 1><<<hist_grid, kBlock, 0, s>>>(a, tq);
     k_topq_hist<Op, kBlock, 2><<<hist_grid, kBlock, 0, s>>>(a, tq);
+  }
+
+  void launch_scan(cudaStream_t s) const {
+    if (learned) k_scan<Op, kBlock, true><<<scan_grid, kBlock, 0, s>>>(a);
+    else k_scan<Op, kBlock><<<scan_grid, kBlock, 0, s>>>(a);
   }
 
   // One round: [selection passes], frontier scan, then the push, whose CTAs
@@ -104,7 +121,7 @@ struct Phase {
   // and wait in griddepcontrol.wait for the scan's writes.
   void launch_round(cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
                     bool chained) const {
-    launch_select(s);
+    launch_select(s, chained);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -113,11 +130,15 @@ struct Phase {
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (chained && !a.topq) {
+    if (learned) {
+      // after the threshold kernel, whose writes griddepcontrol.wait shows
+      cfg.gridDim = dim3(scan_grid);
+      cudaLaunchKernelEx(&cfg, k_scan<Op, kBlock, true>, a);
+    } else if (chained && !a.topq) {
       cfg.gridDim = dim3(scan_grid);
       cudaLaunchKernelEx(&cfg, k_scan<Op, kBlock>, a);
     } else {
-      k_scan<Op, kBlock><<<scan_grid, kBlock, 0, s>>>(a);
+      launch_scan(s);
     }
     cfg.gridDim = dim3(push_grid);
     cudaLaunchKernelEx(&cfg, k_push<Op, kBlock>, a, h, use_cond);
@@ -166,15 +187,15 @@ struct Phase {
       k_hold<<<1, 32, 0, st>>>(kHoldNs);
       MAITER_CUDA(cudaEventRecord(e[0], st));
       launch_select(st);
-      k_scan<Op, kBlock><<<scan_grid, kBlock, 0, st>>>(a);
+      launch_scan(st);
       MAITER_CUDA(cudaEventRecord(e[1], st));
       k_push<Op, kBlock><<<push_grid, kBlock, 0, st>>>(a, cudaGraphConditionalHandle{}, 0);
       MAITER_CUDA(cudaEventRecord(e[2], st));
       if (trace && trace->records < trace->max_records) {
         const int64_t o = static_cast<int64_t>(trace->records) * trace->ns;
         k_trace<Op><<<(trace->ns + 255) / 256, 256, 0, st>>>(
-            a, indeg, trace->sample, trace->ns, trace->feat + o * kMlpIn, trace->dl + o,
-            trace->vs + o, trace->la + o);
+            a, trace->sample, trace->ns, trace->feat + o * kMlpIn, trace->dl + o, trace->vs + o,
+            trace->la + o);
         ++trace->records;
       }
       MAITER_CUDA(cudaGetLastError());

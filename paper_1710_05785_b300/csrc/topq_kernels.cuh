@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(BLOCK) k_topq_hist(KArgs<Op> a, TopqCtl* tq) {
   unsigned long long npend = 0;
   for (int j = blockIdx.x * BLOCK + threadIdx.x; j < a.n; j += gridDim.x * BLOCK) {
     const typename Op::V vv = Op::kIsSum ? typename Op::V(0) : a.v[j];
-    const unsigned key = a.keys ? a.keys[j] : priority_key<Op>(a.delta[j], vv);
+    const unsigned key = priority_key<Op>(a.delta[j], vv);
     if (key == 0u) continue;
     if (PASS == 0) ++npend;
     if (PASS == 0 || (key >> kHigh) == prefix)

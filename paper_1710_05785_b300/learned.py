@@ -6,11 +6,15 @@ with top-fraction scheduling, the scorer's 8 input features of a sample of
 vertices, their deltas and the round of their last update.  Labels are
 hindsight facts of the same run:
 
-* sum ops (PageRank-style): log of the mass a vertex moves per message when
-  it is next updated, (1 - d [outdeg > 0]) |Delta_j at that update| n /
-  (outdeg_j + 1).  A high score means "this vertex's update will be cheap for
-  what it spreads": the scheduler updates those first and lets other deltas
-  accumulate.
+* sum ops (PageRank-style): log of the mass an update of the vertex in the
+  recorded round moves per message, (1 - d [outdeg > 0]) |Delta_j| n /
+  (outdeg_j + 1): the residual sum_k |Delta_k| falls by (1 - d) |Delta_j| (all
+  of it for a dangling vertex) and the update costs outdeg_j messages.  The
+  paper's priority |Delta_j| (Section 3.5) weighed by that cost; a high score
+  means "cheap for what it removes", so the scheduler updates those first and
+  lets the other deltas accumulate.  (Labelling with the mass moved at the
+  vertex's next update in the trace instead taught the network mostly its
+  degrees and scheduled worse.)
 * min (SSSP): 1 if the vertex's tentative distance Delta_j is already its
   final distance, else 0: updating a vertex whose distance will still drop
   sends messages that will be sent again.
@@ -25,30 +29,13 @@ import numpy as np
 INF32 = 0xFFFFFFFF
 
 
-def _next_update(last_update: np.ndarray) -> np.ndarray:
-    """nxt[r, s] = the first record r' >= r after whose push sample s was
-    updated (its last-update round changed between records r' and r' + 1),
-    or -1 if none within the trace."""
-    R, S = last_update.shape
-    nxt = np.full((R, S), -1, dtype=np.int64)
-    upd = np.zeros((R, S), dtype=bool)
-    upd[:-1] = last_update[1:] != last_update[:-1]
-    cur = np.full(S, -1, dtype=np.int64)
-    for r in range(R - 1, -1, -1):
-        cur = np.where(upd[r], r, cur)
-        nxt[r] = cur
-    return nxt
-
-
 def labels_sum(tr: dict, outdeg: np.ndarray, n: int, d: float):
-    """(X, y) for a sum-op trace (see module docstring)."""
+    """(X, y) for a sum-op trace (see module docstring): every record of a
+    sampled vertex with a non-zero delta."""
     feat, dl = tr["features"], tr["delta"]
-    nxt = _next_update(tr["last_update"])
-    R, S = dl.shape
-    rr, ss = np.nonzero((dl != 0.0) & (nxt >= 0))
-    r2 = nxt[rr, ss]
+    rr, ss = np.nonzero(dl != 0.0)
     deg = outdeg[ss].astype(np.float64)
-    mass = np.abs(dl[r2, ss]) * np.where(deg > 0, 1.0 - d, 1.0) * n / (deg + 1.0)
+    mass = np.abs(dl[rr, ss]) * np.where(deg > 0, 1.0 - d, 1.0) * n / (deg + 1.0)
     keep = mass > 0
     X = feat[rr[keep], ss[keep]].astype(np.float32)
     y = np.log10(mass[keep]).astype(np.float32)
