@@ -141,23 +141,23 @@ struct KArgs {
   DevCtl* ctl;
   const TopqCtl* topq;           // non-null: select key >= topq->key_thr (TOPFRAC, LEARNED)
   const MlpWeights* mlp;         // non-null (LEARNED): the scorer whose output is the key
-  const int* indeg;              // LEARNED / traces: in-degrees (a feature)
+  const uint2* lstat;            // LEARNED / traces: graph-static scorer features per vertex
   unsigned* last_act;            // non-null: round of each vertex's last update (1-based)
   int cut_warp;                  // deg <  cut_warp : small bucket
   int cut_cta;                   // deg >= cut_cta  : large bucket (chunked)
   int bucket;                    // min: distance-ordered selection (Delta_j < tau)
 };
 
-// What the scorer reads of vertex j: its delta and state, out-degree, round
-// of last update and in-degree.  Loaded apart from the arithmetic so that a
-// thread can have the loads of several vertices in flight at once.
+// What the scorer reads of vertex j: its delta and state, the round of its
+// last update and its graph-static features.  Loaded apart from the
+// arithmetic so that a thread can have the loads of several vertices in
+// flight at once.
 template <class Op>
 struct LearnIn {
   typename Op::D d;
   typename Op::V v;
-  int deg;
-  int indeg;
   unsigned la;
+  uint2 st;
 };
 
 template <class Op>
@@ -165,23 +165,25 @@ __device__ __forceinline__ LearnIn<Op> learn_in(const KArgs<Op>& a, int j) {
   LearnIn<Op> in;
   in.d = a.delta[j];
   in.v = a.v[j];
-  in.deg = __ldg(a.rp + j + 1) - __ldg(a.rp + j);
-  in.indeg = a.indeg[j];
   in.la = a.last_act ? a.last_act[j] : 0u;
+  in.st = a.lstat[j];
   return in;
 }
 
-// Scorer features (see vertex_features) of a vertex at round `round`.
+__device__ __forceinline__ unsigned age_of(unsigned la, unsigned round) {
+  return la ? round + 1u - la : round + 1u;
+}
+
+// The scorer's input row of a vertex at round `round` (see feature_row);
+// agef = age_feature(its age).
 template <class Op>
-__device__ __forceinline__ void features_of(const KArgs<Op>& a, const LearnIn<Op>& in,
-                                            unsigned round, float* f) {
-  const unsigned age = in.la ? round + 1u - in.la : round + 1u;
+__device__ __forceinline__ uint4 learn_row(const KArgs<Op>& a, const LearnIn<Op>& in, float agef) {
   const float n = u32_to_f32(static_cast<unsigned>(a.n));
   if constexpr (Op::kIsSum) {
-    vertex_features<true>(abs_f32(in.d), abs_f32(in.v), true, true, in.indeg, in.deg, age, n, f);
+    return feature_row<true>(abs_f32(in.d), abs_f32(in.v), true, true, in.st, agef, n);
   } else {
-    vertex_features<false>(Op::fvalue(in.d), Op::fvalue(in.v), in.d != Op::kNone,
-                           in.v != Op::kNone, in.indeg, in.deg, age, n, f);
+    return feature_row<false>(Op::fvalue(in.d), Op::fvalue(in.v), in.d != Op::kNone,
+                              in.v != Op::kNone, in.st, agef, n);
   }
 }
 
@@ -229,8 +231,10 @@ __global__ void __launch_bounds__(BLOCK, kLearn ? 3 : kScanMinBlocks) k_scan(KAr
   // the scorer's weights do not change during a run: staged before the wait
   // (unreferenced, so not allocated, without kLearn)
   __shared__ MlpFrag s_w[1];
+  __shared__ float s_agef[kLearn ? kMaxAge : 1];   // f4 of every age a scored vertex has
   if constexpr (kLearn) {
     stage_mlp(a.mlp, s_w);
+    if (threadIdx.x < kMaxAge) s_agef[threadIdx.x] = age_feature(threadIdx.x);
     __syncthreads();
   }
   // Launched as a programmatic dependent of the kernel before it: wait until
@@ -291,7 +295,8 @@ __global__ void __launch_bounds__(BLOCK, kLearn ? 3 : kScanMinBlocks) k_scan(KAr
       vv[u] = Op::kIsSum ? typename Op::V(0) : (in ? a.v[j] : typename Op::V(Op::kNone));
     }
     unsigned lkey[kItems];
-    if constexpr (kLearn) {
+    // threshold 1 (a round that selects every pending vertex): no scoring
+    if (kLearn && key_thr > 1u) {
       // the scorer's inputs of this thread's pending items (coalesced loads,
       // all in flight before any is used)
       bool pnd[kItems];
@@ -302,14 +307,12 @@ __global__ void __launch_bounds__(BLOCK, kLearn ? 3 : kScanMinBlocks) k_scan(KAr
         pnd[u] = j < a.n && Op::pending(dd[u], vv[u]);
         in[u].d = dd[u];
         in[u].v = vv[u];
-        in[u].deg = 0;
-        in[u].indeg = 0;
         in[u].la = 0u;
+        in[u].st = make_uint2(0u, 0u);
         if (pnd[u]) {
           if constexpr (Op::kIsSum) in[u].v = a.v[j];
-          in[u].deg = __ldg(a.rp + j + 1) - __ldg(a.rp + j);
-          in[u].indeg = a.indeg[j];
           in[u].la = a.last_act[j];
+          in[u].st = a.lstat[j];
         }
       }
       // rows of the warp's scored vertices, compacted (a sparse frontier
@@ -323,11 +326,8 @@ __global__ void __launch_bounds__(BLOCK, kLearn ? 3 : kScanMinBlocks) k_scan(KAr
         const bool sc = pnd[u] && !aged;
         const unsigned b = __ballot_sync(0xffffffffu, sc);
         slot[u] = sc ? static_cast<int>(cnt_w + __popc(b & lt)) : -1;
-        if (sc) {
-          float f[kMlpIn];
-          features_of(a, in[u], round, f);
-          s_lf[wid][slot[u]] = pack_features(f);
-        }
+        // a scored vertex is younger than kMaxAge: its f4 is in the table
+        if (sc) s_lf[wid][slot[u]] = learn_row(a, in[u], s_agef[age_of(in[u].la, round)]);
         lkey[u] = aged ? kAgedKey : 0u;
         cnt_w += __popc(b);
       }
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(BLOCK, kLearn ? 3 : kScanMinBlocks) k_scan(KAr
       }
       if (a.topq) {
         unsigned key;
-        if constexpr (kLearn) key = lkey[u];
+        if constexpr (kLearn) key = key_thr > 1u ? lkey[u] : 1u;
         else key = priority_key<Op>(dd[u], vv[u]);
         s = pend && key >= key_thr;
       }

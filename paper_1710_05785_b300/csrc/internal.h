@@ -71,7 +71,7 @@ struct maiter_graph {
   int* col = nullptr;          // m targets
   uint32_t* w = nullptr;       // m weights or null
   uint2* cw = nullptr;         // weighted graphs: (target, weight) per edge, one 8-byte load
-  int* indeg = nullptr;        // in-degrees (computed on first use by the learned scorer)
+  uint2* lstat = nullptr;      // graph-static scorer features (computed on first use)
   int wf32 = 0;                // w read as float: 0 unchecked, 1 finite and >= 0, 2 not
   int64_t* rp64 = nullptr;     // staging of the int64 offsets (kept after the first update)
   unsigned* flag = nullptr;    // validation flags (kept after the first update)

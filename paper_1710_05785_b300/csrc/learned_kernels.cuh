@@ -24,8 +24,13 @@ namespace maiter {
 // to finish finds the key ranked ceil(q x pending draws) from the top by a
 // four-pass radix select (8 bits a pass) and stores it as the threshold.
 // The scan then selects every pending vertex whose key is at least that.
-// When no draw hits a pending vertex the threshold is 1: every pending
-// vertex is selected, so every round makes progress.
+// When few draws hit a pending vertex (kLearnedMinPend) the threshold is 1:
+// every pending vertex is selected, so every round makes progress.
+// Rounds whose sample holds fewer pending draws than this (a frontier below
+// 1/16 of the vertices) select every pending vertex: a small frontier costs
+// little to push in full, and holding part of it back would only add rounds,
+// whose fixed cost is what the schedule must save.
+constexpr unsigned kLearnedMinPend = 256;
 constexpr int kLearnedBlock = 256;
 constexpr int kLearnedBlocks = kLearnedSample / kLearnedBlock;
 static_assert(kLearnedBlocks * kLearnedBlock == kLearnedSample, "one draw per thread");
@@ -71,11 +76,7 @@ __global__ void __launch_bounds__(kLearnedBlock) k_learned_threshold(KArgs<Op> a
   const bool sc = p && !aged;
   const unsigned b = __ballot_sync(0xffffffffu, sc);
   const int slot = __popc(b & ((1u << lane) - 1u));
-  if (sc) {
-    float f[kMlpIn];
-    features_of(a, in, round, f);
-    s_lf[wid][slot] = pack_features(f);
-  }
+  if (sc) s_lf[wid][slot] = learn_row(a, in, age_feature(age_of(in.la, round)));
   __syncwarp();
   warp_score(s_w, s_lf[wid], __popc(b), s_ly[wid]);
   __syncwarp();
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(kLearnedBlock) k_learned_threshold(KArgs<Op> a
   for (int t = 0; t < kLearnedSample / kLearnedBlock; ++t)
     kk[t] = __ldcg(tq->sample + t * kLearnedBlock + threadIdx.x);
   const unsigned P = atomicAdd(&tq->sample_pend, 0u);
-  if (P == 0u) {
+  if (P < kLearnedMinPend) {
     if (threadIdx.x == 0) {
       tq->key_thr = 1u;
       tq->sample_done = 0u;
@@ -167,7 +168,9 @@ __global__ void k_trace(KArgs<Op> a, const int* __restrict__ sample, int ns, flo
   const unsigned round = static_cast<unsigned>(a.ctl->rounds);
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
     const int j = sample[s];
-    features_of(a, learn_in(a, j), round, feat + static_cast<int64_t>(s) * kMlpIn);
+    const LearnIn<Op> in = learn_in(a, j);
+    unpack_row(learn_row(a, in, age_feature(age_of(in.la, round))),
+               feat + static_cast<int64_t>(s) * kMlpIn);
     dl[s] = static_cast<double>(a.delta[j]);
     vs[s] = static_cast<double>(a.v[j]);
     la[s] = a.last_act ? a.last_act[j] : 0u;
@@ -179,6 +182,13 @@ static __global__ void k_indegree(const int* __restrict__ col, int64_t m, int* _
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < m;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x)
     atomicAdd(indeg + col[e], 1);
+}
+
+// The graph-static scorer features of every vertex (static_features).
+static __global__ void k_learn_static(const int* __restrict__ rp, const int* __restrict__ indeg, int n,
+                                      uint2* __restrict__ st) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    st[j] = static_features(static_cast<unsigned>(indeg[j]), static_cast<unsigned>(rp[j + 1] - rp[j]));
 }
 
 }  // namespace maiter

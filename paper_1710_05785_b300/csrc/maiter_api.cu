@@ -123,7 +123,7 @@ void maiter_graph_destroy(maiter_graph* g) {
   cudaFree(g->cw);
   cudaFree(g->rp64);
   cudaFree(g->flag);
-  cudaFree(g->indeg);
+  cudaFree(g->lstat);
   free_bins(g);
   delete g;
 }
@@ -226,8 +226,8 @@ maiter_status maiter_graph_update(maiter_graph* g, const int64_t* row_ptr, const
   MAITER_CUDA(cudaMemcpyAsync(&h_flag, g->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   MAITER_CUDA(cudaStreamSynchronize(st));
   // contents changed: derived data is recomputed on its next use
-  cudaFree(g->indeg);
-  g->indeg = nullptr;
+  cudaFree(g->lstat);
+  g->lstat = nullptr;
   g->wf32 = 0;
   invalidate_bins(g);
   if (h_flag & 1u) {
@@ -376,15 +376,31 @@ static maiter_status check_float_weights(const maiter_graph* g) {
   return MAITER_OK;
 }
 
-// In-degrees of a graph (computed once, kept with the graph).
-static maiter_status ensure_indegree(const maiter_graph* g) {
-  if (g->indeg) return MAITER_OK;
+// The graph-static scorer features (from the in- and out-degrees), computed
+// once and kept with the graph.
+static maiter_status ensure_learn_static(const maiter_graph* g) {
+  if (g->lstat) return MAITER_OK;
   maiter_graph* mg = const_cast<maiter_graph*>(g);
-  MAITER_CUDA(cudaMalloc(&mg->indeg, sizeof(int) * (g->n > 0 ? g->n : 1)));
-  MAITER_CUDA(cudaMemset(mg->indeg, 0, sizeof(int) * (g->n > 0 ? g->n : 1)));
-  if (g->m > 0) k_indegree<<<g->num_sms * 4, 256>>>(g->col, g->m, mg->indeg);
-  MAITER_CUDA(cudaGetLastError());
-  MAITER_CUDA(cudaDeviceSynchronize());
+  const int64_t n1 = g->n > 0 ? g->n : 1;
+  int* indeg = nullptr;
+  MAITER_CUDA(cudaMalloc(&indeg, sizeof(int) * n1));
+  cudaError_t e = cudaMalloc(&mg->lstat, sizeof(uint2) * n1);
+  if (e == cudaSuccess) e = cudaMemset(indeg, 0, sizeof(int) * n1);
+  if (e == cudaSuccess && g->m > 0) {
+    k_indegree<<<g->num_sms * 4, 256>>>(g->col, g->m, indeg);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && g->n > 0) {
+    k_learn_static<<<g->num_sms * 4, 256>>>(g->rp, indeg, static_cast<int>(g->n), mg->lstat);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(indeg);
+  if (e != cudaSuccess) {
+    cudaFree(mg->lstat);
+    mg->lstat = nullptr;
+  }
+  MAITER_CUDA(e);
   return MAITER_OK;
 }
 
@@ -401,7 +417,7 @@ static maiter_status setup_plan(const maiter_graph* g, const maiter_run_params* 
   if ((learned || track) && !r->last_act)
     MAITER_CUDA(cudaMalloc(&r->last_act, sizeof(unsigned) * (g->n > 0 ? g->n : 1)));
   if (learned || track) {
-    maiter_status s = ensure_indegree(g);
+    maiter_status s = ensure_learn_static(g);
     if (s != MAITER_OK) return s;
   }
   const MlpWeights* W = learned ? mlp_device_weights(p->scorer) : nullptr;

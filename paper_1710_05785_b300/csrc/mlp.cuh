@@ -15,7 +15,7 @@
 //   f3 log1p(outdeg_j)                              same
 //   f4 log1p(r - last activation round)             same (never activated: r + 1)
 //   f5 1                                            1 if Delta_j finite
-//   f6 ln(|Delta_j| n / (outdeg_j + 1)) / 16        1 if v_j finite
+//   f6 (ln(|Delta_j| n) - log1p(outdeg_j)) / 16     1 if v_j finite
 //   f7 0                                            0
 #pragma once
 #include <cstddef>
@@ -72,31 +72,54 @@ __device__ __forceinline__ float abs_f64_to_f32(double x) {
 __device__ __forceinline__ float abs_f32(float x) { return fabsf(x); }
 __device__ __forceinline__ float abs_f32(double x) { return abs_f64_to_f32(x); }
 
-__device__ __forceinline__ float log_feature(float x) { return __logf(fmaxf(x, kFeatFloor)) * kFeatScale; }
 __device__ __forceinline__ float log1p_feature(float x) { return __logf(1.0f + x); }
 
+// The BF16 bits (low 16) of x rounded to the nearest BF16.
+__device__ __forceinline__ unsigned bf16_bits(float x) { return __float_as_uint(bf16r(x)) >> 16; }
+
+// A vertex's features as one scorer input row: 8 BF16 values, f[2t] in the
+// low half of word t.  The graph-static part comes precomputed per vertex
+// (static_features): word 1 is (f2, f3), and the FP32 log(1 + outdeg) from
+// which f6 = (ln(|Delta| n) - log(1 + outdeg)) / 16 is formed.  agef is
+// f4 = log1p(age) (age_feature).  delta and v are magnitudes for +.
+__device__ __forceinline__ uint2 static_features(unsigned indeg, unsigned outdeg) {
+  const float l_out = log1p_feature(u32_to_f32(outdeg));
+  const unsigned w = bf16_bits(log1p_feature(u32_to_f32(indeg))) | (bf16_bits(l_out) << 16);
+  return make_uint2(w, __float_as_uint(l_out));
+}
+
+__device__ __forceinline__ float age_feature(unsigned age) { return bf16r(log1p_feature(u32_to_f32(age))); }
+
+constexpr unsigned kBf16One = 0x3F80u;
+
 template <bool kIsSum>
-__device__ __forceinline__ void vertex_features(float delta, float v, bool d_finite, bool v_finite,
-                                                int indeg, int outdeg, unsigned age, float n,
-                                                float* f) {
+__device__ __forceinline__ uint4 feature_row(float delta, float v, bool d_finite, bool v_finite,
+                                             uint2 st, float agef, float n) {
+  unsigned w0, w2, w3;
   if (kIsSum) {
-    const float ad = delta * n;   // delta and v: magnitudes
-    f[0] = log_feature(ad);
-    f[1] = log_feature(v * n);
-    f[5] = 1.0f;
-    f[6] = log_feature(ad / (u32_to_f32(static_cast<unsigned>(outdeg)) + 1.0f));
+    const float l0 = __logf(fmaxf(delta * n, kFeatFloor));
+    const float l1 = __logf(fmaxf(v * n, kFeatFloor));
+    w0 = bf16_bits(l0 * kFeatScale) | (bf16_bits(l1 * kFeatScale) << 16);
+    w2 = bf16_bits(agef) | (kBf16One << 16);
+    w3 = bf16_bits((l0 - __uint_as_float(st.y)) * kFeatScale);
   } else {
-    f[0] = d_finite ? log1p_feature(delta) : 0.0f;
-    f[1] = v_finite ? log1p_feature(v) : 0.0f;
-    f[5] = d_finite ? 1.0f : 0.0f;
-    f[6] = v_finite ? 1.0f : 0.0f;
+    const unsigned f0 = d_finite ? bf16_bits(log1p_feature(delta)) : 0u;
+    const unsigned f1 = v_finite ? bf16_bits(log1p_feature(v)) : 0u;
+    w0 = f0 | (f1 << 16);
+    w2 = bf16_bits(agef) | ((d_finite ? kBf16One : 0u) << 16);
+    w3 = v_finite ? kBf16One : 0u;
   }
-  f[2] = log1p_feature(u32_to_f32(static_cast<unsigned>(indeg)));
-  f[3] = log1p_feature(u32_to_f32(static_cast<unsigned>(outdeg)));
-  f[4] = log1p_feature(u32_to_f32(age));
-  f[7] = 0.0f;
+  return make_uint4(w0, st.x, w2, w3);
+}
+
+// The row's 8 features as FP32 values.
+__device__ __forceinline__ void unpack_row(uint4 r, float* f) {
+  const unsigned w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
-  for (int i = 0; i < kMlpIn; ++i) f[i] = bf16r(f[i]);   // BF16 inputs
+  for (int t = 0; t < 4; ++t) {
+    f[2 * t] = __uint_as_float(w[t] << 16);
+    f[2 * t + 1] = __uint_as_float(w[t] & 0xFFFF0000u);
+  }
 }
 
 static_assert(sizeof(MlpWeights) >= kMlpParams * 2 && offsetof(MlpWeights, b2) == (kMlpParams - 1) * 2,

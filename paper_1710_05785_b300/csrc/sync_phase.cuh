@@ -47,7 +47,7 @@ struct Phase {
              bool track = false) {
     learned = scorer != nullptr;
     a.mlp = scorer;
-    a.indeg = g->indeg;
+    a.lstat = g->lstat;
     a.last_act = (scorer || track) ? r->last_act : nullptr;
     a.n = static_cast<int>(g->n);
     a.rp = g->rp;
