@@ -133,7 +133,7 @@ typedef enum {
                                  reduction tests termination and re-seeds the queue
                                  (the periodic check of Section 5.1).  SUM_F64 and
                                  MIN_U32; schedules ALL and THRESHOLD. */
-  MAITER_ENGINE_BINNED = 2    /* rounds in which every vertex with a pending delta
+  MAITER_ENGINE_BINNED = 2,   /* rounds in which every vertex with a pending delta
                                  sends (the synchronous DAIC of Section 3.2, schedule
                                  ALL), for SUM_F64 / SUM_MIXED with g = SCALE_BY_SRC.
                                  The messages of a round are written to bins of
@@ -145,6 +145,17 @@ typedef enum {
                                  about 4 bytes per edge for the layout plus 8 per
                                  edge for the messages of a result.  The loop and its
                                  termination test run on the device as for SYNC. */
+  MAITER_ENGINE_PULL = 3      /* the same dense rounds (schedule ALL, SUM_F64 /
+                                 SUM_MIXED, g = SCALE_BY_SRC) with the receive step
+                                 of Eq. 5 computed at the receivers: every vertex
+                                 sums the messages c_j Delta_j of its in-neighbours
+                                 over the transpose of the graph (built by the
+                                 library on first use and after maiter_graph_update:
+                                 4 bytes per edge + 4 per vertex), then folds.  No
+                                 atomic per edge; one per 1024 in-edges of a vertex
+                                 with more than 256.  Memory per result: two n x 8
+                                 byte message buffers.  The loop and its termination
+                                 test run on the device as for SYNC. */
 } maiter_engine;
 
 /* Run flags (bit set). */

@@ -34,7 +34,7 @@ OP_SUM_F64, OP_SUM_MIXED, OP_MIN_U32, OP_MIN_F32, OP_MAX_I32 = 0, 1, 2, 3, 4
 G_SCALE_BY_SRC, G_ADD_EDGE, G_SCALE_BY_EDGE, G_IDENTITY = 0, 1, 2, 3
 SCHED_ALL, SCHED_THRESHOLD, SCHED_TOPFRAC, SCHED_LEARNED, SCHED_BUCKET = 0, 1, 2, 3, 4
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 8, 64, 641
-ENGINE_SYNC, ENGINE_ASYNC, ENGINE_BINNED = 0, 1, 2
+ENGINE_SYNC, ENGINE_ASYNC, ENGINE_BINNED, ENGINE_PULL = 0, 1, 2, 3
 FLAG_PROFILE_KERNELS, FLAG_INJECT_STALL = 1, 2
 # maiter_batch_params.mode
 BATCH_DENSE, BATCH_SPARSE, BATCH_DENSE_CHAINED = 0, 1, 2

@@ -571,7 +571,7 @@ constexpr int kSortBlock = 256;
 // segment, bitonic in shared memory; padding slots go last.  Segments longer
 // than kSortMax are left as placed: the gather is correct on any order, the
 // sort only lets it combine messages to the same receiver.
-__global__ void __launch_bounds__(kSortBlock) k_bin_sort(const int* __restrict__ T, int nchunks,
+static __global__ void __launch_bounds__(kSortBlock) k_bin_sort(const int* __restrict__ T, int nchunks,
                                                          int nbins,
                                                          unsigned short* __restrict__ src_local,
                                                          unsigned short* __restrict__ dst_local) {

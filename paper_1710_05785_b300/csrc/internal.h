@@ -62,6 +62,7 @@ struct Tuning {
 
 namespace maiter {
 struct BinLayout;   // binned engine: the edges by (sender cell, receiver bin)
+struct PullLayout;  // receive-side engine: the transpose and its chunk list
 }
 
 struct maiter_graph {
@@ -78,6 +79,7 @@ struct maiter_graph {
   bool invalid = false;        // the last update failed validation: no runs
   int num_sms = 0;
   maiter::BinLayout* bins = nullptr;   // binned engine layout (built on first use)
+  maiter::PullLayout* pull = nullptr;  // receive-side engine layout (built on first use)
 };
 
 struct maiter_result {
@@ -117,6 +119,7 @@ struct maiter_result {
   void* bin_cmsg = nullptr;            // n coefficients c_j (8 bytes each)
   void* bin_msg_e = nullptr;           // one message per padded edge slot (8 bytes each)
   size_t bin_msg_e_cap = 0;
+  void* pull_msg = nullptr;            // receive-side engine: the second message buffer (n x 8 bytes)
   maiter_stats stats{};
 };
 
@@ -136,4 +139,10 @@ maiter_status run_binned(const maiter_graph* g, const maiter_run_params* p, mait
                          cudaStream_t st);
 void free_bins(maiter_graph* g);
 void invalidate_bins(maiter_graph* g);
+// Receive-side engine (pull_engine.cu): dense rounds of + summed at the
+// receivers over the transpose; v and Delta are initialised.
+maiter_status run_pull(const maiter_graph* g, const maiter_run_params* p, maiter_result* r,
+                       cudaStream_t st);
+void free_pull(maiter_graph* g);
+void invalidate_pull(maiter_graph* g);
 }  // namespace maiter

@@ -125,6 +125,7 @@ void maiter_graph_destroy(maiter_graph* g) {
   cudaFree(g->flag);
   cudaFree(g->lstat);
   free_bins(g);
+  free_pull(g);
   delete g;
 }
 
@@ -230,6 +231,7 @@ maiter_status maiter_graph_update(maiter_graph* g, const int64_t* row_ptr, const
   g->lstat = nullptr;
   g->wf32 = 0;
   invalidate_bins(g);
+  invalidate_pull(g);
   if (h_flag & 1u) {
     set_error("row_ptr must start at 0, be non-decreasing and end at m = %lld", (long long)m);
     return MAITER_ERR_INVALID_ARG;
@@ -261,6 +263,7 @@ void maiter_result_destroy(maiter_result* r) {
   cudaFree(r->bin_msg_v);
   cudaFree(r->bin_cmsg);
   cudaFree(r->bin_msg_e);
+  cudaFree(r->pull_msg);
   free_async(r);
   if (r->h_ctl) cudaFreeHost(r->h_ctl);
   if (r->ev0) cudaEventDestroy(r->ev0);
@@ -740,6 +743,7 @@ static maiter_status run_op(const maiter_graph* g, const maiter_run_params* p, m
   }
   s = (p->engine == MAITER_ENGINE_ASYNC)    ? run_async(g, p, r, st)
       : (p->engine == MAITER_ENGINE_BINNED) ? run_binned(g, p, r, st)
+      : (p->engine == MAITER_ENGINE_PULL)   ? run_pull(g, p, r, st)
                                             : run_sync(g, p, r, st, trace);
   r->stats.kernel_launches += init_launches;
   return s;
@@ -787,12 +791,13 @@ static maiter_status run_impl(const maiter_graph* g, const maiter_run_params* p,
     MAITER_REQUIRE(p->top_frac > 0.0 && p->top_frac <= 1.0, "top_frac must lie in (0, 1]");
   }
   MAITER_REQUIRE(p->engine == MAITER_ENGINE_SYNC || p->engine == MAITER_ENGINE_ASYNC ||
-                     p->engine == MAITER_ENGINE_BINNED,
+                     p->engine == MAITER_ENGINE_BINNED || p->engine == MAITER_ENGINE_PULL,
                  "unknown engine %d", p->engine);
-  if (p->engine == MAITER_ENGINE_BINNED &&
+  if ((p->engine == MAITER_ENGINE_BINNED || p->engine == MAITER_ENGINE_PULL) &&
       (!is_sum || p->g != MAITER_G_SCALE_BY_SRC || p->sched != MAITER_SCHED_ALL || trace ||
        (p->flags & MAITER_FLAG_INJECT_STALL))) {
-    set_error("the binned engine runs sums with g = SCALE_BY_SRC and schedule ALL");
+    set_error("the binned and receive-side engines run sums with g = SCALE_BY_SRC and "
+              "schedule ALL");
     return MAITER_ERR_UNSUPPORTED;
   }
   MAITER_REQUIRE(p->timeout_ms >= 0, "timeout_ms must be >= 0");

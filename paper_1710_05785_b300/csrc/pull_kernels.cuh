@@ -1,0 +1,270 @@
+// Receive-side engine for dense rounds of (+) with g_{j,k}(x) = c_j x
+// (PageRank, personalised PageRank, Katz): in a round of the synchronous
+// DAIC (Section 3.2) in which every vertex with a pending delta sends, the
+// receive step of Eq. 5, Delta_k <- Delta_k + sum of the messages that
+// reached k, is computed at the receiver: k reads the messages c_j Delta_j
+// of its in-neighbours j through the transpose of the graph and sums them in
+// registers.  No edge needs an atomic; per edge the round reads one source
+// index (streamed) and one message (a random read of an n-entry array that
+// stays in L2 for FP32 messages up to 2^25 vertices).
+//
+// Static layout (pull_engine.cu, once per graph content):
+//   crp, csrc - the transpose in CSR form: the senders of every receiver;
+//   receivers in groups of 32 consecutive vertices, one warp each: the
+//     in-edges of a group's rows are contiguous and each carries its row
+//     within the group (one byte), so every lane takes one edge per step and
+//     a segmented shuffle reduction sums each row's part of the step; rows
+//     with more than kPullCut in-edges keep their edges in a tail region
+//     after all the others and are
+//   cut into chunks of kPullChunk edges, one warp each: the warp's sum goes
+//     to an FP64 accumulator of the row by one atomic, and the warp that adds
+//     the row's last chunk folds the row.
+// A round is two kernels: k_pull_decide (one thread: the termination test of
+// Section 5.1 on the totals of the round before, shared with the binned
+// engine) and k_pull (sum, then fold: v_k <- v_k + Delta_k, Delta_k <- sum,
+// message c_k Delta_k for the next round, and the totals of the new deltas).
+// Messages alternate between two buffers by the control block's set: a round
+// reads msg[ws ^ 1] and writes msg[ws].
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "binned_kernels.cuh"
+
+namespace maiter {
+
+constexpr int kPullBlock = 256;
+constexpr int kPullCut = 256;       // in-edges of the largest row a group sums
+constexpr int kPullChunk = 1024;    // in-edges per chunk of a larger row
+constexpr int kPullSteps = 4;       // 32-edge steps of a group whose loads are issued together
+
+struct PullArgs {
+  int n;
+  int ngroups;                            // ceil(n / 32)
+  int nlarge;                             // chunk entries of the large rows
+  const int* __restrict__ rp;             // out-edge offsets (out-degrees)
+  const int* __restrict__ crp;            // n + 1: in-edge offsets of the small rows (a
+                                          // large row has none here: its edges are in
+                                          // the tail, reached through its chunks)
+  const int* __restrict__ csrc;           // m: sender of every in-edge
+  const unsigned char* __restrict__ crow; // m: row of every small-row in-edge within its
+                                          // group of 32 (k mod 32)
+  const unsigned* __restrict__ lbits;     // ceil(n / 32): bit k mod 32 of word k / 32 set
+                                          // when row k is large
+  const int4* __restrict__ large;         // {row, first edge, end edge, large row index}
+  const int* __restrict__ large_nch;      // chunks of every large row
+  double* lacc;                           // FP64 sum of every large row (zero between rounds)
+  unsigned* lcnt;                         // chunks of every large row added this round
+  const void* coef;                       // per-source c_j (CT), or null: damping / outdeg
+  double damping;
+  double* v;                              // FP64 state
+  void* delta;                            // DT[n]
+  void* msg[2];                           // MT[n] each: c_j Delta_j, alternating by set
+  void* cmsg;                             // MT[n]: c_j in the message precision (prime)
+  DevCtl* ctl;
+};
+
+// Primes a phase: msg[ws][j] = c_j Delta_j and the totals of Delta into set
+// ws (as k_bin_prime, with the message buffer of the set).
+template <class DT, class MT, class CT>
+__global__ void __launch_bounds__(256) k_pull_prime(PullArgs a, const double* __restrict__ wide,
+                                                    cudaGraphConditionalHandle cond,
+                                                    int use_cond) {
+  DevCtl* ctl = a.ctl;
+  const unsigned ws = ctl->scan_set;
+  DT* delta = static_cast<DT*>(a.delta);
+  MT* msg = static_cast<MT*>(a.msg[ws]);
+  MT* cmsg = static_cast<MT*>(a.cmsg);
+  double resid = 0.0, mass = 0.0;
+  unsigned long long act = 0, push = 0;
+  for (int j = blockIdx.x * 256 + threadIdx.x; j < a.n; j += gridDim.x * 256) {
+    DT d;
+    if (wide) {
+      d = static_cast<DT>(wide[j]);
+      delta[j] = d;
+    } else {
+      d = delta[j];
+    }
+    const int deg = __ldg(a.rp + j + 1) - __ldg(a.rp + j);
+    double c = 0.0;
+    if (deg > 0)
+      c = a.coef ? static_cast<double>(static_cast<const CT*>(a.coef)[j])
+                 : a.damping / static_cast<double>(deg);
+    const MT cj = static_cast<MT>(c);
+    cmsg[j] = cj;
+    const MT m = (d != DT(0)) ? cj * static_cast<MT>(d) : MT(0);
+    msg[j] = m;
+    resid += fabs(static_cast<double>(d));
+    mass += static_cast<double>(deg) * fabs(static_cast<double>(m));
+    act += (d != DT(0));
+    push += (d != DT(0)) ? static_cast<unsigned long long>(deg) : 0ull;
+  }
+  bin_block_totals<256>(ctl, ws, resid, act, push, mass);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->push_set = ws;
+    if (wide) {
+      const int st = ctl->status;
+      ctl->status = (st == 1) ? 0 : st;
+      ctl->phase = (st == 1) ? 1 : 0;
+      ctl->warm_rounds = ctl->rounds;
+      ctl->warm_activations = ctl->activations;
+      ctl->warm_pushes = ctl->pushes;
+      ctl->switch_frac = 0.0;
+      ctl->rounds_in[ws] = ctl->rounds;
+      ctl->eps_in[ws] = ctl->eps;
+      if (use_cond) cudaGraphSetConditional(cond, st == 1 ? 1u : 0u);
+    }
+  }
+}
+
+// The round's termination decision (one thread), then the WHILE condition.
+static __global__ void k_pull_decide(DevCtl* ctl, cudaGraphConditionalHandle cond, int use_cond) {
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
+  if (threadIdx.x == 0) bin_decide(ctl, cond, use_cond);
+}
+
+// Fold of receiver k with its new delta: v_k += Delta_k (old), Delta_k =
+// sum, its message for the next round, and its share of the totals.
+template <class DT, class MT>
+__device__ __forceinline__ void pull_fold(const PullArgs& a, MT* msg_out, int k, double sum,
+                                          double& resid, double& mass, unsigned long long& act,
+                                          unsigned long long& push) {
+  DT* delta = static_cast<DT*>(a.delta);
+  const DT dnew = static_cast<DT>(sum);
+  const DT dold = delta[k];
+  if (dold != DT(0)) a.v[k] += static_cast<double>(dold);
+  delta[k] = dnew;
+  const int deg = __ldg(a.rp + k + 1) - __ldg(a.rp + k);
+  const MT m = (dnew != DT(0)) ? __ldg(static_cast<const MT*>(a.cmsg) + k) * static_cast<MT>(dnew)
+                               : MT(0);
+  msg_out[k] = m;
+  resid += fabs(static_cast<double>(dnew));
+  mass += static_cast<double>(deg) * fabs(static_cast<double>(m));
+  act += (dnew != DT(0));
+  push += (dnew != DT(0)) ? static_cast<unsigned long long>(deg) : 0ull;
+}
+
+// One dense round: the large rows' chunks, then the groups of 32 rows, a
+// warp each (no block barrier).  Sums in the message precision within a
+// step, in MT per row across steps (FP64 across the large rows' chunks).
+template <class DT, class MT>
+__global__ void __launch_bounds__(kPullBlock) k_pull(PullArgs a) {
+  cudaGridDependencySynchronize();
+  cudaTriggerProgrammaticLaunchCompletion();
+  DevCtl* ctl = a.ctl;
+  if (ctl->status != 0) return;   // the decision stopped the run
+  const unsigned ws = ctl->scan_set;
+  const MT* __restrict__ msg_in = static_cast<const MT*>(a.msg[ws ^ 1u]);
+  MT* msg_out = static_cast<MT*>(a.msg[ws]);
+  double resid = 0.0, mass = 0.0;
+  unsigned long long act = 0, push = 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ MT s_row[kPullBlock / 32][32];   // a group's row sums, one warp each
+  const int gw = blockIdx.x * (kPullBlock / 32) + wid;
+  const int nw = gridDim.x * (kPullBlock / 32);
+
+  // large rows: a warp per chunk, the chunk's sum added to the row's FP64
+  // accumulator by one atomic; the warp that adds the last chunk folds the row
+  for (int c = gw; c < a.nlarge; c += nw) {
+    const int4 ent = __ldg(a.large + c);
+    MT x[4] = {MT(0), MT(0), MT(0), MT(0)};
+    for (int e = ent.y + lane; e < ent.z; e += 128) {
+      int src[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) src[u] = e + 32 * u < ent.z ? __ldg(a.csrc + e + 32 * u) : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) if (src[u] >= 0) x[u] += msg_in[src[u]];
+    }
+    double t = static_cast<double>(x[0]) + static_cast<double>(x[1]) +
+               static_cast<double>(x[2]) + static_cast<double>(x[3]);
+    t = warp_sum(t);
+    int last = 0;
+    if (lane == 0) {
+      atomicAdd(a.lacc + ent.w, t);
+      __threadfence();
+      last = atomicAdd(a.lcnt + ent.w, 1u) == static_cast<unsigned>(__ldg(a.large_nch + ent.w)) - 1u;
+      if (last) {
+        __threadfence();
+        const double sum = __longlong_as_double(static_cast<long long>(
+            atomicExch(reinterpret_cast<unsigned long long*>(a.lacc + ent.w), 0ull)));
+        a.lcnt[ent.w] = 0u;
+        pull_fold<DT, MT>(a, msg_out, ent.x, sum, resid, mass, act, push);
+      }
+    }
+  }
+
+  // groups of 32 rows, one warp each: the small rows' in-edges of a group
+  // are contiguous, each tagged with its row
+  for (int gi = gw; gi < a.ngroups; gi += nw) {
+    const int k = gi * 32 + lane;
+    const int gb = __ldg(a.crp + gi * 32);
+    const int ge = __ldg(a.crp + min(gi * 32 + 32, a.n));
+    s_row[wid][lane] = MT(0);
+    __syncwarp();
+    // kPullSteps steps of 32 edges at a time: their loads in flight together
+    for (int e0 = gb; e0 < ge; e0 += 32 * kPullSteps) {
+      int r[kPullSteps];
+      MT x[kPullSteps];
+      int src[kPullSteps];
+#pragma unroll
+      for (int h = 0; h < kPullSteps; ++h) {
+        const int e = e0 + 32 * h + lane;
+        src[h] = e < ge ? __ldg(a.csrc + e) : -1;
+        r[h] = e < ge ? static_cast<int>(__ldg(a.crow + e)) : 32;   // past the end: a key of its own
+      }
+#pragma unroll
+      for (int h = 0; h < kPullSteps; ++h) x[h] = src[h] >= 0 ? msg_in[src[h]] : MT(0);
+#pragma unroll
+      for (int h = 0; h < kPullSteps; ++h) {
+        // segmented suffix sums over runs of equal r (runs are contiguous)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const MT y = __shfl_down_sync(0xffffffffu, x[h], o);
+          const int ry = __shfl_down_sync(0xffffffffu, r[h], o);
+          if (lane + o < 32 && ry == r[h]) x[h] += y;
+        }
+        // the first lane of each run adds the run's sum to its row (a row
+        // has one run per step: no two lanes add to a row at once)
+        const int rprev = __shfl_up_sync(0xffffffffu, r[h], 1);
+        if (r[h] < 32 && (lane == 0 || rprev != r[h])) s_row[wid][r[h]] += x[h];
+        __syncwarp();
+      }
+    }
+    const MT acc = s_row[wid][lane];
+    __syncwarp();   // s_row is reset by the warp's next group
+    const bool large = (__ldg(a.lbits + gi) >> lane) & 1u;
+    if (k < a.n && !large)
+      pull_fold<DT, MT>(a, msg_out, k, static_cast<double>(acc), resid, mass, act, push);
+  }
+  bin_block_totals<kPullBlock>(ctl, ws, resid, act, push, mass);
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->push_set = ws;
+}
+
+// ---------------------------------------------------------- layout build
+
+// In-degree of every vertex (cnt zeroed by the caller).
+static __global__ void k_pull_indegree(const int* __restrict__ col, int64_t m, int* __restrict__ cnt) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < m;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    atomicAdd(cnt + __ldg(col + e), 1);
+}
+
+// In-edge placement: csrc[cursor[k]++] = j for every edge j -> k (cursor
+// starts at row k's first slot, in the small-row region or in the tail), and
+// the slot's row within its group.
+static __global__ void k_pull_place(const int* __restrict__ rp, const int* __restrict__ col, int n,
+                                    int* __restrict__ cursor, int* __restrict__ csrc,
+                                    unsigned char* __restrict__ crow) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const int e1 = __ldg(rp + j + 1);
+    for (int e = __ldg(rp + j); e < e1; ++e) {
+      const int k = __ldg(col + e);
+      const int pos = atomicAdd(cursor + k, 1);
+      csrc[pos] = j;
+      crow[pos] = static_cast<unsigned char>(k & 31);
+    }
+  }
+}
+
+}  // namespace maiter
