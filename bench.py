@@ -343,9 +343,10 @@ def pagerank_config(wl, cfg, g, world):
 def run_pagerank(args, wl, dist=None, nested=None):
     """PageRank workloads: one step = one run from v0 = 0, Delta1 = 1 - d to
     sum |Delta| < eps; value = m / time-to-tolerance (GTEPS per solution).
-    The headline engine is the binned one (mixed precision at scale 24);
-    beside it the plain form (FP64 round engine), the round engine in mixed
-    precision and top-q scheduling."""
+    The headline at scale 24 is the receive-side engine with FP32 deltas and
+    messages (FP64 state and residual); beside it the plain form (FP64 round
+    engine), the round engine in mixed precision, the receive-side engine in
+    the other precisions, the binned engine and top-q scheduling."""
     import torch
     import paper_1710_05785_b300 as mt
 
@@ -361,18 +362,24 @@ def run_pagerank(args, wl, dist=None, nested=None):
     G = mt.Graph(torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col).to(dev), device=local)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     eps = cfg["eps"]
-    # the headline: the round engine (frontier scan + push with L2 atomics,
-    # messages propagating within a round); beside it the plain form (FP64),
-    # the binned engine (no L2 atomic per edge, exact per-bin sums) and top-q
-    head = "mixed_sync" if mixed else "plain_f64_sync"
+    # the headline: the receive-side engine (every receiver sums its
+    # in-messages over the transpose: no atomic per edge) with FP32 deltas
+    # and messages from the first round (no delta accumulates under atomics,
+    # so no FP64 warm-up is needed); beside it the plain form (FP64), the
+    # round engine (frontier scan + push with L2 atomics) in mixed precision,
+    # the binned engine and top-q
+    head = "pull_f32" if mixed else "plain_f64_sync"
     variants = {
+        "pull_f32": dict(op=mt.OP_SUM_MIXED, engine=mt.ENGINE_PULL, mixed_switch=1.0),
         "mixed_sync": dict(op=mt.OP_SUM_MIXED),
         "plain_f64_sync": dict(op=mt.OP_SUM_F64),
-        "binned_mixed": dict(op=mt.OP_SUM_MIXED, engine=mt.ENGINE_BINNED),
+        "pull_mixed": dict(op=mt.OP_SUM_MIXED, engine=mt.ENGINE_PULL),
+        "pull_f64": dict(op=mt.OP_SUM_F64, engine=mt.ENGINE_PULL),
         "binned_f32": dict(op=mt.OP_SUM_MIXED, engine=mt.ENGINE_BINNED, mixed_switch=1.0),
-        "binned_f64": dict(op=mt.OP_SUM_F64, engine=mt.ENGINE_BINNED),
         "f64_topq10_sync": dict(op=mt.OP_SUM_F64, sched=mt.SCHED_TOPFRAC, top_frac=0.1),
     }
+    if not mixed:
+        del variants["pull_f32"]
     if cfg["scale"] < 20:
         variants["f64_async"] = dict(op=mt.OP_SUM_F64, engine=mt.ENGINE_ASYNC)
     if args.head_only:
@@ -453,36 +460,56 @@ def run_pagerank(args, wl, dist=None, nested=None):
                                f"{results[name]['error_bound']:.3g}")
     bound = results[head]["error_bound"]
     # kernel-level roofline: the headline run again with per-kernel events
-    prof = mt.run(G, eps=eps, damping=D_PR, stream=stream.cuda_stream,
-                  flags=mt.FLAG_PROFILE_KERNELS, **variants[head]).stats()
-    alg = pagerank_alg_bytes(prof, mixed)
     peaks, peak_kind = measured_peaks()
-    launches = max(prof["push_launches"], 1)
-    achieved = alg / (prof["push_ms"] * 1e-3) / 1e9
-    traffic = None
+    traffic_tab = {}
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get(f"k_push_pagerank_mixed_rmat{cfg['scale']}")
+            traffic_tab = json.load(f)
     except (OSError, ValueError):
         pass
-    roofline = {"bound": "hbm", "kernel": "k_push<OpSumMixed> (warm-up rounds k_push<OpSumWarm>)"
-                if mixed else "k_push<OpSumF64>",
-                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "peak_kind": f"{peak_kind} copy bandwidth",
-                "push_launches": prof["push_launches"],
-                "push_ms_per_launch": prof["push_ms"] / launches,
-                "scan_ms_per_launch": prof["scan_ms"] / max(prof["scan_launches"], 1),
-                "alg_bytes_per_launch": alg / launches,
-                "random_access": random_access(
-                    mt, mt.PROBE_RED_F32 if mixed else mt.PROBE_RED_F64, g.n, local,
-                    prof["edge_pushes"], prof["push_ms"],
-                    "f32 atomicAdd" if mixed else "f64 atomicAdd"),
-                "note": "achieved = algorithmic bytes of the push (12 B per FP32 message, 32 B "
-                        "per update; FP64 warm-up rounds at 20 / 40 B) / device time of the "
-                        "push launches"}
+
+    def kernel_roofline(kw, kernel, kind, what, traffic_key, note):
+        pf = mt.run(G, eps=eps, damping=D_PR, stream=stream.cuda_stream,
+                    flags=mt.FLAG_PROFILE_KERNELS, **kw).stats()
+        is_mixed = kw["op"] == mt.OP_SUM_MIXED
+        alg = pagerank_alg_bytes(pf, is_mixed)
+        launches = max(pf["push_launches"], 1)
+        achieved = alg / (pf["push_ms"] * 1e-3) / 1e9
+        out = {"bound": "hbm", "kernel": kernel,
+               "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_tab.get(traffic_key),
+               "peak_kind": f"{peak_kind} copy bandwidth",
+               "launches": pf["push_launches"],
+               "ms_per_launch": pf["push_ms"] / launches,
+               "alg_bytes_per_launch": alg / launches,
+               "random_access": random_access(mt, kind, g.n, local, pf["edge_pushes"],
+                                              pf["push_ms"], what),
+               "note": note}
+        if pf["scan_launches"]:
+            out["scan_ms_per_launch"] = pf["scan_ms"] / pf["scan_launches"]
+        return out
+
+    if head == "pull_f32":
+        roofline = kernel_roofline(
+            variants[head], "k_pull<float,float> (a warp per 32 receivers or per 1024-edge "
+            "chunk of a receiver of in-degree > 256)", mt.PROBE_LOAD_32,
+            "32-bit loads", f"k_pull_pagerank_f32_rmat{cfg['scale']}",
+            "achieved = algorithmic bytes (12 B per FP32 message, 32 B per update, the same "
+            "definition as the push's) / device time of the pull launches")
+        push_roofline = kernel_roofline(
+            variants["mixed_sync"], "k_push<OpSumMixed> (warm-up rounds k_push<OpSumWarm>)",
+            mt.PROBE_RED_F32, "f32 atomicAdd", f"k_push_pagerank_mixed_rmat{cfg['scale']}",
+            "achieved = algorithmic bytes of the push (12 B per FP32 message, 32 B per update; "
+            "FP64 warm-up rounds at 20 / 40 B) / device time of the push launches")
+    else:
+        roofline = kernel_roofline(
+            variants[head], "k_push<OpSumF64>", mt.PROBE_RED_F64, "f64 atomicAdd",
+            f"k_push_pagerank_f64_rmat{cfg['scale']}",
+            "achieved = algorithmic bytes of the push (20 B per FP64 message, 40 B per update) "
+            "/ device time of the push launches")
+        push_roofline = None
     bprof = None
-    if "binned_mixed" in variants:
+    if "binned_f32" in variants:
         bp = mt.run(G, eps=eps, damping=D_PR, stream=stream.cuda_stream,
                     flags=mt.FLAG_PROFILE_KERNELS, **variants["binned_f32"]).stats()
         br = max(bp["push_launches"], 1)
@@ -502,16 +529,20 @@ def run_pagerank(args, wl, dist=None, nested=None):
         "dtype": "f32/f64" if mixed else "f64", "data": "synthetic",
         "config": pagerank_config(wl, cfg, g, world),
         "headline": head,
-        "engine": "round engine: frontier scan + degree-bucketed push with L2 atomics; CUDA "
+        "engine": ("receive-side engine: every receiver sums the messages of its in-neighbours "
+                   "over the transpose (no atomic per edge), then folds; CUDA graph with a "
+                   "device-side WHILE") if head == "pull_f32" else
+                  "round engine: frontier scan + degree-bucketed push with L2 atomics; CUDA "
                   "graph with a device-side WHILE",
-        "precision": ("FP32 deltas and messages after an FP64 warm-up; FP64 state, sums and "
-                      "residual") if mixed else "FP64",
+        "precision": ("FP32 deltas and messages from the first round; FP64 state and residual "
+                      "reduction") if mixed else "FP64",
         "time_to_tolerance_ms": ms,
         "vs_plain_form": plain_t / ms if plain_t else None,
         "error_bound": bound,
         "variants": results,
         "gteps_work": hs["edge_pushes"] / (ms * 1e-3) / 1e9,
         "roofline": roofline,
+        "push_roofline": push_roofline,
         "binned_roofline": bprof,
         "e2e": e2e,
         # every timed run's kernels, + one L2 flush fill per step

@@ -5,7 +5,6 @@
 // condition set by the decision kernel (no host round trip per round).
 #include <algorithm>
 #include <cstring>
-#include <vector>
 
 #include "internal.h"
 #include "pull_kernels.cuh"
@@ -63,10 +62,11 @@ cudaError_t grow(T** p, size_t* cap, size_t need) {
 
 }  // namespace
 
-// Builds (or rebuilds after an update) the transpose of g on stream st: the
-// in-degrees on the device, the row offsets, the tail offsets of the large
-// rows and their chunk list on the host (once per graph content), then the
-// senders placed by one atomic cursor per receiver.
+// Builds (or rebuilds after an update) the transpose of g on stream st, on
+// the device: the in-degrees, one int4 prefix scan over the rows (small-row
+// offsets, tail offsets, chunk entries, large-row index) whose total is the
+// one value read back (to size the chunk list), then the senders placed by
+// one atomic cursor per receiver.
 maiter_status ensure_pull(const maiter_graph* cg, cudaStream_t st) {
   maiter_graph* g = const_cast<maiter_graph*>(cg);
   if (g->pull && g->pull->valid) return MAITER_OK;
@@ -74,82 +74,62 @@ maiter_status ensure_pull(const maiter_graph* cg, cudaStream_t st) {
   PullLayout* L = g->pull;
   const int64_t n = g->n, m = g->m;
   const int64_t nwords = (n + 31) / 32;
+  const int ntiles = static_cast<int>((n + kPullScanTile - 1) / kPullScanTile);
   MAITER_CUDA(grow(&L->crp, &L->crp_cap, static_cast<size_t>(n + 1)));
   MAITER_CUDA(grow(&L->csrc, &L->csrc_cap, static_cast<size_t>(m)));
   MAITER_CUDA(grow(&L->crow, &L->crow_cap, static_cast<size_t>(m)));
   MAITER_CUDA(grow(&L->lbits, &L->lbits_cap, static_cast<size_t>(nwords)));
-  int* cursor = nullptr;
-  MAITER_CUDA(cudaMalloc(&cursor, sizeof(int) * std::max<int64_t>(n, 1)));
-  cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(int) * std::max<int64_t>(n, 1), st);
+  const size_t n1 = static_cast<size_t>(std::max<int64_t>(n, 1));
+  int* indeg = nullptr;
+  int* first = nullptr;
+  int4* sums = nullptr;
+  cudaError_t e = cudaMalloc(&indeg, sizeof(int) * n1);
+  if (e == cudaSuccess) e = cudaMalloc(&first, sizeof(int) * n1);
+  if (e == cudaSuccess) e = cudaMalloc(&sums, sizeof(int4) * (ntiles + 1));
+  if (e == cudaSuccess) e = cudaMemsetAsync(indeg, 0, sizeof(int) * n1, st);
   if (e == cudaSuccess && m > 0) {
-    k_pull_indegree<<<g->num_sms * 4, 256, 0, st>>>(g->col, m, cursor);
+    k_pull_indegree<<<g->num_sms * 4, 256, 0, st>>>(g->col, m, indeg);
     e = cudaGetLastError();
   }
-  std::vector<int> indeg(static_cast<size_t>(n));
-  if (e == cudaSuccess && n > 0)
-    e = cudaMemcpyAsync(indeg.data(), cursor, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  std::vector<int> crp(static_cast<size_t>(n + 1)), first(static_cast<size_t>(n));
-  std::vector<unsigned> lbits(static_cast<size_t>(std::max<int64_t>(nwords, 1)), 0u);
-  std::vector<int4> large;
-  std::vector<int> nch;
-  if (e == cudaSuccess) {
-    // small rows first (their offsets are crp), then the large rows' edges
-    int64_t run = 0;
-    for (int64_t k = 0; k < n; ++k) {
-      crp[k] = static_cast<int>(run);
-      first[k] = static_cast<int>(run);
-      if (indeg[k] <= kPullCut) run += indeg[k];
-    }
-    crp[n] = static_cast<int>(run);
-    for (int64_t k = 0; k < n; ++k) {
-      const int d = indeg[k];
-      if (d <= kPullCut) continue;
-      lbits[k >> 5] |= 1u << (k & 31);
-      first[k] = static_cast<int>(run);
-      const int li = static_cast<int>(nch.size());
-      int c = 0;
-      for (int b = 0; b < d; b += kPullChunk, ++c)
-        large.push_back(make_int4(static_cast<int>(k), static_cast<int>(run + b),
-                                  static_cast<int>(run + std::min(d, b + kPullChunk)), li));
-      nch.push_back(c);
-      run += d;
-    }
-    e = cudaMemcpyAsync(L->crp, crp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st);
-  }
-  if (e == cudaSuccess && n > 0)
-    e = cudaMemcpyAsync(cursor, first.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && nwords > 0)
-    e = cudaMemcpyAsync(L->lbits, lbits.data(), sizeof(unsigned) * nwords, cudaMemcpyHostToDevice, st);
+  int4 totals = make_int4(0, 0, 0, 0);   // small edges, tail edges, chunks, large rows
   if (e == cudaSuccess && n > 0) {
-    k_pull_place<<<g->num_sms * 8, 256, 0, st>>>(g->rp, g->col, static_cast<int>(n), cursor, L->csrc,
-                                                 L->crow);
+    k_pull_tile_sums<<<ntiles, kPullScanBlock, 0, st>>>(indeg, static_cast<int>(n), sums);
+    k_pull_scan_sums<<<1, kPullScanBlock, 0, st>>>(sums, ntiles);
     e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&totals, sums + ntiles, sizeof(int4), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  } else if (e == cudaSuccess) {
+    e = cudaMemsetAsync(L->crp, 0, sizeof(int), st);
   }
-  L->nlarge = static_cast<int>(large.size());
-  L->nlrows = static_cast<int>(nch.size());
-  if (e == cudaSuccess) e = grow(&L->large, &L->large_cap, large.size());
-  if (e == cudaSuccess) e = grow(&L->large_nch, &L->lrow_cap, nch.size());
+  L->nlarge = totals.z;
+  L->nlrows = totals.w;
+  if (e == cudaSuccess) e = grow(&L->large, &L->large_cap, static_cast<size_t>(totals.z));
+  if (e == cudaSuccess) e = grow(&L->large_nch, &L->lrow_cap, static_cast<size_t>(totals.w));
   if (e == cudaSuccess) {
-    // lacc / lcnt: one entry per large row
+    // lacc / lcnt: one entry per large row, zero between rounds
     cudaFree(L->lacc);
     cudaFree(L->lcnt);
     L->lacc = nullptr;
     L->lcnt = nullptr;
-    e = cudaMalloc(&L->lacc, sizeof(double) * std::max<size_t>(nch.size(), 1));
-    if (e == cudaSuccess) e = cudaMalloc(&L->lcnt, sizeof(unsigned) * std::max<size_t>(nch.size(), 1));
+    const size_t nl = static_cast<size_t>(std::max(totals.w, 1));
+    e = cudaMalloc(&L->lacc, sizeof(double) * nl);
+    if (e == cudaSuccess) e = cudaMalloc(&L->lcnt, sizeof(unsigned) * nl);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->lacc, 0, sizeof(double) * nl, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->lcnt, 0, sizeof(unsigned) * nl, st);
   }
-  if (e == cudaSuccess && !large.empty())
-    e = cudaMemcpyAsync(L->large, large.data(), sizeof(int4) * large.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && !nch.empty())
-    e = cudaMemcpyAsync(L->large_nch, nch.data(), sizeof(int) * nch.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(L->lacc, 0, sizeof(double) * std::max<size_t>(nch.size(), 1), st);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(L->lcnt, 0, sizeof(unsigned) * std::max<size_t>(nch.size(), 1), st);
-  // the host vectors are read by the copies: wait before they go out of scope
+  if (e == cudaSuccess && n > 0) {
+    k_pull_offsets<<<ntiles, kPullScanBlock, 0, st>>>(indeg, static_cast<int>(n), sums, ntiles,
+                                                       L->crp, first, L->lbits, L->large,
+                                                       L->large_nch);
+    k_pull_place<<<g->num_sms * 8, 256, 0, st>>>(g->rp, g->col, static_cast<int>(n), first,
+                                                 L->csrc, L->crow);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(cursor);
+  cudaFree(indeg);
+  cudaFree(first);
+  cudaFree(sums);
   MAITER_CUDA(e);
   L->valid = true;
   return MAITER_OK;

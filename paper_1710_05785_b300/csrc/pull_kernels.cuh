@@ -149,7 +149,7 @@ __device__ __forceinline__ void pull_fold(const PullArgs& a, MT* msg_out, int k,
 // warp each (no block barrier).  Sums in the message precision within a
 // step, in MT per row across steps (FP64 across the large rows' chunks).
 template <class DT, class MT>
-__global__ void __launch_bounds__(kPullBlock) k_pull(PullArgs a) {
+__global__ void __launch_bounds__(kPullBlock, 8) k_pull(PullArgs a) {
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();
   DevCtl* ctl = a.ctl;
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kPullBlock) k_pull(PullArgs a) {
     for (int e = ent.y + lane; e < ent.z; e += 128) {
       int src[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) src[u] = e + 32 * u < ent.z ? __ldg(a.csrc + e + 32 * u) : -1;
+      for (int u = 0; u < 4; ++u) src[u] = e + 32 * u < ent.z ? __ldcs(a.csrc + e + 32 * u) : -1;
 #pragma unroll
       for (int u = 0; u < 4; ++u) if (src[u] >= 0) x[u] += msg_in[src[u]];
     }
@@ -210,8 +210,10 @@ __global__ void __launch_bounds__(kPullBlock) k_pull(PullArgs a) {
 #pragma unroll
       for (int h = 0; h < kPullSteps; ++h) {
         const int e = e0 + 32 * h + lane;
-        src[h] = e < ge ? __ldg(a.csrc + e) : -1;
-        r[h] = e < ge ? static_cast<int>(__ldg(a.crow + e)) : 32;   // past the end: a key of its own
+        // the edge streams are read once a round: evict-first in L2, so
+        // they do not push the message array (read at random) out of it
+        src[h] = e < ge ? __ldcs(a.csrc + e) : -1;
+        r[h] = e < ge ? static_cast<int>(__ldcs(a.crow + e)) : 32;   // past the end: a key of its own
       }
 #pragma unroll
       for (int h = 0; h < kPullSteps; ++h) x[h] = src[h] >= 0 ? msg_in[src[h]] : MT(0);
@@ -243,6 +245,124 @@ __global__ void __launch_bounds__(kPullBlock) k_pull(PullArgs a) {
 
 // ---------------------------------------------------------- layout build
 
+// ------------------------------------------------ layout build (device)
+// The layout's four counts of row k: small-row in-edges, tail in-edges,
+// chunks and large rows (one), scanned together as an int4 over the rows in
+// three passes: tile totals, a scan of the tile totals (one CTA), and the
+// tiles' own scans, which write the offsets.
+constexpr int kPullScanBlock = 256;
+constexpr int kPullScanItems = 8;
+constexpr int kPullScanTile = kPullScanBlock * kPullScanItems;   // rows per tile
+
+__device__ __forceinline__ int4 pull_counts(int d) {
+  const bool big = d > kPullCut;
+  return make_int4(big ? 0 : d, big ? d : 0, big ? (d + kPullChunk - 1) / kPullChunk : 0, big ? 1 : 0);
+}
+__device__ __forceinline__ int4 add4(int4 a, int4 b) {
+  return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ int4 shfl_up4(int4 v, int o) {
+  return make_int4(__shfl_up_sync(0xffffffffu, v.x, o), __shfl_up_sync(0xffffffffu, v.y, o),
+                   __shfl_up_sync(0xffffffffu, v.z, o), __shfl_up_sync(0xffffffffu, v.w, o));
+}
+// Inclusive block scan of one int4 per thread; returns the block total too.
+__device__ __forceinline__ int4 block_scan4(int4 v, int4* total) {
+  __shared__ int4 s_w[kPullScanBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int4 t = shfl_up4(v, o);
+    if (lane >= o) v = add4(v, t);
+  }
+  if (lane == 31) s_w[wid] = v;
+  __syncthreads();
+  int4 off = make_int4(0, 0, 0, 0), tot = make_int4(0, 0, 0, 0);
+  for (int w = 0; w < kPullScanBlock / 32; ++w) {
+    if (w < wid) off = add4(off, s_w[w]);
+    tot = add4(tot, s_w[w]);
+  }
+  __syncthreads();   // s_w is reused by the caller's next scan
+  *total = tot;
+  return add4(v, off);
+}
+
+// Pass 1: every tile's total.
+static __global__ void __launch_bounds__(kPullScanBlock) k_pull_tile_sums(const int* __restrict__ indeg,
+                                                                          int n, int4* __restrict__ sums) {
+  const int base = blockIdx.x * kPullScanTile + threadIdx.x * kPullScanItems;
+  int4 v = make_int4(0, 0, 0, 0);
+#pragma unroll
+  for (int i = 0; i < kPullScanItems; ++i)
+    if (base + i < n) v = add4(v, pull_counts(__ldg(indeg + base + i)));
+  int4 tot;
+  block_scan4(v, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Pass 2 (one CTA): exclusive scan of the tile totals in place, and the
+// grand total in sums[ntiles].
+static __global__ void __launch_bounds__(kPullScanBlock) k_pull_scan_sums(int4* sums, int ntiles) {
+  int4 carry = make_int4(0, 0, 0, 0);
+  for (int b0 = 0; b0 < ntiles; b0 += kPullScanBlock) {
+    const int b = b0 + threadIdx.x;
+    const int4 v = b < ntiles ? sums[b] : make_int4(0, 0, 0, 0);
+    int4 tot;
+    const int4 inc = block_scan4(v, &tot);
+    if (b < ntiles) sums[b] = add4(carry, make_int4(inc.x - v.x, inc.y - v.y, inc.z - v.z, inc.w - v.w));
+    carry = add4(carry, tot);
+  }
+  if (threadIdx.x == 0) sums[ntiles] = carry;
+}
+
+// Pass 3: each tile's scan from its offset: crp (small-row offsets), the
+// first slot of every row (its crp, or its tail offset after all small-row
+// edges), the large-row flags and, for every large row, its chunk entries.
+static __global__ void __launch_bounds__(kPullScanBlock) k_pull_offsets(
+    const int* __restrict__ indeg, int n, const int4* __restrict__ sums, int ntiles,
+    int* __restrict__ crp, int* __restrict__ first, unsigned* __restrict__ lbits,
+    int4* __restrict__ large, int* __restrict__ large_nch) {
+  const int base = blockIdx.x * kPullScanTile + threadIdx.x * kPullScanItems;
+  int d[kPullScanItems];
+  int4 v = make_int4(0, 0, 0, 0);
+#pragma unroll
+  for (int i = 0; i < kPullScanItems; ++i) {
+    d[i] = base + i < n ? __ldg(indeg + base + i) : 0;
+    v = add4(v, pull_counts(d[i]));
+  }
+  int4 tot;
+  const int4 inc = block_scan4(v, &tot);
+  const int4 tile_off = sums[blockIdx.x];
+  const int small_total = sums[ntiles].x;
+  int4 run = add4(tile_off, make_int4(inc.x - v.x, inc.y - v.y, inc.z - v.z, inc.w - v.w));
+  unsigned flags = 0u;
+#pragma unroll
+  for (int i = 0; i < kPullScanItems; ++i) {
+    const int k = base + i;
+    if (k >= n) break;
+    const int4 c = pull_counts(d[i]);
+    crp[k] = run.x;
+    if (c.w) {
+      flags |= 1u << i;
+      const int tail = small_total + run.y;
+      first[k] = tail;
+      large_nch[run.w] = c.z;
+      for (int q = 0; q < c.z; ++q)
+        large[run.z + q] = make_int4(k, tail + q * kPullChunk, tail + min(d[i], (q + 1) * kPullChunk), run.w);
+    } else {
+      first[k] = run.x;
+    }
+    run = add4(run, c);
+  }
+  if (base < n && base + kPullScanItems >= n) crp[n] = small_total;   // the thread of the last row
+  // 32 consecutive rows = 4 threads' flags
+  const int lane = threadIdx.x & 31;
+  const unsigned sh = (lane & 3) * kPullScanItems;
+  unsigned w = flags << sh;
+  w |= __shfl_down_sync(0xffffffffu, w, 1);
+  w |= __shfl_down_sync(0xffffffffu, w, 2);
+  if ((lane & 3) == 0 && base < n) lbits[base >> 5] = w;
+}
+
 // In-degree of every vertex (cnt zeroed by the caller).
 static __global__ void k_pull_indegree(const int* __restrict__ col, int64_t m, int* __restrict__ cnt) {
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < m;
@@ -252,13 +372,17 @@ static __global__ void k_pull_indegree(const int* __restrict__ col, int64_t m, i
 
 // In-edge placement: csrc[cursor[k]++] = j for every edge j -> k (cursor
 // starts at row k's first slot, in the small-row region or in the tail), and
-// the slot's row within its group.
+// the slot's row within its group.  A warp per sender, its lanes over the
+// sender's out-edges (a sender of high out-degree is not one thread's loop).
 static __global__ void k_pull_place(const int* __restrict__ rp, const int* __restrict__ col, int n,
                                     int* __restrict__ cursor, int* __restrict__ csrc,
                                     unsigned char* __restrict__ crow) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int j = w0; j < n; j += nw) {
     const int e1 = __ldg(rp + j + 1);
-    for (int e = __ldg(rp + j); e < e1; ++e) {
+    for (int e = __ldg(rp + j) + lane; e < e1; e += 32) {
       const int k = __ldg(col + e);
       const int pos = atomicAdd(cursor + k, 1);
       csrc[pos] = j;

@@ -7,7 +7,7 @@ in FP64) satisfies (I - dP^T)(v* - v) = r, hence
 and since v only grows towards v* (Section 3.5), max_j v_j <= max_j v*_j.
 
 The FP64 run is bounded directly this way.  For the mixed-precision runs
-and the binned engine's runs the L1 bound is loose (it sums FP32 rounding
+and the binned and receive-side engines' runs the L1 bound is loose (it sums FP32 rounding
 over every vertex), so their max error is bounded through the FP64 run:
     max|v_other - v*| <= max|v_other - v_f64| + ||r_f64||_1 / (1 - d)."""
 import numpy as np
@@ -37,7 +37,11 @@ def runs(mt, pagerank24):
                      ("binned_f64", dict(op=mt.OP_SUM_F64, engine=mt.ENGINE_BINNED)),
                      ("binned_mixed", dict(op=mt.OP_SUM_MIXED, engine=mt.ENGINE_BINNED)),
                      ("binned_f32", dict(op=mt.OP_SUM_MIXED, engine=mt.ENGINE_BINNED,
-                                         mixed_switch=1.0))]:
+                                         mixed_switch=1.0)),
+                     ("pull_f64", dict(op=mt.OP_SUM_F64, engine=mt.ENGINE_PULL)),
+                     ("pull_mixed", dict(op=mt.OP_SUM_MIXED, engine=mt.ENGINE_PULL)),
+                     ("pull_f32", dict(op=mt.OP_SUM_MIXED, engine=mt.ENGINE_PULL,
+                                       mixed_switch=1.0))]:
         op = kw.pop("op")
         r = mt.run(G, op, damping=D, eps=4e-8, **kw)
         assert r.stats()["converged"] == 1
@@ -58,8 +62,9 @@ def test_pagerank_scale24_mixed_within_1e6(runs):
     assert err <= 1e-6 * vf.max(), (err, vf.max())
 
 
-@pytest.mark.parametrize("name", ["binned_f64", "binned_mixed", "binned_f32"])
-def test_pagerank_scale24_binned_within_1e6(runs, name):
+@pytest.mark.parametrize("name", ["binned_f64", "binned_mixed", "binned_f32",
+                                  "pull_f64", "pull_mixed", "pull_f32"])
+def test_pagerank_scale24_binned_and_pull_within_1e6(runs, name):
     vb, vf = runs[name], runs["OP_SUM_F64"]
     err = np.abs(vb - vf).max() + runs["bound_f64"]
     assert err <= 1e-6 * vf.max(), (name, err, vf.max())
