@@ -1,18 +1,23 @@
-"""Benchmark: SSSP in DAIC form on a seeded R-MAT graph (scale 20, edge factor
-16, uint32 weights uniform in [1, 255]), 8 sources run one after another, every
-run to the exact fixed point (no pending vertex).  One step = the 8 sources.
+"""Benchmark of DAIC delta propagation on one B300.
 
-Metric: GTEPS = (sources x m) / device time of the step, with the graph
-resident in HBM.  Beside it: time to solution per source, GTEPS over the edge
-pushes actually performed, the push kernel's fraction of the measured HBM
-copy bandwidth, an end-to-end figure through the C ABI from pinned host
-buffers, and the CPU oracle (Dijkstra, one core) on the machine's host.
+Default workload: PageRank in DAIC form (d = 0.8, v0 = 0, Delta1 = 0.2) on a
+seeded R-MAT graph of scale 24, edge factor 16 (16.8 M vertices, 268 M
+edges), FP32 deltas and messages with FP64 state and residual reduction, run
+to sum |Delta| < 4e-8 on the receive-side engine; one step = one run from the
+initial state to the tolerance.  Metric: GTEPS = m / time-to-tolerance, with
+the graph resident in HBM.  Beside it: the plain FP64 form and the other
+engines and precisions as checked variants, the dominant kernel's fraction of
+the measured HBM copy bandwidth (and the push kernel's), an end-to-end figure
+through the C ABI from pinned host buffers, the CPU oracle on the machine's host
+and the clocks seen during the timed region.  The SSSP record (R-MAT scale
+20, 8 sources one after another, exact) is nested in the same line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload NAME]
 
-Multi-GPU (torchrun): the sources are independent problems, so each rank runs
-its own 8 sources on its own copy of the graph (weak scaling, no collective on
-the data path; a barrier and a max over ranks frame the timing).
+Multi-GPU (torchrun): the runs are independent problems, so each rank runs
+its own copy (weak scaling, no collective on the data path; a barrier and a
+max over ranks frame the timing).
 """
 from __future__ import annotations
 
