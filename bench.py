@@ -385,8 +385,7 @@ def run_pagerank(args, wl, dist=None, nested=None):
     }
     if not mixed:
         del variants["pull_f32"]
-    if cfg["scale"] < 20:
-        variants["f64_async"] = dict(op=mt.OP_SUM_F64, engine=mt.ENGINE_ASYNC)
+    variants["f64_async"] = dict(op=mt.OP_SUM_F64, engine=mt.ENGINE_ASYNC)
     if args.head_only:
         variants = {head: variants[head]}
     res = {}

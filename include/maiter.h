@@ -125,14 +125,18 @@ typedef enum {
   MAITER_ENGINE_SYNC = 0,     /* round loop: frontier, then push; the loop and its
                                  termination test run on the device (CUDA graph
                                  with a conditional node), no host round trip */
-  MAITER_ENGINE_ASYNC = 1,    /* persistent kernel over a device work queue: warps
-                                 take queued vertices, update them and re-queue
-                                 receivers whose delta crosses the threshold (ALL:
-                                 eps / (2n)), with no barrier between CTAs (Eq. 5,
-                                 Section 3.2).  Between launches an exact device
-                                 reduction tests termination and re-seeds the queue
-                                 (the periodic check of Section 5.1).  SUM_F64 and
-                                 MIN_U32; schedules ALL and THRESHOLD. */
+  MAITER_ENGINE_ASYNC = 1,    /* persistent kernel of round-robin workers: every
+                                 CTA owns an interleaved share of the vertices and
+                                 sweeps it again and again, updating each pending
+                                 vertex it finds and scattering its messages with
+                                 atomics, with no barrier between CTAs (Eq. 5,
+                                 Section 3.2).  A launch ends when no CTA finds
+                                 work; between launches an exact device reduction
+                                 tests termination (the periodic check of Section
+                                 5.1).  Sums update a vertex whose |delta| exceeds
+                                 half the mean |delta| of the check before (ALL:
+                                 never less than eps / (2n)).  SUM_F64 and MIN_U32;
+                                 schedules ALL and THRESHOLD. */
   MAITER_ENGINE_BINNED = 2,   /* rounds in which every vertex with a pending delta
                                  sends (the synchronous DAIC of Section 3.2, schedule
                                  ALL), for SUM_F64 / SUM_MIXED with g = SCALE_BY_SRC.

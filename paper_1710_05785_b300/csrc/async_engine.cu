@@ -6,33 +6,22 @@
 
 namespace maiter {
 
-constexpr int kAsyncBlock = 512;
+constexpr int kAsyncBlock = 256;
 
 void free_async(maiter_result* r) {
   if (r->aexec) cudaGraphExecDestroy(r->aexec);
   if (r->agraph) cudaGraphDestroy(r->agraph);
-  cudaFree(r->aqueue);
-  cudaFree(r->inq);
   cudaFree(r->actl);
   if (r->h_actl) cudaFreeHost(r->h_actl);
   r->aexec = nullptr;
   r->agraph = nullptr;
-  r->aqueue = nullptr;
-  r->inq = nullptr;
   r->actl = nullptr;
   r->h_actl = nullptr;
 }
 
-static maiter_status alloc_async(const maiter_graph* g, maiter_result* r) {
-  if (r->aqueue) return MAITER_OK;
-  const size_t n = static_cast<size_t>(g->n > 0 ? g->n : 1);
-  // At most n vertices are queued at once (in-queue flags); twice that plus
-  // room for every warp's in-flight reservation keeps producers off slots
-  // that a slow consumer has not emptied yet.
-  r->acap = 2ull * n + 65536ull;
-  cudaError_t e = cudaMalloc(&r->aqueue, sizeof(int) * r->acap);
-  if (e == cudaSuccess) e = cudaMalloc(&r->inq, sizeof(unsigned) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&r->actl, sizeof(AsyncCtl));
+static maiter_status alloc_async(const maiter_graph*, maiter_result* r) {
+  if (r->actl) return MAITER_OK;
+  cudaError_t e = cudaMalloc(&r->actl, sizeof(AsyncCtl));
   if (e == cudaSuccess) e = cudaMallocHost(&r->h_actl, sizeof(AsyncCtl));
   if (e != cudaSuccess) {
     set_error("async buffers: %s", cudaGetErrorString(e));
@@ -57,9 +46,6 @@ struct AsyncPlan {
     a.damping = damping;
     a.v = static_cast<typename Op::V*>(r->v);
     a.delta = static_cast<typename Op::D*>(r->delta);
-    a.queue = r->aqueue;
-    a.cap = r->acap;
-    a.inq = r->inq;
     a.ctl = r->actl;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -67,6 +53,7 @@ struct AsyncPlan {
             cudaSuccess ||
         per_sm < 1)
       per_sm = 1;
+    // persistent: every CTA resident at once (an idle CTA waits for the others)
     grid = g->num_sms * per_sm;
     seed_grid = g->num_sms * 4;
     const int need = static_cast<int>((g->n + kAsyncBlock - 1) / kAsyncBlock);
@@ -129,19 +116,20 @@ static maiter_status run_async_op(const maiter_graph* g, const maiter_run_params
   }
   AsyncCtl c{};
   if (Op::kIsSum) {
-    // All pending vertices: re-activate a vertex once its delta exceeds
-    // eps / (2n), so the queue empties with sum |Delta| <= eps / 2.
+    // All pending vertices: a vertex is worth an update once its delta
+    // exceeds eps / (2n), so a quiescent launch leaves sum |Delta| <= eps / 2;
+    // each launch raises that to a fraction of the mean delta (k_async_seed).
     c.tau = (p->sched == MAITER_SCHED_THRESHOLD) ? p->threshold
                                                  : p->eps / (2.0 * static_cast<double>(g->n));
+    c.theta = c.tau;
   }
+  c.grid = plan.grid;
   c.eps = p->eps;
   c.max_epochs = p->max_rounds > 0 ? p->max_rounds : 1000000;
   const long long tmo = p->timeout_ms > 0 ? p->timeout_ms : 10000;
   c.timeout_ns = static_cast<unsigned long long>(tmo) * 1000000ull;
   c.inject_stall = (p->flags & MAITER_FLAG_INJECT_STALL) ? 1 : 0;
   *r->h_actl = c;
-  MAITER_CUDA(cudaMemsetAsync(r->aqueue, 0xFF, sizeof(int) * r->acap, st));
-  MAITER_CUDA(cudaMemsetAsync(r->inq, 0, sizeof(unsigned) * g->n, st));
   MAITER_CUDA(cudaMemcpyAsync(r->actl, r->h_actl, sizeof(AsyncCtl), cudaMemcpyHostToDevice, st));
   maiter_stats& s = r->stats;
   s = maiter_stats{};

@@ -106,9 +106,6 @@ struct maiter_result {
   cudaGraphExec_t exec = nullptr;
   uint64_t exec_key = 0;
   // asynchronous engine (allocated on its first use)
-  int* aqueue = nullptr;               // ring of vertex ids, acap slots
-  unsigned long long acap = 0;
-  unsigned int* inq = nullptr;         // n in-queue flags
   maiter::AsyncCtl* actl = nullptr;
   maiter::AsyncCtl* h_actl = nullptr;  // pinned mirror
   cudaGraph_t agraph = nullptr;
