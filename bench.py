@@ -122,7 +122,10 @@ def run_in_threads(fns):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed
+    region (every 50 ms).  The timed region starts only once the first sample
+    is in, so a region shorter than the interval still has the sample taken
+    at its start; `samples_in_region` counts those taken after it began."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -131,19 +134,27 @@ class ClockSampler:
     def __init__(self, device: int):
         self.device = device
         self.proc = None
+        self.first = []
 
     def __enter__(self):
+        import select
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+        if self.proc is not None:
+            ready, _, _ = select.select([self.proc.stdout], [], [], 10.0)
+            if ready:
+                line = self.proc.stdout.readline()
+                if line.strip():
+                    self.first = [line]
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
+        self.lines = list(self.first)
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -151,7 +162,7 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
                 out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            self.lines += [l for l in out.splitlines() if l.strip()]
 
     def summary(self):
         sm, mx, reasons = [], 0.0, set()
@@ -169,7 +180,8 @@ class ClockSampler:
                 if val.lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sm)}
+                "sm_max_mhz": mx or None, "reasons": sorted(reasons), "samples": len(sm),
+                "samples_in_region": max(0, len(sm) - len(self.first))}
 
 
 def cpu_baseline(g, sources, budget_s=25.0):

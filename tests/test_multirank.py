@@ -91,4 +91,10 @@ def test_clock_summary_reports_median_clock_and_throttle_reasons():
     c.lines = ["0, 1500, 2032, 500.0, 0x8, Active, Not Active, Active, Not Active"]
     assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     c.lines = []
-    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                           "samples_in_region": 0}
+    # the sample taken as the region starts counts in samples, not in the region's
+    c.first = ["0, 2032, 2032, 600.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    c.lines = c.first + ["0, 2032, 2032, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    s = c.summary()
+    assert s["samples"] == 2 and s["samples_in_region"] == 1
