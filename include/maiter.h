@@ -464,7 +464,19 @@ typedef struct maiter_batch_params {
                               vertex) items as described above; 2 = dense with
                               the branches chained: the queries run one after
                               another, in order, inside one graph launch (no
-                              host round trip between them) */
+                              host round trip between them); 3 = the
+                              personalised-PageRank queries of each graph in
+                              groups of up to 64, each group one receive-side
+                              run (the receive step of Eq. 5 at the receivers,
+                              as MAITER_ENGINE_PULL) over query vectors: a
+                              vertex's deltas, states and messages for the
+                              group's queries are contiguous, so an in-edge
+                              costs one 256-byte read for all of them; FP32
+                              deltas and messages, FP64 states and per-query
+                              FP64 residuals, each query stopping its count at
+                              sum |Delta| < eps_q / 2 (the other half of its
+                              bound is left to the FP32 rounding; the group
+                              runs until all have); SSSP queries as in mode 0 */
   int32_t reserved;        /* must be 0 */
 } maiter_batch_params;
 

@@ -37,7 +37,7 @@ MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 8, 64, 641
 ENGINE_SYNC, ENGINE_ASYNC, ENGINE_BINNED, ENGINE_PULL = 0, 1, 2, 3
 FLAG_PROFILE_KERNELS, FLAG_INJECT_STALL = 1, 2
 # maiter_batch_params.mode
-BATCH_DENSE, BATCH_SPARSE, BATCH_DENSE_CHAINED = 0, 1, 2
+BATCH_DENSE, BATCH_SPARSE, BATCH_DENSE_CHAINED, BATCH_PULL_GROUPS = 0, 1, 2, 3
 # maiter_probe_kind
 PROBE_RED_F32, PROBE_RED_F64, PROBE_MIN_U32, PROBE_LOAD_32 = 0, 1, 2, 3
 
@@ -418,8 +418,10 @@ def run_batch(graphs, queries, *, max_rounds: int = 1000000, stream=None, cut_la
     (OP_SUM_F64 or OP_MIN_U32), graph (index), seeds (ids), and for PageRank
     damping and eps.  ``mode``: BATCH_DENSE (each query a round-engine run,
     all side by side in one graph launch), BATCH_SPARSE ((query, vertex)
-    frontiers) or BATCH_DENSE_CHAINED (the dense runs one after another, in
-    order, in one graph launch)."""
+    frontiers), BATCH_DENSE_CHAINED (the dense runs one after another, in
+    order, in one graph launch) or BATCH_PULL_GROUPS (the PageRank queries of
+    a graph 64 at a time as one receive-side run over query vectors, FP32
+    deltas and FP64 state; SSSP queries as in BATCH_DENSE)."""
     G = (ctypes.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
     Q = (QuerySpec * len(queries))()
     keep = []

@@ -8,7 +8,22 @@
 
 #include "internal.h"
 #include "batch_kernels.cuh"
+#include "pull_vec_kernels.cuh"
 #include "sync_phase.cuh"
+
+// Mode 3: personalised-PageRank queries of one graph, kVQ at a time, as one
+// receive-side run with query vectors (pull_vec_kernels.cuh).
+struct VGroup {
+  int graph = 0;
+  int nq = 0;
+  int q[maiter::kVQ];                 // batch query of each slot
+  maiter::PullVArgs a{};
+  maiter::VCtl init{};
+  int2* d_seeds = nullptr;            // (slot, vertex)
+  float* d_seedval = nullptr;
+  int nseeds = 0;
+  int pull_grid = 1, prime_grid = 1, init_grid = 1;
+};
 
 struct maiter_batch {
   int device = 0;
@@ -45,6 +60,10 @@ struct maiter_batch {
   int* d_qseeds = nullptr;
   maiter::DevCtl* h_ctls = nullptr;      // pinned, one per query
   int dense_grid_cap = 0;
+  // mode 3: the query groups and each query's group and slot (-1: own branch)
+  std::vector<VGroup> vg;
+  std::vector<int> q_group, q_slot;
+  maiter::VCtl* h_vctl = nullptr;        // pinned, one per group
   maiter_stats stats{};
 };
 
@@ -85,13 +104,138 @@ __global__ void k_dense_seed(D* __restrict__ d, const int* __restrict__ seeds, i
   if (i < ns) d[seeds[i]] = value;
 }
 
+static void free_vec(maiter_batch* b) {
+  for (VGroup& G : b->vg) {
+    cudaFree(G.a.v);
+    cudaFree(G.a.delta);
+    cudaFree(G.a.msg[0]);
+    cudaFree(G.a.msg[1]);
+    cudaFree(const_cast<float*>(G.a.inv_deg));
+    cudaFree(G.a.lacc);
+    cudaFree(G.a.lcnt);
+    cudaFree(G.a.ctl);
+    cudaFree(G.d_seeds);
+    cudaFree(G.d_seedval);
+  }
+  b->vg.clear();
+  b->q_group.clear();
+  b->q_slot.clear();
+  if (b->h_vctl) cudaFreeHost(b->h_vctl);
+  b->h_vctl = nullptr;
+}
+
 static void free_dense(maiter_batch* b) {
+  free_vec(b);
   for (maiter_result* r : b->qres) maiter_result_destroy(r);
   b->qres.clear();
   cudaFree(b->d_qseeds);
   b->d_qseeds = nullptr;
   if (b->h_ctls) cudaFreeHost(b->h_ctls);
   b->h_ctls = nullptr;
+}
+
+// Mode 3: the seeds, damping and tolerances of every group's slots (also on
+// a rerun with new values), into each group's seed arrays and initial
+// control block.
+static maiter_status vec_values(maiter_batch* b, const maiter_query* qs) {
+  for (VGroup& G : b->vg) {
+    VCtl c{};
+    for (int s = 0; s < kVQ; ++s) c.conv_round[s] = -1;
+    c.nq = G.nq;
+    std::vector<int2> seeds;
+    std::vector<float> vals;
+    for (int s = 0; s < G.nq; ++s) {
+      const maiter_query& Q = qs[G.q[s]];
+      // half of the query's tolerance for the termination test, half left
+      // to the FP32 rounding of its deltas and messages
+      c.eps[s] = kVecEpsFrac * Q.eps;
+      c.dq[s] = static_cast<float>(Q.damping);
+      c.dq_lo[s] = static_cast<float>(Q.damping - static_cast<double>(c.dq[s]));
+      const float init = static_cast<float>((1.0 - Q.damping) / static_cast<double>(Q.num_seeds));
+      for (int i = 0; i < Q.num_seeds; ++i) {
+        seeds.push_back(make_int2(s, Q.seeds[i]));
+        vals.push_back(init);
+      }
+    }
+    G.init = c;
+    if (static_cast<int>(seeds.size()) != G.nseeds) {
+      cudaFree(G.d_seeds);
+      cudaFree(G.d_seedval);
+      G.d_seeds = nullptr;
+      G.d_seedval = nullptr;
+      MAITER_CUDA(cudaMalloc(&G.d_seeds, sizeof(int2) * std::max<size_t>(seeds.size(), 1)));
+      MAITER_CUDA(cudaMalloc(&G.d_seedval, sizeof(float) * std::max<size_t>(vals.size(), 1)));
+      G.nseeds = static_cast<int>(seeds.size());
+    }
+    MAITER_CUDA(cudaMemcpy(G.d_seeds, seeds.data(), sizeof(int2) * seeds.size(), cudaMemcpyHostToDevice));
+    MAITER_CUDA(cudaMemcpy(G.d_seedval, vals.data(), sizeof(float) * vals.size(), cudaMemcpyHostToDevice));
+  }
+  return MAITER_OK;
+}
+
+// Mode 3: personalised-PageRank queries grouped kVQ at a time per graph, and
+// each group's query-minor state, messages and large-row accumulators.
+static maiter_status vec_setup(maiter_batch* b, const maiter_query* qs) {
+  const int nq = b->nq;
+  b->q_group.assign(nq, -1);
+  b->q_slot.assign(nq, -1);
+  for (int gi = 0; gi < b->ng; ++gi) {
+    for (int q = 0; q < nq; ++q) {
+      if (qs[q].graph != gi || qs[q].op != MAITER_OP_SUM_F64) continue;
+      if (b->vg.empty() || b->vg.back().graph != gi || b->vg.back().nq == kVQ) {
+        b->vg.emplace_back();
+        b->vg.back().graph = gi;
+      }
+      VGroup& G = b->vg.back();
+      b->q_group[q] = static_cast<int>(b->vg.size()) - 1;
+      b->q_slot[q] = G.nq;
+      G.q[G.nq++] = q;
+    }
+  }
+  for (VGroup& G : b->vg) {
+    const maiter_graph* g = b->graphs[G.graph];
+    maiter_status s = ensure_pull(g, nullptr);
+    if (s != MAITER_OK) return s;
+    const PullLayout* L = g->pull;
+    const size_t nv = static_cast<size_t>(std::max<int64_t>(g->n, 1)) * kVQ;
+    PullVArgs& a = G.a;
+    a.n = static_cast<int>(g->n);
+    a.crp = L->crp;
+    a.csrc = L->csrc;
+    a.large = L->large;
+    a.large_nch = L->large_nch;
+    a.lbits = L->lbits;
+    a.nlarge = L->nlarge;
+    float* inv = nullptr;
+    cudaError_t e = cudaMalloc(&a.v, sizeof(double) * nv);
+    if (e == cudaSuccess) e = cudaMalloc(&a.delta, sizeof(float) * nv);
+    if (e == cudaSuccess) e = cudaMalloc(&a.msg[0], sizeof(float) * nv);
+    if (e == cudaSuccess) e = cudaMalloc(&a.msg[1], sizeof(float) * nv);
+    if (e == cudaSuccess) e = cudaMalloc(&inv, sizeof(float) * std::max<int64_t>(g->n, 1));
+    if (e == cudaSuccess)
+      e = cudaMalloc(&a.lacc, sizeof(double) * kVQ * std::max(L->nlrows, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&a.lcnt, sizeof(unsigned) * std::max(L->nlrows, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&a.ctl, sizeof(VCtl));
+    if (e == cudaSuccess)
+      e = cudaMemset(a.lacc, 0, sizeof(double) * kVQ * std::max(L->nlrows, 1));
+    if (e == cudaSuccess) e = cudaMemset(a.lcnt, 0, sizeof(unsigned) * std::max(L->nlrows, 1));
+    a.inv_deg = inv;
+    if (e != cudaSuccess) {
+      set_error("batch allocation failed: %s", cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? MAITER_ERR_OOM : MAITER_ERR_CUDA;
+    }
+    if (g->n > 0) k_vec_inv_deg<<<g->num_sms * 4, 256>>>(g->rp, static_cast<int>(g->n), inv);
+    MAITER_CUDA(cudaGetLastError());
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vec_pull, kVBlock, 0);
+    G.pull_grid = g->num_sms * std::max(per_sm, 1);
+    G.prime_grid = std::max(1, std::min(static_cast<int>((g->n + 7) / 8), g->num_sms * 4));
+    G.init_grid = std::max(1, std::min(static_cast<int>((static_cast<int64_t>(g->n) * kVQ + 255) / 256),
+                                       g->num_sms * 8));
+  }
+  MAITER_CUDA(cudaMallocHost(&b->h_vctl, sizeof(VCtl) * std::max<size_t>(b->vg.size(), 1)));
+  MAITER_CUDA(cudaDeviceSynchronize());
+  return vec_values(b, qs);
 }
 
 static maiter_status dense_setup(maiter_batch* b, const maiter_query* qs) {
@@ -102,8 +246,11 @@ static maiter_status dense_setup(maiter_batch* b, const maiter_query* qs) {
   std::vector<int> flat;
   for (int q = 0; q < nq; ++q) {
     const maiter_graph* g = b->graphs[qs[q].graph];
-    maiter_status s = alloc_result(g, qs[q].op, &b->qres[q]);
-    if (s != MAITER_OK) return s;
+    // mode 3 runs the personalised-PageRank queries in groups (vec_setup)
+    if (!(b->mode == 3 && qs[q].op == MAITER_OP_SUM_F64)) {
+      maiter_status s = alloc_result(g, qs[q].op, &b->qres[q]);
+      if (s != MAITER_OK) return s;
+    }
     b->seed_off[q] = static_cast<int>(flat.size());
     b->seed_cnt[q] = qs[q].num_seeds;
     flat.insert(flat.end(), qs[q].seeds, qs[q].seeds + qs[q].num_seeds);
@@ -113,7 +260,84 @@ static maiter_status dense_setup(maiter_batch* b, const maiter_query* qs) {
   MAITER_CUDA(cudaMallocHost(&b->h_ctls, sizeof(DevCtl) * nq));
   MAITER_CUDA(cudaEventCreate(&b->ev0));
   MAITER_CUDA(cudaEventCreate(&b->ev1));
+  if (b->mode == 3) return vec_setup(b, qs);
   return MAITER_OK;
+}
+
+// Mode 3: a group's branch, init -> seeds -> prime -> WHILE(h) { (decide ;
+// pull) x 3 }, after `dep` (none: nullptr).
+static maiter_status vec_add(cudaGraph_t graph, const VGroup& G, const VCtl& init,
+                             cudaGraphNode_t* last) {
+  PullVArgs a = G.a;
+  VCtl ci = init;
+  void* a1[] = {&a, &ci};
+  cudaKernelNodeParams k1{};
+  k1.func = reinterpret_cast<void*>(&k_vec_init);
+  k1.gridDim = dim3(G.init_grid);
+  k1.blockDim = dim3(256);
+  k1.kernelParams = a1;
+  cudaGraphNode_t n1, n2, n3, n4;
+  MAITER_CUDA(cudaGraphAddKernelNode(&n1, graph, nullptr, 0, &k1));
+  const int2* seeds = G.d_seeds;
+  const float* vals = G.d_seedval;
+  int ns = G.nseeds;
+  void* a2[] = {&a, &seeds, &vals, &ns};
+  cudaKernelNodeParams k2{};
+  k2.func = reinterpret_cast<void*>(&k_vec_seed);
+  k2.gridDim = dim3(std::max(1, (ns + 255) / 256));
+  k2.blockDim = dim3(256);
+  k2.kernelParams = a2;
+  MAITER_CUDA(cudaGraphAddKernelNode(&n2, graph, &n1, 1, &k2));
+  void* a3[] = {&a};
+  cudaKernelNodeParams k3{};
+  k3.func = reinterpret_cast<void*>(&k_vec_prime);
+  k3.gridDim = dim3(G.prime_grid);
+  k3.blockDim = dim3(kVBlock);
+  k3.kernelParams = a3;
+  MAITER_CUDA(cudaGraphAddKernelNode(&n3, graph, &n2, 1, &k3));
+  cudaGraphConditionalHandle h;
+  MAITER_CUDA(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  MAITER_CUDA(cudaGraphAddNode(&n4, graph, &n3, nullptr, 1, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t cap;
+  MAITER_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    for (int u = 0; u < 3; ++u) {
+      cudaLaunchConfig_t cfg{};
+      cfg.stream = cap;
+      cfg.attrs = attr;
+      cfg.gridDim = dim3(1);
+      cfg.blockDim = dim3(kVQ);
+      cfg.numAttrs = u > 0 ? 1 : 0;
+      cudaLaunchKernelEx(&cfg, k_vec_decide, a.ctl, h, 1);
+      cfg.gridDim = dim3(G.pull_grid);
+      cfg.blockDim = dim3(kVBlock);
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, k_vec_pull, a);
+    }
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cap, &captured);
+  }
+  cudaStreamDestroy(cap);
+  MAITER_CUDA(e);
+  *last = n4;
+  return MAITER_OK;
+}
+
+static VCtl vec_init(const VGroup& G, const maiter_batch_params* p) {
+  VCtl c = G.init;
+  c.max_rounds = p->max_rounds > 0 ? p->max_rounds : 1000000;
+  return c;
 }
 
 template <class Op>
@@ -181,7 +405,13 @@ static maiter_status dense_build(maiter_batch* b, const maiter_batch_params* p,
   // stopped (its initialisation, which touches only its own buffers, may run
   // earlier)
   cudaGraphNode_t prev = nullptr;
+  for (const VGroup& G : b->vg) {
+    cudaGraphNode_t last;
+    maiter_status s = vec_add(b->graph, G, vec_init(G, p), &last);
+    if (s != MAITER_OK) return s;
+  }
   for (int q = 0; q < b->nq; ++q) {
+    if (!b->qres[q]) continue;   // in a mode-3 group
     const BQuery& Q = b->hq[q];
     const DevCtl init = dense_ctl(Q, p, eps[q]);
     cudaGraphNode_t deps[2], wnode;
@@ -430,7 +660,31 @@ static maiter_status dense_run(maiter_batch* b, const maiter_batch_params* p,
     // queries one after another, each host-driven with events per kernel
     cudaEvent_t e[3];
     for (auto& x : e) MAITER_CUDA(cudaEventCreate(&x));
+    for (const VGroup& G : b->vg) {
+      // a group host-driven: events around each pull
+      k_vec_init<<<G.init_grid, 256, 0, st>>>(G.a, vec_init(G, p));
+      k_vec_seed<<<std::max(1, (G.nseeds + 255) / 256), 256, 0, st>>>(G.a, G.d_seeds, G.d_seedval,
+                                                                        G.nseeds);
+      k_vec_prime<<<G.prime_grid, kVBlock, 0, st>>>(G.a);
+      for (;;) {
+        k_vec_decide<<<1, kVQ, 0, st>>>(G.a.ctl, cudaGraphConditionalHandle{}, 0);
+        k_hold<<<1, 32, 0, st>>>(kHoldNs);
+        MAITER_CUDA(cudaEventRecord(e[0], st));
+        k_vec_pull<<<G.pull_grid, kVBlock, 0, st>>>(G.a);
+        MAITER_CUDA(cudaEventRecord(e[1], st));
+        MAITER_CUDA(cudaGetLastError());
+        VCtl* hc = b->h_vctl;
+        MAITER_CUDA(cudaMemcpyAsync(hc, G.a.ctl, sizeof(VCtl), cudaMemcpyDeviceToHost, st));
+        MAITER_CUDA(cudaStreamSynchronize(st));
+        if (hc->status != 0) break;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e[0], e[1]);
+        s.push_ms += t;
+        s.push_launches++;
+      }
+    }
     for (int q = 0; q < b->nq; ++q) {
+      if (!b->qres[q]) continue;   // in a mode-3 group
       const BQuery& Q = b->hq[q];
       maiter_result* r = b->qres[q];
       const maiter_graph* g = b->graphs[Q.graph];
@@ -459,14 +713,33 @@ static maiter_status dense_run(maiter_batch* b, const maiter_batch_params* p,
   }
   MAITER_CUDA(cudaEventRecord(b->ev1, st));
   for (int q = 0; q < b->nq; ++q)
-    MAITER_CUDA(cudaMemcpyAsync(b->h_ctls + q, b->qres[q]->ctl, sizeof(DevCtl),
+    if (b->qres[q])
+      MAITER_CUDA(cudaMemcpyAsync(b->h_ctls + q, b->qres[q]->ctl, sizeof(DevCtl),
+                                  cudaMemcpyDeviceToHost, st));
+  for (size_t i = 0; i < b->vg.size(); ++i)
+    MAITER_CUDA(cudaMemcpyAsync(b->h_vctl + i, b->vg[i].a.ctl, sizeof(VCtl),
                                 cudaMemcpyDeviceToHost, st));
   MAITER_CUDA(cudaStreamSynchronize(st));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, b->ev0, b->ev1);
   s.elapsed_ms = ms;
   int worst = 1;
+  for (size_t i = 0; i < b->vg.size(); ++i) {
+    const VCtl& h = b->h_vctl[i];
+    const VGroup& G = b->vg[i];
+    const maiter_graph* g = b->graphs[G.graph];
+    s.rounds = std::max<int64_t>(s.rounds, static_cast<int64_t>(h.rounds));
+    // every round updates every vertex of every slot in use
+    s.activations += static_cast<int64_t>(h.rounds) * g->n * G.nq;
+    s.edge_pushes += static_cast<int64_t>(h.rounds) * g->m * G.nq;
+    // init, seeds, prime, then per round a decision and a pull (the graph
+    // runs whole passes of three rounds; profiling adds a hold per round)
+    const int64_t ran = static_cast<int64_t>(h.rounds) + 1;
+    s.kernel_launches += 3 + (profile ? 3 * ran : 2 * 3 * ((ran + 2) / 3));
+    if (h.status != 1) worst = h.status;
+  }
   for (int q = 0; q < b->nq; ++q) {
+    if (!b->qres[q]) continue;
     const DevCtl& h = b->h_ctls[q];
     s.rounds = std::max<int64_t>(s.rounds, static_cast<int64_t>(h.rounds));
     s.activations += static_cast<int64_t>(h.activations);
@@ -611,8 +884,7 @@ maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_gr
   MAITER_REQUIRE(p->cut_large >= 0 && p->chunk >= 0 && (p->chunk == 0 || p->chunk >= 32),
                  "cut_large >= 0 and chunk = 0 or >= 32");
   MAITER_REQUIRE((p->flags & ~MAITER_FLAG_PROFILE_KERNELS) == 0, "unknown flags 0x%x", p->flags);
-  MAITER_REQUIRE((p->mode == 0 || p->mode == 1 || p->mode == 2) && p->reserved == 0,
-                 "mode must be 0, 1 or 2");
+  MAITER_REQUIRE(p->mode >= 0 && p->mode <= 3 && p->reserved == 0, "mode must be 0, 1, 2 or 3");
   for (int q = 0; q < num_queries; ++q) {
     const maiter_query& Q = queries[q];
     MAITER_REQUIRE(Q.graph >= 0 && Q.graph < num_graphs, "query %d: graph %d out of range", q, Q.graph);
@@ -669,6 +941,10 @@ maiter_status maiter_run_batch(const maiter_graph* const* graphs, int32_t num_gr
       flat.insert(flat.end(), Q.seeds, Q.seeds + Q.num_seeds);
     }
     MAITER_CUDA(cudaMemcpy(b->d_qseeds, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice));
+    if (b->mode == 3) {
+      maiter_status s = vec_values(b, queries);
+      if (s != MAITER_OK) return s;
+    }
   } else {
     // same shape: refresh thresholds, seeds and damping
     b->hseeds.clear();
@@ -707,7 +983,12 @@ maiter_status maiter_batch_get_state(const maiter_batch* b, int32_t query, void*
   DeviceGuard guard(b->device);
   const BQuery& q = b->hq[query];
   const size_t bytes = (q.op == 0 ? sizeof(double) : sizeof(uint32_t)) * count;
-  if (b->mode != 1)
+  if (b->mode == 3 && b->q_group[query] >= 0) {
+    // the query's column of its group's query-minor state
+    const VGroup& G = b->vg[b->q_group[query]];
+    MAITER_CUDA(cudaMemcpy2D(out, sizeof(double), G.a.v + b->q_slot[query], sizeof(double) * kVQ,
+                             sizeof(double), static_cast<size_t>(count), cudaMemcpyDefault));
+  } else if (b->mode != 1)
     MAITER_CUDA(cudaMemcpy(out, b->qres[query]->v, bytes, cudaMemcpyDefault));
   else if (q.op == 0)
     MAITER_CUDA(cudaMemcpy(out, b->v_sum + q.off, bytes, cudaMemcpyDefault));
@@ -728,8 +1009,12 @@ maiter_status maiter_batch_query_rounds(const maiter_batch* b, int32_t* out, int
   MAITER_REQUIRE(b && out && count == b->nq, "need num_queries entries");
   DeviceGuard guard(b->device);
   if (b->mode != 1) {
-    // dense: the rounds each query's own loop ran (its control block)
-    for (int q = 0; q < count; ++q) out[q] = static_cast<int32_t>(b->h_ctls[q].rounds);
+    // dense: the rounds each query's own loop ran (its control block); a
+    // mode-3 query: the round at which its residual fell below its eps
+    for (int q = 0; q < count; ++q)
+      out[q] = (b->mode == 3 && b->q_group[q] >= 0)
+                   ? b->h_vctl[b->q_group[q]].conv_round[b->q_slot[q]]
+                   : static_cast<int32_t>(b->h_ctls[q].rounds);
     return MAITER_OK;
   }
   MAITER_CUDA(cudaMemcpy(out, b->qlast, sizeof(int32_t) * count, cudaMemcpyDeviceToHost));

@@ -62,7 +62,23 @@ struct Tuning {
 
 namespace maiter {
 struct BinLayout;   // binned engine: the edges by (sender cell, receiver bin)
-struct PullLayout;  // receive-side engine: the transpose and its chunk list
+
+// Receive-side engine: the transpose of a graph and its chunk list for rows of
+// high in-degree (pull_engine.cu builds it; the batch engine reads it too).
+struct PullLayout {
+  bool valid = false;
+  int nlarge = 0;          // chunk entries
+  int nlrows = 0;          // rows cut into chunks
+  int* crp = nullptr;      // n + 1: offsets of the small rows' in-edges
+  int* csrc = nullptr;     // m: small rows' in-edges, then the large rows' (tail)
+  unsigned char* crow = nullptr;   // m: row within its group of every in-edge
+  unsigned* lbits = nullptr;       // ceil(n / 32) large-row flags
+  int4* large = nullptr;   // nlarge entries
+  int* large_nch = nullptr;
+  double* lacc = nullptr;
+  unsigned* lcnt = nullptr;
+  size_t crp_cap = 0, csrc_cap = 0, crow_cap = 0, lbits_cap = 0, large_cap = 0, lrow_cap = 0;
+};
 }
 
 struct maiter_graph {
@@ -142,4 +158,6 @@ maiter_status run_pull(const maiter_graph* g, const maiter_run_params* p, maiter
                        cudaStream_t st);
 void free_pull(maiter_graph* g);
 void invalidate_pull(maiter_graph* g);
+// Builds (or rebuilds after an update) the transpose of g on stream st.
+maiter_status ensure_pull(const maiter_graph* g, cudaStream_t st);
 }  // namespace maiter

@@ -12,21 +12,6 @@
 
 namespace maiter {
 
-struct PullLayout {
-  bool valid = false;
-  int nlarge = 0;          // chunk entries
-  int nlrows = 0;          // rows cut into chunks
-  int* crp = nullptr;      // n + 1: offsets of the small rows' in-edges
-  int* csrc = nullptr;     // m: small rows' in-edges, then the large rows' (tail)
-  unsigned char* crow = nullptr;   // m: row within its group of every in-edge
-  unsigned* lbits = nullptr;       // ceil(n / 32) large-row flags
-  int4* large = nullptr;   // nlarge entries
-  int* large_nch = nullptr;
-  double* lacc = nullptr;
-  unsigned* lcnt = nullptr;
-  size_t crp_cap = 0, csrc_cap = 0, crow_cap = 0, lbits_cap = 0, large_cap = 0, lrow_cap = 0;
-};
-
 void free_pull(maiter_graph* g) {
   if (!g->pull) return;
   PullLayout* L = g->pull;

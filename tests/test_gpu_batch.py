@@ -50,7 +50,7 @@ def check(mt, graphs, queries, b):
             assert oracle.relative_error(v, vstar) <= 1e-6, qi
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_batch_mixed_queries_uneven_graphs(mt, mode):
     graphs, queries = make_batch([8, 10, 11, 12], n_ppr=6, n_sssp=3)
     G = [mt.Graph.from_csr(g) for g in graphs]
@@ -63,7 +63,7 @@ def test_batch_mixed_queries_uneven_graphs(mt, mode):
     assert (qr >= 0).all() and qr.max() <= st["rounds"] and (qr > 0).sum() > len(queries) // 2
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_batch_reuse_gives_the_same_answer(mt, mode):
     graphs, queries = make_batch([9, 11], n_ppr=4, n_sssp=2, seed=3)
     G = [mt.Graph.from_csr(g) for g in graphs]
@@ -78,7 +78,7 @@ def test_batch_reuse_gives_the_same_answer(mt, mode):
             assert oracle.relative_error(b.state(i), first[i]) <= 1e-6
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_batch_multi_source_sssp_and_hub_chunks(mt, mode):
     # a star hub (chunked path) plus an R-MAT graph; a two-seed SSSP query
     n = 6000
@@ -144,3 +144,36 @@ def test_chained_mode_runs_queries_one_after_another(mt):
     for i in range(len(src)):
         np.testing.assert_array_equal(b2.state(i), b0.state(i))
     assert b2.stats()["converged"] == 1
+
+
+def test_pull_groups_of_64_queries(mt):
+    # mode 3: 70 personalised-PageRank queries on one graph (a full group of
+    # 64 and a group of 6) and 40 on another, with different damping factors
+    # in one group, and SSSP queries on their own branches
+    g1 = graphgen.rmat(10, 8, weights=True, seed=41)
+    g2 = graphgen.rmat(9, 8, weights=True, seed=42)
+    queries = []
+    for gi, (g, count) in enumerate([(g1, 70), (g2, 40)]):
+        for q, S in enumerate(graphgen.ppr_seed_sets(g.n, count, seed=50 + gi, max_size=8)):
+            d = 0.85 if q % 3 == 0 else D
+            queries.append(dict(op=0, graph=gi, seeds=S, damping=d, eps=1e-6 * (1 - d) ** 2 / len(S)))
+        queries.append(dict(op=2, graph=gi, seeds=[int(graphgen.sssp_sources(g, 1)[0])]))
+    G = [mt.Graph.from_csr(g1), mt.Graph.from_csr(g2)]
+    b = mt.run_batch(G, queries, mode=3)
+    graphs = [g1, g2]
+    for qi, q in enumerate(queries):
+        g = graphs[q["graph"]]
+        if q["op"] == 2:
+            np.testing.assert_array_equal(b.state(qi), oracle.dijkstra(g, int(q["seeds"][0])))
+        else:
+            vstar = oracle.pagerank(g, q["damping"], seeds=q["seeds"])
+            assert oracle.relative_error(b.state(qi), vstar) <= 1e-6, qi
+    st = b.stats()
+    qr = b.query_rounds()
+    assert st["converged"] == 1 and (qr >= 1).all() and qr.max() <= st["rounds"]
+    # profiling mode: the same answers, host-driven
+    bp = mt.run_batch(G, queries, mode=3, flags=mt.FLAG_PROFILE_KERNELS)
+    assert bp.stats()["push_launches"] > 0
+    for qi, q in enumerate(queries):
+        if q["op"] == 0:
+            assert oracle.relative_error(bp.state(qi), b.state(qi)) <= 1e-6

@@ -4,7 +4,8 @@ against the oracle.
 Batch: 512 personalised-PageRank queries (seed sets of 1-64 vertices,
 log-uniform sizes) and 128 SSSP sources over 8 R-MAT graphs of scales 16-22
 (edge factor 16), exactly as the bench builds them, run in the dense mode
-(the autotuner's pick on a B300) and in the chained dense mode.  SSSP answers
+(the autotuner's pick on a B300), in the chained dense mode and with the
+PageRank queries in receive-side groups (mode 3).  SSSP answers
 are compared bit for bit with Dijkstra.  PPR answers are bounded by the
 oracle's one-step residual r = c + P^T v - v: ||v* - v||_1 <= ||r||_1 / (1 - d),
 divided by max v for the norm-wise relative error (<= 1e-6).
@@ -90,6 +91,35 @@ def test_batch_full_config_against_the_oracle(mt, c4, mode):
     worst = check_batch(graphs, queries, b, dijkstra, coefs)
     print(f"mode {mode}: {st['elapsed_ms']:.1f} ms, worst PPR bound {worst:.2e}")
     b.close()
+
+
+def test_batch_full_config_pull_groups(mt, c4):
+    # mode 3 (FP32 deltas): SSSP bit for bit; each PPR state bounded through
+    # an FP64 mode-0 state of the same query run to eps_q / 100 and that
+    # state's own residual bound (the L1 residual of an FP32-delta state sums
+    # the rounding of every vertex; a reference stopped at eps_q would spend
+    # the whole 1e-6 on its own bound)
+    graphs, queries, G, dijkstra, coefs = c4
+    tight = [dict(q, eps=q["eps"] / 100) if q["op"] == 0 else q for q in queries]
+    b0 = mt.run_batch(G, tight, mode=0)
+    b3 = mt.run_batch(G, queries, mode=3)
+    assert b3.stats()["converged"] == 1
+    worst = 0.0
+    for i, q in enumerate(queries):
+        v3 = b3.state(i)
+        if q["op"] == 2:
+            np.testing.assert_array_equal(v3, dijkstra[i], err_msg=f"SSSP query {i}")
+            continue
+        g = graphs[q["graph"]]
+        v0 = b0.state(i)
+        r = oracle.linear_residual(g, coefs[q["graph"]], oracle.pagerank_c(g.n, D, q["seeds"]), v0)
+        e = float(np.abs(v3 - v0).max() / v0.max() + np.abs(r).sum() / (1 - D) / v0.max())
+        assert e <= 1e-6, f"PPR query {i}: norm-wise error bound {e}"
+        worst = max(worst, e)
+    print(f"mode 3: {b3.stats()['elapsed_ms']:.1f} ms against {b0.stats()['elapsed_ms']:.1f} ms "
+          f"for mode 0, worst PPR bound {worst:.2e}")
+    b0.close()
+    b3.close()
 
 
 @pytest.fixture(scope="module")
