@@ -512,7 +512,7 @@ def run_pagerank(args, wl, dist=None, nested=None):
             "32-bit loads", f"k_pull_pagerank_f32_rmat{cfg['scale']}",
             "achieved = algorithmic bytes (12 B per FP32 message, 32 B per update, the same "
             "definition as the push's) / device time of the pull launches")
-        push_roofline = kernel_roofline(
+        push_roofline = None if "mixed_sync" not in variants else kernel_roofline(
             variants["mixed_sync"], "k_push<OpSumMixed> (warm-up rounds k_push<OpSumWarm>)",
             mt.PROBE_RED_F32, "f32 atomicAdd", f"k_push_pagerank_mixed_rmat{cfg['scale']}",
             "achieved = algorithmic bytes of the push (12 B per FP32 message, 32 B per update; "
@@ -1051,6 +1051,10 @@ def _jacobi_system(n, per_row, seed):
 
 
 ROW_WORKLOADS = ["sssp-f32-lognormal20", "components-rmat20", "jacobi-2e20"]
+# default step counts of the millisecond-scale workloads (0.4-5 ms a step): a
+# timed region of about 0.2-0.5 s, several periods of the 50 ms clock sampler
+SHORT_STEPS = {"pagerank-rmat13": 200, "components-rmat20": 500, "jacobi-2e20": 100,
+               "sssp-f32-lognormal20": 60, "sssp-rmat20": 60}
 
 
 def run_row(args, name):
@@ -1240,7 +1244,10 @@ def run_row(args, name):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 10; the millisecond-scale workloads "
+                         "default to enough steps for a timed region of a few tenths of a "
+                         "second, so that the clock sampler sees it)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1258,6 +1265,8 @@ def main():
                     help="pagerank-mixed-rmat24 (default: PageRank, mixed precision, R-MAT "
                          "scale 24, with the SSSP scale-20 record nested) or another workload")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = SHORT_STEPS.get(args.workload, 10) if args.impl == "ours" else 10
     if args.impl == "reference":
         run_reference(args)
         return

@@ -110,7 +110,7 @@ static void free_vec(maiter_batch* b) {
     cudaFree(G.a.delta);
     cudaFree(G.a.msg[0]);
     cudaFree(G.a.msg[1]);
-    cudaFree(const_cast<float*>(G.a.inv_deg));
+    cudaFree(const_cast<float2*>(G.a.inv_deg));
     cudaFree(G.a.lacc);
     cudaFree(G.a.lcnt);
     cudaFree(G.a.ctl);
@@ -202,16 +202,18 @@ static maiter_status vec_setup(maiter_batch* b, const maiter_query* qs) {
     a.n = static_cast<int>(g->n);
     a.crp = L->crp;
     a.csrc = L->csrc;
+    a.sbase = L->sbase;
+    a.smask = L->smask;
     a.large = L->large;
     a.large_nch = L->large_nch;
     a.lbits = L->lbits;
     a.nlarge = L->nlarge;
-    float* inv = nullptr;
+    float2* inv = nullptr;
     cudaError_t e = cudaMalloc(&a.v, sizeof(double) * nv);
     if (e == cudaSuccess) e = cudaMalloc(&a.delta, sizeof(float) * nv);
     if (e == cudaSuccess) e = cudaMalloc(&a.msg[0], sizeof(float) * nv);
     if (e == cudaSuccess) e = cudaMalloc(&a.msg[1], sizeof(float) * nv);
-    if (e == cudaSuccess) e = cudaMalloc(&inv, sizeof(float) * std::max<int64_t>(g->n, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&inv, sizeof(float2) * std::max<int64_t>(g->n, 1));
     if (e == cudaSuccess)
       e = cudaMalloc(&a.lacc, sizeof(double) * kVQ * std::max(L->nlrows, 1));
     if (e == cudaSuccess) e = cudaMalloc(&a.lcnt, sizeof(unsigned) * std::max(L->nlrows, 1));

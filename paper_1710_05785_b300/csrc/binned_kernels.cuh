@@ -212,7 +212,11 @@ __global__ void __launch_bounds__(256) k_bin_prime(BinArgs a, const double* __re
 // (-1: a round after the stopping one in the same pass; nothing is recorded).
 __device__ __forceinline__ int bin_decide(DevCtl* ctl, cudaGraphConditionalHandle cond,
                                           int use_cond) {
-  if (ctl->status != 0) return -1;
+  if (ctl->status != 0) {
+    // stopped before (by this test or by a kernel's error status): the loop ends
+    if (blockIdx.x == 0 && use_cond) cudaGraphSetConditional(cond, 0u);
+    return -1;
+  }
   const unsigned ps = ctl->push_set;
   const double resid = ctl->resid_acc[ps];
   const unsigned long long act = ctl->act_acc[ps], psh = ctl->push_acc[ps];

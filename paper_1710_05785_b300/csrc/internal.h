@@ -77,7 +77,12 @@ struct PullLayout {
   int* large_nch = nullptr;
   double* lacc = nullptr;
   unsigned* lcnt = nullptr;
-  size_t crp_cap = 0, csrc_cap = 0, crow_cap = 0, lbits_cap = 0, large_cap = 0, lrow_cap = 0;
+  // message slots by sender rank (senders: the vertices of out-degree > 0)
+  int nsend = 0;
+  int* sbase = nullptr;            // ceil(n / 32): senders before every word of 32 rows
+  unsigned* smask = nullptr;       // ceil(n / 32): the word's senders, one bit per row
+  size_t crp_cap = 0, csrc_cap = 0, crow_cap = 0, lbits_cap = 0, large_cap = 0, lrow_cap = 0,
+         sbase_cap = 0, smask_cap = 0;
 };
 }
 

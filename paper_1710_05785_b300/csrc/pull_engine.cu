@@ -5,6 +5,7 @@
 // condition set by the decision kernel (no host round trip per round).
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "internal.h"
 #include "pull_kernels.cuh"
@@ -23,6 +24,8 @@ void free_pull(maiter_graph* g) {
   cudaFree(L->large_nch);
   cudaFree(L->lacc);
   cudaFree(L->lcnt);
+  cudaFree(L->sbase);
+  cudaFree(L->smask);
   delete L;
   g->pull = nullptr;
 }
@@ -45,6 +48,33 @@ cudaError_t grow(T** p, size_t* cap, size_t need) {
   return e;
 }
 
+// Sender masks and ranks of g (every vertex of out-degree > 0 gets the next
+// message slot in id order); L->nsend the number of senders.
+cudaError_t sender_ranks(const maiter_graph* g, PullLayout* L, cudaStream_t st) {
+  const int64_t n = g->n;
+  const int nwords = static_cast<int>(std::max<int64_t>((n + 31) / 32, 1));
+  const int ntiles = (nwords + kPullScanTile - 1) / kPullScanTile;
+  L->nsend = 0;
+  cudaError_t e = grow(&L->sbase, &L->sbase_cap, static_cast<size_t>(nwords));
+  if (e == cudaSuccess) e = grow(&L->smask, &L->smask_cap, static_cast<size_t>(nwords));
+  if (e != cudaSuccess || n == 0) return e;
+  int4* sums = nullptr;
+  e = cudaMalloc(&sums, sizeof(int4) * (ntiles + 1));
+  int4 tot = make_int4(0, 0, 0, 0);
+  if (e == cudaSuccess) {
+    k_send_masks<<<g->num_sms * 4, 256, 0, st>>>(g->rp, static_cast<int>(n), L->smask);
+    k_send_tile_sums<<<ntiles, kPullScanBlock, 0, st>>>(L->smask, nwords, sums);
+    k_pull_scan_sums<<<1, kPullScanBlock, 0, st>>>(sums, ntiles);
+    k_send_offsets<<<ntiles, kPullScanBlock, 0, st>>>(L->smask, nwords, sums, L->sbase);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, sums + ntiles, sizeof(int4), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) L->nsend = tot.x;
+  cudaFree(sums);
+  return e;
+}
+
 }  // namespace
 
 // Builds (or rebuilds after an update) the transpose of g on stream st, on
@@ -61,8 +91,6 @@ maiter_status ensure_pull(const maiter_graph* cg, cudaStream_t st) {
   const int64_t nwords = (n + 31) / 32;
   const int ntiles = static_cast<int>((n + kPullScanTile - 1) / kPullScanTile);
   MAITER_CUDA(grow(&L->crp, &L->crp_cap, static_cast<size_t>(n + 1)));
-  MAITER_CUDA(grow(&L->csrc, &L->csrc_cap, static_cast<size_t>(m)));
-  MAITER_CUDA(grow(&L->crow, &L->crow_cap, static_cast<size_t>(m)));
   MAITER_CUDA(grow(&L->lbits, &L->lbits_cap, static_cast<size_t>(nwords)));
   const size_t n1 = static_cast<size_t>(std::max<int64_t>(n, 1));
   int* indeg = nullptr;
@@ -89,6 +117,13 @@ maiter_status ensure_pull(const maiter_graph* cg, cudaStream_t st) {
   }
   L->nlarge = totals.z;
   L->nlrows = totals.w;
+  // edge slots: the small rows' in-edges, the tail from the next multiple of
+  // 4 (each large row's part padded to a multiple of 4), and 16 slots of
+  // slack for the kernels' 4-slot loads that end past the last edge
+  const size_t slots = static_cast<size_t>((static_cast<int64_t>(totals.x) + 3) & ~int64_t{3}) +
+                       static_cast<size_t>(totals.y) + 16;
+  if (e == cudaSuccess) e = grow(&L->csrc, &L->csrc_cap, slots);
+  if (e == cudaSuccess) e = grow(&L->crow, &L->crow_cap, slots);
   if (e == cudaSuccess) e = grow(&L->large, &L->large_cap, static_cast<size_t>(totals.z));
   if (e == cudaSuccess) e = grow(&L->large_nch, &L->lrow_cap, static_cast<size_t>(totals.w));
   if (e == cudaSuccess) {
@@ -103,12 +138,13 @@ maiter_status ensure_pull(const maiter_graph* cg, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaMemsetAsync(L->lacc, 0, sizeof(double) * nl, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(L->lcnt, 0, sizeof(unsigned) * nl, st);
   }
+  if (e == cudaSuccess) e = sender_ranks(g, L, st);
   if (e == cudaSuccess && n > 0) {
     k_pull_offsets<<<ntiles, kPullScanBlock, 0, st>>>(indeg, static_cast<int>(n), sums, ntiles,
                                                        L->crp, first, L->lbits, L->large,
                                                        L->large_nch);
-    k_pull_place<<<g->num_sms * 8, 256, 0, st>>>(g->rp, g->col, static_cast<int>(n), first,
-                                                 L->csrc, L->crow);
+    k_pull_place<<<g->num_sms * 8, 256, 0, st>>>(g->rp, g->col, static_cast<int>(n), L->sbase,
+                                                 L->smask, first, L->csrc, L->crow);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -218,6 +254,8 @@ void setup_phase(PullPhase<DT, MT, CT>& ph, const maiter_graph* g, maiter_result
   a.msg[0] = r->bin_msg_v;
   a.msg[1] = r->pull_msg;
   a.cmsg = r->bin_cmsg;
+  a.sbase = L->sbase;
+  a.smask = L->smask;
   a.ctl = r->ctl;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pull<DT, MT>, kPullBlock, 0);
@@ -269,6 +307,8 @@ maiter_status run_pull(const maiter_graph* g, const maiter_run_params* p, maiter
   mix(reinterpret_cast<uintptr_t>(L->large));
   mix(reinterpret_cast<uintptr_t>(L->lacc));
   mix(reinterpret_cast<uintptr_t>(r->pull_msg));
+  mix(reinterpret_cast<uintptr_t>(L->sbase));
+  mix(reinterpret_cast<uintptr_t>(L->smask));
   if (!profile && (!r->exec || r->exec_key != key)) {
     if (r->exec) { cudaGraphExecDestroy(r->exec); r->exec = nullptr; }
     if (r->graph) { cudaGraphDestroy(r->graph); r->graph = nullptr; }

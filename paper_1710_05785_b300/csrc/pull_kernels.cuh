@@ -12,13 +12,21 @@
 //   crp, csrc - the transpose in CSR form: the senders of every receiver;
 //   receivers in groups of 32 consecutive vertices, one warp each: the
 //     in-edges of a group's rows are contiguous and each carries its row
-//     within the group (one byte), so every lane takes one edge per step and
-//     a segmented shuffle reduction sums each row's part of the step; rows
-//     with more than kPullCut in-edges keep their edges in a tail region
-//     after all the others and are
+//     within the group (one byte); every lane takes 4 consecutive edges per
+//     step (one 16-byte load of senders, one 4-byte load of rows), sums the
+//     runs of equal rows among them in registers, and one segmented shuffle
+//     scan over the lanes joins the runs that cross lanes; rows with more
+//     than kPullCut in-edges keep their edges in a tail region after all the
+//     others (each row's part starting at a multiple of 4 slots) and are
 //   cut into chunks of kPullChunk edges, one warp each: the warp's sum goes
 //     to an FP64 accumulator of the row by one atomic, and the warp that adds
-//     the row's last chunk folds the row.
+//     the row's last chunk folds the row;
+//   message slots: a round's messages are stored by sender rank (the
+//     vertices of out-degree > 0 in id order; in R-MAT graphs about half of
+//     all vertices), so that the two message arrays of a round, the one read
+//     at random and the one written, stay in L2 together; a vertex's rank is
+//     the count of senders before its word of 32 rows (sbase) plus the bits
+//     below it in the word's sender mask (smask).
 // A round is two kernels: k_pull_decide (one thread: the termination test of
 // Section 5.1 on the totals of the round before, shared with the binned
 // engine) and k_pull (sum, then fold: v_k <- v_k + Delta_k, Delta_k <- sum,
@@ -34,9 +42,14 @@
 namespace maiter {
 
 constexpr int kPullBlock = 256;
+// resident CTAs per SM the register budget allows (40 registers a thread for
+// FP32 messages, 64 for FP64 ones)
+template <class MT>
+constexpr int pull_min_blocks() { return sizeof(MT) == 4 ? 6 : 4; }
 constexpr int kPullCut = 256;       // in-edges of the largest row a group sums
 constexpr int kPullChunk = 1024;    // in-edges per chunk of a larger row
-constexpr int kPullSteps = 4;       // 32-edge steps of a group whose loads are issued together
+constexpr int kPullSteps = 2;       // 128-edge steps of a group whose loads are issued together
+constexpr int kPullLargeSteps = 2;  // 128-edge steps of a chunk whose loads are issued together
 
 struct PullArgs {
   int n;
@@ -46,7 +59,7 @@ struct PullArgs {
   const int* __restrict__ crp;            // n + 1: in-edge offsets of the small rows (a
                                           // large row has none here: its edges are in
                                           // the tail, reached through its chunks)
-  const int* __restrict__ csrc;           // m: sender of every in-edge
+  const int* __restrict__ csrc;           // sender rank of every in-edge
   const unsigned char* __restrict__ crow; // m: row of every small-row in-edge within its
                                           // group of 32 (k mod 32)
   const unsigned* __restrict__ lbits;     // ceil(n / 32): bit k mod 32 of word k / 32 set
@@ -59,10 +72,19 @@ struct PullArgs {
   double damping;
   double* v;                              // FP64 state
   void* delta;                            // DT[n]
-  void* msg[2];                           // MT[n] each: c_j Delta_j, alternating by set
+  void* msg[2];                           // MT[nsend] each: c_j Delta_j by sender rank,
+                                          // alternating by set
+  const int* __restrict__ sbase;          // ceil(n / 32): senders before every word of 32 rows
+  const unsigned* __restrict__ smask;     // ceil(n / 32): bit r set when row 32 w + r sends
   void* cmsg;                             // MT[n]: c_j in the message precision (prime)
   DevCtl* ctl;
 };
+
+// Message slot of sender k (out-degree > 0): its rank among the senders.
+__device__ __forceinline__ int sender_index(const int* __restrict__ sbase,
+                                            const unsigned* __restrict__ smask, int k) {
+  return __ldg(sbase + (k >> 5)) + __popc(__ldg(smask + (k >> 5)) & ((1u << (k & 31)) - 1u));
+}
 
 // Primes a phase: msg[ws][j] = c_j Delta_j and the totals of Delta into set
 // ws (as k_bin_prime, with the message buffer of the set).
@@ -93,7 +115,7 @@ __global__ void __launch_bounds__(256) k_pull_prime(PullArgs a, const double* __
     const MT cj = static_cast<MT>(c);
     cmsg[j] = cj;
     const MT m = (d != DT(0)) ? cj * static_cast<MT>(d) : MT(0);
-    msg[j] = m;
+    if (deg > 0) msg[sender_index(a.sbase, a.smask, j)] = m;
     resid += fabs(static_cast<double>(d));
     mass += static_cast<double>(deg) * fabs(static_cast<double>(m));
     act += (d != DT(0));
@@ -138,18 +160,73 @@ __device__ __forceinline__ void pull_fold(const PullArgs& a, MT* msg_out, int k,
   const int deg = __ldg(a.rp + k + 1) - __ldg(a.rp + k);
   const MT m = (dnew != DT(0)) ? __ldg(static_cast<const MT*>(a.cmsg) + k) * static_cast<MT>(dnew)
                                : MT(0);
-  msg_out[k] = m;
+  if (deg > 0) msg_out[sender_index(a.sbase, a.smask, k)] = m;
   resid += fabs(static_cast<double>(dnew));
   mass += static_cast<double>(deg) * fabs(static_cast<double>(m));
   act += (dnew != DT(0));
   push += (dnew != DT(0)) ? static_cast<unsigned long long>(deg) : 0ull;
 }
 
+__device__ __forceinline__ int int4_at(const int4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// One step of a group's warp over 128 slots, 4 consecutive ones per lane,
+// k[i] the row of slot i within the group (-1 before the group's first
+// edge, 32 from its end on: never written) and x[i] its message.  Rows are
+// non-decreasing along the slots, so a row's slots are contiguous: within a
+// lane, a run that is neither the lane's first (head) nor its last (tail)
+// run lies in this lane alone and is added to its row at once; the head runs
+// of lanes with the same first row are joined by a segmented suffix scan,
+// and the first lane of such a segment also takes the tail of the lane
+// before it when that tail is the same row.  Every row is added to by at
+// most one lane per step.
+template <class MT>
+__device__ __forceinline__ void pull_group_step(MT* s_row, int lane, const int (&k)[4],
+                                                const MT (&x)[4]) {
+  MT head = MT(0), run = x[0];
+  int rk = k[0];
+  bool split = false;
+#pragma unroll
+  for (int i = 1; i < 4; ++i) {
+    if (k[i] != rk) {
+      if (!split) head = run;
+      else if (rk >= 0 && rk < 32) s_row[rk] += run;   // a run inside the lane
+      split = true;
+      run = x[i];
+      rk = k[i];
+    } else {
+      run += x[i];
+    }
+  }
+  if (!split) head = run;
+  const MT tail = split ? run : MT(0);
+  const int f = k[0], l = k[3];
+  MT hv = head;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const MT y = __shfl_down_sync(0xffffffffu, hv, o);
+    const int fy = __shfl_down_sync(0xffffffffu, f, o);
+    if (lane + o < 32 && fy == f) hv += y;
+  }
+  const int fprev = __shfl_up_sync(0xffffffffu, f, 1);
+  const int lprev = __shfl_up_sync(0xffffffffu, l, 1);
+  const MT tprev = __shfl_up_sync(0xffffffffu, tail, 1);
+  const int fnext = __shfl_down_sync(0xffffffffu, f, 1);
+  if (lane == 0 || fprev != f) {
+    if (lane > 0 && lprev == f) hv += tprev;
+    if (f >= 0 && f < 32) s_row[f] += hv;
+  }
+  if (split && (lane == 31 || fnext != l) && l >= 0 && l < 32) s_row[l] += tail;
+}
+
 // One dense round: the large rows' chunks, then the groups of 32 rows, a
 // warp each (no block barrier).  Sums in the message precision within a
 // step, in MT per row across steps (FP64 across the large rows' chunks).
+// The edge streams are read once a round: evict-first in L2 (__ldcs), so
+// they do not push the message array (read at random) out of it.
 template <class DT, class MT>
-__global__ void __launch_bounds__(kPullBlock, 8) k_pull(PullArgs a) {
+__global__ void __launch_bounds__(kPullBlock, pull_min_blocks<MT>()) k_pull(PullArgs a) {
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();
   DevCtl* ctl = a.ctl;
@@ -164,17 +241,24 @@ __global__ void __launch_bounds__(kPullBlock, 8) k_pull(PullArgs a) {
   const int gw = blockIdx.x * (kPullBlock / 32) + wid;
   const int nw = gridDim.x * (kPullBlock / 32);
 
-  // large rows: a warp per chunk, the chunk's sum added to the row's FP64
-  // accumulator by one atomic; the warp that adds the last chunk folds the row
+  // large rows: a warp per chunk (its first slot a multiple of 4), the
+  // chunk's sum added to the row's FP64 accumulator by one atomic; the warp
+  // that adds the last chunk folds the row
   for (int c = gw; c < a.nlarge; c += nw) {
     const int4 ent = __ldg(a.large + c);
     MT x[4] = {MT(0), MT(0), MT(0), MT(0)};
-    for (int e = ent.y + lane; e < ent.z; e += 128) {
-      int src[4];
+    for (int e0 = ent.y + 4 * lane; e0 < ent.z; e0 += 128 * kPullLargeSteps) {
+      int4 src[kPullLargeSteps];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) src[u] = e + 32 * u < ent.z ? __ldcs(a.csrc + e + 32 * u) : -1;
+      for (int u = 0; u < kPullLargeSteps; ++u) {
+        const int e = e0 + 128 * u;
+        src[u] = e < ent.z ? __ldcs(reinterpret_cast<const int4*>(a.csrc + e)) : make_int4(0, 0, 0, 0);
+      }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) if (src[u] >= 0) x[u] += msg_in[src[u]];
+      for (int u = 0; u < kPullLargeSteps; ++u)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (e0 + 128 * u + i < ent.z) x[i] += msg_in[int4_at(src[u], i)];
     }
     double t = static_cast<double>(x[0]) + static_cast<double>(x[1]) +
                static_cast<double>(x[2]) + static_cast<double>(x[3]);
@@ -195,41 +279,37 @@ __global__ void __launch_bounds__(kPullBlock, 8) k_pull(PullArgs a) {
   }
 
   // groups of 32 rows, one warp each: the small rows' in-edges of a group
-  // are contiguous, each tagged with its row
+  // are contiguous, each tagged with its row; a step covers 128 slots from a
+  // multiple of 4 at or below the group's first edge
   for (int gi = gw; gi < a.ngroups; gi += nw) {
     const int k = gi * 32 + lane;
     const int gb = __ldg(a.crp + gi * 32);
     const int ge = __ldg(a.crp + min(gi * 32 + 32, a.n));
     s_row[wid][lane] = MT(0);
     __syncwarp();
-    // kPullSteps steps of 32 edges at a time: their loads in flight together
-    for (int e0 = gb; e0 < ge; e0 += 32 * kPullSteps) {
-      int r[kPullSteps];
-      MT x[kPullSteps];
-      int src[kPullSteps];
+    for (int e0 = (gb & ~3) + 4 * lane; e0 - 4 * lane < ge; e0 += 128 * kPullSteps) {
+      int4 src[kPullSteps];
+      unsigned tag[kPullSteps];
 #pragma unroll
       for (int h = 0; h < kPullSteps; ++h) {
-        const int e = e0 + 32 * h + lane;
-        // the edge streams are read once a round: evict-first in L2, so
-        // they do not push the message array (read at random) out of it
-        src[h] = e < ge ? __ldcs(a.csrc + e) : -1;
-        r[h] = e < ge ? static_cast<int>(__ldcs(a.crow + e)) : 32;   // past the end: a key of its own
+        const int e = e0 + 128 * h;
+        const bool in = e < ge;
+        src[h] = in ? __ldcs(reinterpret_cast<const int4*>(a.csrc + e)) : make_int4(0, 0, 0, 0);
+        tag[h] = in ? __ldcs(reinterpret_cast<const unsigned*>(a.crow + e)) : 0u;
       }
+      MT x[kPullSteps][4];
+      int r[kPullSteps][4];
 #pragma unroll
-      for (int h = 0; h < kPullSteps; ++h) x[h] = src[h] >= 0 ? msg_in[src[h]] : MT(0);
+      for (int h = 0; h < kPullSteps; ++h)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int e = e0 + 128 * h + i;
+          r[h][i] = e < gb ? -1 : (e >= ge ? 32 : static_cast<int>((tag[h] >> (8 * i)) & 0xffu));
+          x[h][i] = (e >= gb && e < ge) ? msg_in[int4_at(src[h], i)] : MT(0);
+        }
 #pragma unroll
       for (int h = 0; h < kPullSteps; ++h) {
-        // segmented suffix sums over runs of equal r (runs are contiguous)
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const MT y = __shfl_down_sync(0xffffffffu, x[h], o);
-          const int ry = __shfl_down_sync(0xffffffffu, r[h], o);
-          if (lane + o < 32 && ry == r[h]) x[h] += y;
-        }
-        // the first lane of each run adds the run's sum to its row (a row
-        // has one run per step: no two lanes add to a row at once)
-        const int rprev = __shfl_up_sync(0xffffffffu, r[h], 1);
-        if (r[h] < 32 && (lane == 0 || rprev != r[h])) s_row[wid][r[h]] += x[h];
+        pull_group_step<MT>(s_row[wid], lane, r[h], x[h]);
         __syncwarp();
       }
     }
@@ -256,7 +336,8 @@ constexpr int kPullScanTile = kPullScanBlock * kPullScanItems;   // rows per til
 
 __device__ __forceinline__ int4 pull_counts(int d) {
   const bool big = d > kPullCut;
-  return make_int4(big ? 0 : d, big ? d : 0, big ? (d + kPullChunk - 1) / kPullChunk : 0, big ? 1 : 0);
+  return make_int4(big ? 0 : d, big ? (d + 3) & ~3 : 0, big ? (d + kPullChunk - 1) / kPullChunk : 0,
+                   big ? 1 : 0);
 }
 __device__ __forceinline__ int4 add4(int4 a, int4 b) {
   return make_int4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
@@ -333,6 +414,7 @@ static __global__ void __launch_bounds__(kPullScanBlock) k_pull_offsets(
   const int4 inc = block_scan4(v, &tot);
   const int4 tile_off = sums[blockIdx.x];
   const int small_total = sums[ntiles].x;
+  const int tail_base = (small_total + 3) & ~3;   // the tail's rows start at multiples of 4
   int4 run = add4(tile_off, make_int4(inc.x - v.x, inc.y - v.y, inc.z - v.z, inc.w - v.w));
   unsigned flags = 0u;
 #pragma unroll
@@ -343,7 +425,7 @@ static __global__ void __launch_bounds__(kPullScanBlock) k_pull_offsets(
     crp[k] = run.x;
     if (c.w) {
       flags |= 1u << i;
-      const int tail = small_total + run.y;
+      const int tail = tail_base + run.y;
       first[k] = tail;
       large_nch[run.w] = c.z;
       for (int q = 0; q < c.z; ++q)
@@ -370,24 +452,71 @@ static __global__ void k_pull_indegree(const int* __restrict__ col, int64_t m, i
     atomicAdd(cnt + __ldg(col + e), 1);
 }
 
-// In-edge placement: csrc[cursor[k]++] = j for every edge j -> k (cursor
-// starts at row k's first slot, in the small-row region or in the tail), and
-// the slot's row within its group.  A warp per sender, its lanes over the
-// sender's out-edges (a sender of high out-degree is not one thread's loop).
+// In-edge placement: csrc[cursor[k]++] = the rank of sender j for every
+// edge j -> k (cursor starts at row k's first slot, in the small-row region
+// or in the tail), and the slot's row within its group.
+// A warp per sender, its lanes over the sender's out-edges (a sender of high
+// out-degree is not one thread's loop).
 static __global__ void k_pull_place(const int* __restrict__ rp, const int* __restrict__ col, int n,
+                                    const int* __restrict__ sbase, const unsigned* __restrict__ smask,
                                     int* __restrict__ cursor, int* __restrict__ csrc,
                                     unsigned char* __restrict__ crow) {
   const int lane = threadIdx.x & 31;
   const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int j = w0; j < n; j += nw) {
-    const int e1 = __ldg(rp + j + 1);
-    for (int e = __ldg(rp + j) + lane; e < e1; e += 32) {
+    const int e0 = __ldg(rp + j), e1 = __ldg(rp + j + 1);
+    if (e1 == e0) continue;
+    const int tag = sender_index(sbase, smask, j);
+    for (int e = e0 + lane; e < e1; e += 32) {
       const int k = __ldg(col + e);
       const int pos = atomicAdd(cursor + k, 1);
-      csrc[pos] = j;
+      csrc[pos] = tag;
       crow[pos] = static_cast<unsigned char>(k & 31);
     }
+  }
+}
+
+// Sender masks and ranks: smask[w] bit r set when row 32 w + r has
+// out-edges; sbase[w] the senders in words before w (an exclusive scan of
+// the masks' popcounts, in the three passes of the offsets above).
+static __global__ void k_send_masks(const int* __restrict__ rp, int n, unsigned* __restrict__ smask) {
+  const int lane = threadIdx.x & 31;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k - lane < n; k += gridDim.x * blockDim.x) {
+    const bool s = k < n && __ldg(rp + k + 1) > __ldg(rp + k);
+    const unsigned b = __ballot_sync(0xffffffffu, s);
+    if (lane == 0) smask[k >> 5] = b;
+  }
+}
+static __global__ void __launch_bounds__(kPullScanBlock) k_send_tile_sums(const unsigned* __restrict__ smask,
+                                                                          int nwords, int4* __restrict__ sums) {
+  const int base = blockIdx.x * kPullScanTile + threadIdx.x * kPullScanItems;
+  int c = 0;
+#pragma unroll
+  for (int i = 0; i < kPullScanItems; ++i)
+    if (base + i < nwords) c += __popc(__ldg(smask + base + i));
+  int4 tot;
+  block_scan4(make_int4(c, 0, 0, 0), &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+static __global__ void __launch_bounds__(kPullScanBlock) k_send_offsets(const unsigned* __restrict__ smask,
+                                                                        int nwords, const int4* __restrict__ sums,
+                                                                        int* __restrict__ sbase) {
+  const int base = blockIdx.x * kPullScanTile + threadIdx.x * kPullScanItems;
+  int c[kPullScanItems];
+  int t = 0;
+#pragma unroll
+  for (int i = 0; i < kPullScanItems; ++i) {
+    c[i] = base + i < nwords ? __popc(__ldg(smask + base + i)) : 0;
+    t += c[i];
+  }
+  int4 tot;
+  const int4 inc = block_scan4(make_int4(t, 0, 0, 0), &tot);
+  int run = sums[blockIdx.x].x + inc.x - t;
+#pragma unroll
+  for (int i = 0; i < kPullScanItems; ++i) {
+    if (base + i < nwords) sbase[base + i] = run;
+    run += c[i];
   }
 }
 

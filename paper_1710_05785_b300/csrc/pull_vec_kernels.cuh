@@ -47,17 +47,19 @@ struct VCtl {
 struct PullVArgs {
   int n;
   const int* __restrict__ crp;
-  const int* __restrict__ csrc;
+  const int* __restrict__ csrc;          // sender rank of every in-edge
+  const int* __restrict__ sbase;         // senders before every word of 32 rows
+  const unsigned* __restrict__ smask;    // the word's senders, one bit per row
   const int4* __restrict__ large;
   const int* __restrict__ large_nch;
   const unsigned* __restrict__ lbits;
   int nlarge;
   double* lacc;                    // [large row][kVQ]: FP64 sums, zero between rounds
   unsigned* lcnt;                  // [large row]: chunks added this round
-  const float* __restrict__ inv_deg;   // 1 / outdeg (0 without out-edges)
+  const float2* __restrict__ inv_deg;  // 1 / outdeg as an FP32 pair hi + lo (0 without out-edges)
   double* v;                       // [n][kVQ]
   float* delta;                    // [n][kVQ]
-  float* msg[2];                   // [n][kVQ] each, alternating by set
+  float* msg[2];                   // [sender rank][kVQ] each, alternating by set
   VCtl* ctl;
 };
 
@@ -84,10 +86,13 @@ static __global__ void k_vec_seed(PullVArgs a, const int2* __restrict__ seeds,
 }
 
 // The two messages d_q / outdeg(k) x Delta of a lane: t = Delta / outdeg
-// (one rounding), then t x (dq + dq_lo) with one more.
-__device__ __forceinline__ float2 vec_message(float s0, float s1, float inv_deg, float2 dq,
+// (Delta x (hi + lo) in one fused rounding), then t x (dq + dq_lo) with one
+// more.  Both constants enter as FP32 pairs: a coefficient rounded once to
+// FP32 would scale every message of the vertex by the same error, a bias the
+// PageRank sum amplifies by up to d / (1 - d).
+__device__ __forceinline__ float2 vec_message(float s0, float s1, float2 inv_deg, float2 dq,
                                               float2 dl) {
-  const float t0 = s0 * inv_deg, t1 = s1 * inv_deg;
+  const float t0 = fmaf(s0, inv_deg.x, s0 * inv_deg.y), t1 = fmaf(s1, inv_deg.x, s1 * inv_deg.y);
   return make_float2(fmaf(t0, dq.x, t0 * dl.x), fmaf(t1, dq.y, t1 * dl.y));
 }
 
@@ -121,8 +126,11 @@ static __global__ void __launch_bounds__(kVBlock) k_vec_prime(PullVArgs a) {
   for (int k = w0; k < a.n; k += nw) {
     const int64_t o = static_cast<int64_t>(k) * kVQ + 2 * lane;
     const float2 d = *reinterpret_cast<const float2*>(a.delta + o);
-    const float c = __ldg(a.inv_deg + k);
-    *reinterpret_cast<float2*>(msg + o) = vec_message(d.x, d.y, c, dq, dl);
+    const float2 c = __ldg(a.inv_deg + k);
+    if (c.x != 0.0f) {   // a sender: its message slot is its rank
+      const int64_t om = static_cast<int64_t>(sender_index(a.sbase, a.smask, k)) * kVQ + 2 * lane;
+      *reinterpret_cast<float2*>(msg + om) = vec_message(d.x, d.y, c, dq, dl);
+    }
     r0 += fabs(static_cast<double>(d.x));
     r1 += fabs(static_cast<double>(d.y));
   }
@@ -166,7 +174,7 @@ static __global__ void k_vec_decide(VCtl* ctl, cudaGraphConditionalHandle cond, 
 // One round for the group: the large rows' chunks, a warp each (FP64
 // accumulation per row, the last chunk folds), then the other rows, a warp
 // per row.
-static __global__ void __launch_bounds__(kVBlock) k_vec_pull(PullVArgs a) {
+static __global__ void __launch_bounds__(kVBlock, 4) k_vec_pull(PullVArgs a) {
   cudaGridDependencySynchronize();
   cudaTriggerProgrammaticLaunchCompletion();
   VCtl* ctl = a.ctl;
@@ -189,8 +197,11 @@ static __global__ void __launch_bounds__(kVBlock) k_vec_pull(PullVArgs a) {
     vv.y += static_cast<double>(dold.y);
     *reinterpret_cast<double2*>(a.v + o) = vv;
     *reinterpret_cast<float2*>(a.delta + o) = make_float2(s0, s1);
-    const float c = __ldg(a.inv_deg + k);
-    *reinterpret_cast<float2*>(msg_out + o) = vec_message(s0, s1, c, dq, dl);
+    const float2 c = __ldg(a.inv_deg + k);
+    if (c.x != 0.0f) {
+      const int64_t om = static_cast<int64_t>(sender_index(a.sbase, a.smask, k)) * kVQ + 2 * lane;
+      *reinterpret_cast<float2*>(msg_out + om) = vec_message(s0, s1, c, dq, dl);
+    }
     r0 += fabs(static_cast<double>(s0));
     r1 += fabs(static_cast<double>(s1));
   };
@@ -264,11 +275,14 @@ static __global__ void __launch_bounds__(kVBlock) k_vec_pull(PullVArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->push_set = ws;
 }
 
-// 1 / outdeg of every vertex as FP32 (0 without out-edges).
-static __global__ void k_vec_inv_deg(const int* __restrict__ rp, int n, float* __restrict__ out) {
+// 1 / outdeg of every vertex as an FP32 pair: hi = 1 / outdeg rounded, lo =
+// the remainder rounded (0, 0 without out-edges).
+static __global__ void k_vec_inv_deg(const int* __restrict__ rp, int n, float2* __restrict__ out) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int d = __ldg(rp + k + 1) - __ldg(rp + k);
-    out[k] = d > 0 ? static_cast<float>(1.0 / static_cast<double>(d)) : 0.0f;
+    const double x = d > 0 ? 1.0 / static_cast<double>(d) : 0.0;
+    const float hi = static_cast<float>(x);
+    out[k] = make_float2(hi, static_cast<float>(x - static_cast<double>(hi)));
   }
 }
 

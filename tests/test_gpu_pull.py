@@ -41,7 +41,9 @@ def reversed_star(leaves, into=0):
     return graphgen.small_graph(leaves + 1, edges)
 
 
-@pytest.mark.parametrize("scale,ef", [(6, 4), (10, 8), (13, 8), (16, 16)])
+# scale 17: 131,072 receivers (4,096 groups), message slots for about half
+# of them (the senders)
+@pytest.mark.parametrize("scale,ef", [(6, 4), (10, 8), (13, 8), (16, 16), (17, 16)])
 @pytest.mark.parametrize("opname", ["OP_SUM_F64", "OP_SUM_MIXED"])
 def test_pull_pagerank_matches_oracle(mt, scale, ef, opname):
     g = graphgen.rmat(scale, ef)
@@ -80,6 +82,19 @@ def test_pull_rows_at_and_past_the_cut(mt, leaves):
         want_c = (1 - D) + leaves * D * (1 - D)
         assert abs(v[0] - want_c) <= 1e-6 * want_c, (leaves, op, v[0], want_c)
         np.testing.assert_allclose(v[1:], 1 - D, rtol=1e-7)
+
+
+@pytest.mark.parametrize("leaves", [1, 300, 200000])
+def test_pull_star_of_one_sender(mt, leaves):
+    # the centre, the only sender (message slot 0), sends to every leaf; closed form:
+    # v_centre = 1 - d, v_leaf = (1 - d) + d (1 - d) / L
+    edges = np.stack([np.zeros(leaves, dtype=np.int64), np.arange(1, leaves + 1)], axis=1)
+    g = graphgen.small_graph(leaves + 1, edges)
+    G = mt.Graph.from_csr(g)
+    for op in (mt.OP_SUM_F64, mt.OP_SUM_MIXED):
+        v = pull(mt, G, op, damping=D, eps=1e-12).state()
+        assert abs(v[0] - (1 - D)) <= 1e-12
+        np.testing.assert_allclose(v[1:], (1 - D) + D * (1 - D) / leaves, rtol=1e-7)
 
 
 def test_pull_hubs_inside_a_random_graph(mt):
