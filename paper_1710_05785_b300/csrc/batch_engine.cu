@@ -194,9 +194,9 @@ static maiter_status vec_setup(maiter_batch* b, const maiter_query* qs) {
   }
   for (VGroup& G : b->vg) {
     const maiter_graph* g = b->graphs[G.graph];
-    maiter_status s = ensure_pull(g, nullptr);
+    maiter_status s = ensure_pull(g, nullptr, true);
     if (s != MAITER_OK) return s;
-    const PullLayout* L = g->pull;
+    const PullLayout* L = g->pullv;
     const size_t nv = static_cast<size_t>(std::max<int64_t>(g->n, 1)) * kVQ;
     PullVArgs& a = G.a;
     a.n = static_cast<int>(g->n);

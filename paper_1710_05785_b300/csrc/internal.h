@@ -67,6 +67,7 @@ struct BinLayout;   // binned engine: the edges by (sender cell, receiver bin)
 // high in-degree (pull_engine.cu builds it; the batch engine reads it too).
 struct PullLayout {
   bool valid = false;
+  int cut = 0, chunk = 0;  // largest row of a group; in-edges per chunk of a larger row
   int nlarge = 0;          // chunk entries
   int nlrows = 0;          // rows cut into chunks
   int* crp = nullptr;      // n + 1: offsets of the small rows' in-edges
@@ -100,7 +101,8 @@ struct maiter_graph {
   bool invalid = false;        // the last update failed validation: no runs
   int num_sms = 0;
   maiter::BinLayout* bins = nullptr;   // binned engine layout (built on first use)
-  maiter::PullLayout* pull = nullptr;  // receive-side engine layout (built on first use)
+  maiter::PullLayout* pull = nullptr;  // receive-side layout of the scalar round (built on first use)
+  maiter::PullLayout* pullv = nullptr; // receive-side layout of the 64-query vector round
 };
 
 struct maiter_result {
@@ -163,6 +165,7 @@ maiter_status run_pull(const maiter_graph* g, const maiter_run_params* p, maiter
                        cudaStream_t st);
 void free_pull(maiter_graph* g);
 void invalidate_pull(maiter_graph* g);
-// Builds (or rebuilds after an update) the transpose of g on stream st.
-maiter_status ensure_pull(const maiter_graph* g, cudaStream_t st);
+// Builds (or rebuilds after an update) the transpose of g on stream st: the
+// scalar round's layout (g->pull), or the vector round's (g->pullv, vec).
+maiter_status ensure_pull(const maiter_graph* g, cudaStream_t st, bool vec = false);
 }  // namespace maiter

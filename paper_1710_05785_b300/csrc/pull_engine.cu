@@ -13,9 +13,10 @@
 
 namespace maiter {
 
-void free_pull(maiter_graph* g) {
-  if (!g->pull) return;
-  PullLayout* L = g->pull;
+namespace {
+
+void free_layout(PullLayout* L) {
+  if (!L) return;
   cudaFree(L->crp);
   cudaFree(L->csrc);
   cudaFree(L->crow);
@@ -27,11 +28,20 @@ void free_pull(maiter_graph* g) {
   cudaFree(L->sbase);
   cudaFree(L->smask);
   delete L;
+}
+
+}  // namespace
+
+void free_pull(maiter_graph* g) {
+  free_layout(g->pull);
+  free_layout(g->pullv);
   g->pull = nullptr;
+  g->pullv = nullptr;
 }
 
 void invalidate_pull(maiter_graph* g) {
   if (g->pull) g->pull->valid = false;
+  if (g->pullv) g->pullv->valid = false;
 }
 
 namespace {
@@ -82,11 +92,14 @@ cudaError_t sender_ranks(const maiter_graph* g, PullLayout* L, cudaStream_t st) 
 // offsets, tail offsets, chunk entries, large-row index) whose total is the
 // one value read back (to size the chunk list), then the senders placed by
 // one atomic cursor per receiver.
-maiter_status ensure_pull(const maiter_graph* cg, cudaStream_t st) {
+maiter_status ensure_pull(const maiter_graph* cg, cudaStream_t st, bool vec) {
   maiter_graph* g = const_cast<maiter_graph*>(cg);
-  if (g->pull && g->pull->valid) return MAITER_OK;
-  if (!g->pull) g->pull = new PullLayout();
-  PullLayout* L = g->pull;
+  PullLayout*& slot = vec ? g->pullv : g->pull;
+  if (slot && slot->valid) return MAITER_OK;
+  if (!slot) slot = new PullLayout();
+  PullLayout* L = slot;
+  L->cut = vec ? kVecCut : kPullCut;
+  L->chunk = vec ? kVecChunk : kPullChunk;
   const int64_t n = g->n, m = g->m;
   const int64_t nwords = (n + 31) / 32;
   const int ntiles = static_cast<int>((n + kPullScanTile - 1) / kPullScanTile);
@@ -106,7 +119,8 @@ maiter_status ensure_pull(const maiter_graph* cg, cudaStream_t st) {
   }
   int4 totals = make_int4(0, 0, 0, 0);   // small edges, tail edges, chunks, large rows
   if (e == cudaSuccess && n > 0) {
-    k_pull_tile_sums<<<ntiles, kPullScanBlock, 0, st>>>(indeg, static_cast<int>(n), sums);
+    k_pull_tile_sums<<<ntiles, kPullScanBlock, 0, st>>>(indeg, static_cast<int>(n), L->cut, L->chunk,
+                                                         sums);
     k_pull_scan_sums<<<1, kPullScanBlock, 0, st>>>(sums, ntiles);
     e = cudaGetLastError();
     if (e == cudaSuccess)
@@ -140,7 +154,8 @@ maiter_status ensure_pull(const maiter_graph* cg, cudaStream_t st) {
   }
   if (e == cudaSuccess) e = sender_ranks(g, L, st);
   if (e == cudaSuccess && n > 0) {
-    k_pull_offsets<<<ntiles, kPullScanBlock, 0, st>>>(indeg, static_cast<int>(n), sums, ntiles,
+    k_pull_offsets<<<ntiles, kPullScanBlock, 0, st>>>(indeg, static_cast<int>(n), L->cut, L->chunk,
+                                                       sums, ntiles,
                                                        L->crp, first, L->lbits, L->large,
                                                        L->large_nch);
     k_pull_place<<<g->num_sms * 8, 256, 0, st>>>(g->rp, g->col, static_cast<int>(n), L->sbase,

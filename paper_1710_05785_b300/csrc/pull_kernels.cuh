@@ -16,9 +16,9 @@
 //     step (one 16-byte load of senders, one 4-byte load of rows), sums the
 //     runs of equal rows among them in registers, and one segmented shuffle
 //     scan over the lanes joins the runs that cross lanes; rows with more
-//     than kPullCut in-edges keep their edges in a tail region after all the
+//     than the layout's cut in-edges keep their edges in a tail region after all the
 //     others (each row's part starting at a multiple of 4 slots) and are
-//   cut into chunks of kPullChunk edges, one warp each: the warp's sum goes
+//   cut into chunks of the layout's chunk size, one warp each: the warp's sum goes
 //     to an FP64 accumulator of the row by one atomic, and the warp that adds
 //     the row's last chunk folds the row;
 //   message slots: a round's messages are stored by sender rank (the
@@ -46,8 +46,16 @@ constexpr int kPullBlock = 256;
 // FP32 messages, 64 for FP64 ones)
 template <class MT>
 constexpr int pull_min_blocks() { return sizeof(MT) == 4 ? 6 : 4; }
-constexpr int kPullCut = 256;       // in-edges of the largest row a group sums
-constexpr int kPullChunk = 1024;    // in-edges per chunk of a larger row
+// A layout's cut (in-edges of the largest row a group sums) and chunk (in-edges
+// per chunk of a larger row) are parameters of its build: the scalar round
+// (k_pull) sums rows of up to 2048 in-edges in groups and splits larger
+// ones into 4096-edge chunks; the 64-query vector round (k_vec_pull, a warp
+// per row) takes rows past 256 in-edges in 1024-edge chunks, spread over
+// many warps.
+constexpr int kPullCut = 2048;
+constexpr int kPullChunk = 4096;
+constexpr int kVecCut = 256;
+constexpr int kVecChunk = 1024;
 constexpr int kPullSteps = 2;       // 128-edge steps of a group whose loads are issued together
 constexpr int kPullLargeSteps = 2;  // 128-edge steps of a chunk whose loads are issued together
 
@@ -334,9 +342,9 @@ constexpr int kPullScanBlock = 256;
 constexpr int kPullScanItems = 8;
 constexpr int kPullScanTile = kPullScanBlock * kPullScanItems;   // rows per tile
 
-__device__ __forceinline__ int4 pull_counts(int d) {
-  const bool big = d > kPullCut;
-  return make_int4(big ? 0 : d, big ? (d + 3) & ~3 : 0, big ? (d + kPullChunk - 1) / kPullChunk : 0,
+__device__ __forceinline__ int4 pull_counts(int d, int cut, int chunk) {
+  const bool big = d > cut;
+  return make_int4(big ? 0 : d, big ? (d + 3) & ~3 : 0, big ? (d + chunk - 1) / chunk : 0,
                    big ? 1 : 0);
 }
 __device__ __forceinline__ int4 add4(int4 a, int4 b) {
@@ -369,12 +377,13 @@ __device__ __forceinline__ int4 block_scan4(int4 v, int4* total) {
 
 // Pass 1: every tile's total.
 static __global__ void __launch_bounds__(kPullScanBlock) k_pull_tile_sums(const int* __restrict__ indeg,
-                                                                          int n, int4* __restrict__ sums) {
+                                                                          int n, int cut, int chunk,
+                                                                          int4* __restrict__ sums) {
   const int base = blockIdx.x * kPullScanTile + threadIdx.x * kPullScanItems;
   int4 v = make_int4(0, 0, 0, 0);
 #pragma unroll
   for (int i = 0; i < kPullScanItems; ++i)
-    if (base + i < n) v = add4(v, pull_counts(__ldg(indeg + base + i)));
+    if (base + i < n) v = add4(v, pull_counts(__ldg(indeg + base + i), cut, chunk));
   int4 tot;
   block_scan4(v, &tot);
   if (threadIdx.x == 0) sums[blockIdx.x] = tot;
@@ -399,7 +408,7 @@ static __global__ void __launch_bounds__(kPullScanBlock) k_pull_scan_sums(int4* 
 // first slot of every row (its crp, or its tail offset after all small-row
 // edges), the large-row flags and, for every large row, its chunk entries.
 static __global__ void __launch_bounds__(kPullScanBlock) k_pull_offsets(
-    const int* __restrict__ indeg, int n, const int4* __restrict__ sums, int ntiles,
+    const int* __restrict__ indeg, int n, int cut, int chunk, const int4* __restrict__ sums, int ntiles,
     int* __restrict__ crp, int* __restrict__ first, unsigned* __restrict__ lbits,
     int4* __restrict__ large, int* __restrict__ large_nch) {
   const int base = blockIdx.x * kPullScanTile + threadIdx.x * kPullScanItems;
@@ -408,7 +417,7 @@ static __global__ void __launch_bounds__(kPullScanBlock) k_pull_offsets(
 #pragma unroll
   for (int i = 0; i < kPullScanItems; ++i) {
     d[i] = base + i < n ? __ldg(indeg + base + i) : 0;
-    v = add4(v, pull_counts(d[i]));
+    v = add4(v, pull_counts(d[i], cut, chunk));
   }
   int4 tot;
   const int4 inc = block_scan4(v, &tot);
@@ -421,7 +430,7 @@ static __global__ void __launch_bounds__(kPullScanBlock) k_pull_offsets(
   for (int i = 0; i < kPullScanItems; ++i) {
     const int k = base + i;
     if (k >= n) break;
-    const int4 c = pull_counts(d[i]);
+    const int4 c = pull_counts(d[i], cut, chunk);
     crp[k] = run.x;
     if (c.w) {
       flags |= 1u << i;
@@ -429,7 +438,7 @@ static __global__ void __launch_bounds__(kPullScanBlock) k_pull_offsets(
       first[k] = tail;
       large_nch[run.w] = c.z;
       for (int q = 0; q < c.z; ++q)
-        large[run.z + q] = make_int4(k, tail + q * kPullChunk, tail + min(d[i], (q + 1) * kPullChunk), run.w);
+        large[run.z + q] = make_int4(k, tail + q * chunk, tail + min(d[i], (q + 1) * chunk), run.w);
     } else {
       first[k] = run.x;
     }

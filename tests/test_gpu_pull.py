@@ -2,8 +2,8 @@
 messages are summed at the receivers over the transpose.  Every run is
 checked against the oracle's fixed point (Theorem 1: any schedule, the
 synchronous one included, reaches the fixed point of Eq. 1), at sizes around
-the 32-row groups, with rows at and past the 256-in-edge cut and over several
-1024-edge chunks, with caller-given coefficients and start vectors, after a
+the 32-row groups, with rows at and past the 2048-in-edge cut and over several
+4096-edge chunks, with caller-given coefficients and start vectors, after a
 round cap (the state left must be a valid DAIC state and resume to the same
 answer), after a graph update, and in profiling mode.
 
@@ -71,7 +71,9 @@ def test_pull_graph_without_edges(mt):
     assert r.stats()["converged"] == 1
 
 
-@pytest.mark.parametrize("leaves", [256, 257, 1024, 1025, 200000])
+# a group holds rows of up to 2048 in-edges; a larger row is cut into chunks
+# of 4096: at and past the cut, one chunk and a ragged second, many chunks
+@pytest.mark.parametrize("leaves", [256, 2048, 2049, 4096, 4097, 200000])
 def test_pull_rows_at_and_past_the_cut(mt, leaves):
     # centre of in-degree L (leaves of out-degree 1): v_leaf = 1 - d,
     # v_centre = (1 - d) + L d (1 - d) (closed form)
@@ -98,11 +100,12 @@ def test_pull_star_of_one_sender(mt, leaves):
 
 
 def test_pull_hubs_inside_a_random_graph(mt):
-    # extra in-edges at two receivers (one over several chunks) of a random graph
+    # extra in-edges at three receivers of a random graph: one over several
+    # chunks, one of a single chunk, one summed inside its group
     base = graphgen.random_graph(60000, 240000, seed=5)
     rng = np.random.default_rng(6)
     src = np.repeat(np.arange(base.n, dtype=np.int64), np.diff(base.row_ptr))
-    extra_dst = np.concatenate([np.full(150000, 8200), np.full(700, 30001)])
+    extra_dst = np.concatenate([np.full(150000, 8200), np.full(3000, 12345), np.full(700, 30001)])
     extra_src = rng.integers(0, base.n, extra_dst.size)
     g2 = graphgen.csr_from_edges(base.n, np.concatenate([src, extra_src]),
                                  np.concatenate([base.col, extra_dst]))
