@@ -82,8 +82,15 @@ struct PullLayout {
   int nsend = 0;
   int* sbase = nullptr;            // ceil(n / 32): senders before every word of 32 rows
   unsigned* smask = nullptr;       // ceil(n / 32): the word's senders, one bit per row
+  // the build's work arrays, kept between builds: a rebuild after an update
+  // allocates and frees nothing (cudaFree would wait for the whole device,
+  // including another stream's upload)
+  int* t_indeg = nullptr;
+  int* t_first = nullptr;
+  int4* t_sums = nullptr;
   size_t crp_cap = 0, csrc_cap = 0, crow_cap = 0, lbits_cap = 0, large_cap = 0, lrow_cap = 0,
-         sbase_cap = 0, smask_cap = 0;
+         sbase_cap = 0, smask_cap = 0, lacc_cap = 0, lcnt_cap = 0, t_indeg_cap = 0, t_first_cap = 0,
+         t_sums_cap = 0;
 };
 }
 

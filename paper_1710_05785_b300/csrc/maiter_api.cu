@@ -226,9 +226,12 @@ maiter_status maiter_graph_update(maiter_graph* g, const int64_t* row_ptr, const
   unsigned h_flag = 0;
   MAITER_CUDA(cudaMemcpyAsync(&h_flag, g->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   MAITER_CUDA(cudaStreamSynchronize(st));
-  // contents changed: derived data is recomputed on its next use
-  cudaFree(g->lstat);
-  g->lstat = nullptr;
+  // contents changed: derived data is recomputed on its next use (a free
+  // only when there is something to free: cudaFree waits for the device)
+  if (g->lstat) {
+    cudaFree(g->lstat);
+    g->lstat = nullptr;
+  }
   g->wf32 = 0;
   invalidate_bins(g);
   invalidate_pull(g);

@@ -27,6 +27,9 @@ void free_layout(PullLayout* L) {
   cudaFree(L->lcnt);
   cudaFree(L->sbase);
   cudaFree(L->smask);
+  cudaFree(L->t_indeg);
+  cudaFree(L->t_first);
+  cudaFree(L->t_sums);
   delete L;
 }
 
@@ -68,8 +71,8 @@ cudaError_t sender_ranks(const maiter_graph* g, PullLayout* L, cudaStream_t st) 
   cudaError_t e = grow(&L->sbase, &L->sbase_cap, static_cast<size_t>(nwords));
   if (e == cudaSuccess) e = grow(&L->smask, &L->smask_cap, static_cast<size_t>(nwords));
   if (e != cudaSuccess || n == 0) return e;
-  int4* sums = nullptr;
-  e = cudaMalloc(&sums, sizeof(int4) * (ntiles + 1));
+  e = grow(&L->t_sums, &L->t_sums_cap, static_cast<size_t>(ntiles) + 1);
+  int4* sums = L->t_sums;
   int4 tot = make_int4(0, 0, 0, 0);
   if (e == cudaSuccess) {
     k_send_masks<<<g->num_sms * 4, 256, 0, st>>>(g->rp, static_cast<int>(n), L->smask);
@@ -81,7 +84,6 @@ cudaError_t sender_ranks(const maiter_graph* g, PullLayout* L, cudaStream_t st) 
   if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, sums + ntiles, sizeof(int4), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) L->nsend = tot.x;
-  cudaFree(sums);
   return e;
 }
 
@@ -106,12 +108,12 @@ maiter_status ensure_pull(const maiter_graph* cg, cudaStream_t st, bool vec) {
   MAITER_CUDA(grow(&L->crp, &L->crp_cap, static_cast<size_t>(n + 1)));
   MAITER_CUDA(grow(&L->lbits, &L->lbits_cap, static_cast<size_t>(nwords)));
   const size_t n1 = static_cast<size_t>(std::max<int64_t>(n, 1));
-  int* indeg = nullptr;
-  int* first = nullptr;
-  int4* sums = nullptr;
-  cudaError_t e = cudaMalloc(&indeg, sizeof(int) * n1);
-  if (e == cudaSuccess) e = cudaMalloc(&first, sizeof(int) * n1);
-  if (e == cudaSuccess) e = cudaMalloc(&sums, sizeof(int4) * (ntiles + 1));
+  cudaError_t e = grow(&L->t_indeg, &L->t_indeg_cap, n1);
+  if (e == cudaSuccess) e = grow(&L->t_first, &L->t_first_cap, n1);
+  if (e == cudaSuccess) e = grow(&L->t_sums, &L->t_sums_cap, static_cast<size_t>(ntiles) + 1);
+  int* indeg = L->t_indeg;
+  int* first = L->t_first;
+  int4* sums = L->t_sums;
   if (e == cudaSuccess) e = cudaMemsetAsync(indeg, 0, sizeof(int) * n1, st);
   if (e == cudaSuccess && m > 0) {
     k_pull_indegree<<<g->num_sms * 4, 256, 0, st>>>(g->col, m, indeg);
@@ -142,30 +144,28 @@ maiter_status ensure_pull(const maiter_graph* cg, cudaStream_t st, bool vec) {
   if (e == cudaSuccess) e = grow(&L->large_nch, &L->lrow_cap, static_cast<size_t>(totals.w));
   if (e == cudaSuccess) {
     // lacc / lcnt: one entry per large row, zero between rounds
-    cudaFree(L->lacc);
-    cudaFree(L->lcnt);
-    L->lacc = nullptr;
-    L->lcnt = nullptr;
     const size_t nl = static_cast<size_t>(std::max(totals.w, 1));
-    e = cudaMalloc(&L->lacc, sizeof(double) * nl);
-    if (e == cudaSuccess) e = cudaMalloc(&L->lcnt, sizeof(unsigned) * nl);
+    e = grow(&L->lacc, &L->lacc_cap, nl);
+    if (e == cudaSuccess) e = grow(&L->lcnt, &L->lcnt_cap, nl);
     if (e == cudaSuccess) e = cudaMemsetAsync(L->lacc, 0, sizeof(double) * nl, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(L->lcnt, 0, sizeof(unsigned) * nl, st);
   }
-  if (e == cudaSuccess) e = sender_ranks(g, L, st);
   if (e == cudaSuccess && n > 0) {
     k_pull_offsets<<<ntiles, kPullScanBlock, 0, st>>>(indeg, static_cast<int>(n), L->cut, L->chunk,
                                                        sums, ntiles,
                                                        L->crp, first, L->lbits, L->large,
                                                        L->large_nch);
+    e = cudaGetLastError();
+  }
+  // the sender ranks reuse the scan's work array (in stream order, after the
+  // offsets pass has read it)
+  if (e == cudaSuccess) e = sender_ranks(g, L, st);
+  if (e == cudaSuccess && n > 0) {
     k_pull_place<<<g->num_sms * 8, 256, 0, st>>>(g->rp, g->col, static_cast<int>(n), L->sbase,
                                                  L->smask, first, L->csrc, L->crow);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(indeg);
-  cudaFree(first);
-  cudaFree(sums);
   MAITER_CUDA(e);
   L->valid = true;
   return MAITER_OK;
