@@ -268,6 +268,16 @@ def sssp_config(g, world):
             "parallelism": f"independent sources x{world}"}
 
 
+def load_traffic():
+    """profiles/traffic.json: DRAM bytes (read + write) per launch of the
+    captured kernels, by capture name ({} when the file is absent)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 PR_WORKLOADS = {
     # FP64 PageRank on R-MAT scale 13, to sum |Delta| < 1e-8
     "pagerank-rmat13": dict(scale=13, ef=8, op="f64", eps=1e-8),
@@ -477,12 +487,7 @@ def run_pagerank(args, wl, dist=None, nested=None):
     bound = results[head]["error_bound"]
     # kernel-level roofline: the headline run again with per-kernel events
     peaks, peak_kind = measured_peaks()
-    traffic_tab = {}
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic_tab = json.load(f)
-    except (OSError, ValueError):
-        pass
+    traffic_tab = load_traffic()
 
     def kernel_roofline(kw, kernel, kind, what, traffic_key, note):
         pf = mt.run(G, eps=eps, damping=D_PR, stream=stream.cuda_stream,
@@ -707,6 +712,12 @@ def run_batch_bench(args):
     assert all(c == 64 for c in nppr), nppr
     alg = 260.0 * prof["edge_pushes"] / 64 + 1800.0 * prof["activations"] / 64
     achieved = alg / (prof["push_ms"] * 1e-3) / 1e9
+    # DRAM traffic per launch from the scale-22 capture, scaled by in-edges
+    # (every graph of the workload has m = 16 n, so traffic grows with m)
+    vec_cap = load_traffic().get("k_vec_pull_ppr64_rmat22")
+    vec_traffic = None
+    if vec_cap and prof["push_launches"]:
+        vec_traffic = vec_cap / float(1 << 26) * (prof["edge_pushes"] / 64) / prof["push_launches"]
     qr = out[head]["qrounds"]
     line = {
         "metric": METRIC, "value": edges / (ms * 1e-3) / 1e9, "unit": "GTEPS",
@@ -732,12 +743,13 @@ def run_batch_bench(args):
         "roofline": {"bound": "hbm", "kernel": "k_vec_pull (a warp per row, 64-query vectors)",
                      "achieved": achieved,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                     "traffic": None, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "traffic": vec_traffic, "peak_kind": f"{peak_kind} copy bandwidth",
                      "push_launches": prof["push_launches"],
                      "push_ms_per_launch": prof["push_ms"] / max(prof["push_launches"], 1),
                      "note": "achieved = the group pull's algorithmic bytes (260 B per in-edge, "
                              "1800 B per vertex and round) / device time of its launches; the "
-                             "SSSP branches are not in it"},
+                             "SSSP branches are not in it; traffic = the scale-22 capture's DRAM "
+                             "bytes per in-edge x this workload's in-edges per launch"},
         "gpu_launches": int(st["kernel_launches"]) * args.steps,
         "checked": "2 SSSP (exact) and 4 PPR queries per graph from the last timed batch: "
                    "PPR bounded through a round-engine FP64 run to eps_q / 100 and its residual "
@@ -1370,12 +1382,7 @@ def run_sssp(args, dist, emit=True):
                     for p in prof)
     peaks, peak_kind = measured_peaks()
     achieved = alg_bytes / (push_ms * 1e-3) / 1e9
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get("k_push_sssp_rmat20")
-    except (OSError, ValueError):
-        pass
+    traffic = load_traffic().get("k_push_sssp_rmat20")
 
     # the other schedules and the asynchronous engine on the same 8 sources
     # (one warm pass, then the best of two timed passes)
