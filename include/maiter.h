@@ -155,10 +155,11 @@ typedef enum {
                                  sums the messages c_j Delta_j of its in-neighbours
                                  over the transpose of the graph (built by the
                                  library on first use and after maiter_graph_update:
-                                 4 bytes per edge + 4 per vertex), then folds.  No
-                                 atomic per edge; one per 1024 in-edges of a vertex
-                                 with more than 256.  Memory per result: two n x 8
-                                 byte message buffers.  The loop and its termination
+                                 about 5 bytes per edge + 12 per vertex; messages
+                                 are stored by sender rank), then folds.  No atomic
+                                 per edge; one per 4096 in-edges of a vertex with
+                                 more than 2048.  Memory per result: two n x 8 byte
+                                 message buffers.  The loop and its termination
                                  test run on the device as for SYNC. */
 } maiter_engine;
 
