@@ -1294,7 +1294,11 @@ def main():
             nested = None
             if args.workload == "pagerank-mixed-rmat24" and not args.no_sssp and not args.scale:
                 def nested(d):
-                    return {"sssp_rmat20_8src": run_sssp(args, d, emit=False)}
+                    # its own step count: 10 steps of ~4.4 ms would end inside one
+                    # period of the clock sampler
+                    sub = argparse.Namespace(**vars(args))
+                    sub.steps = max(args.steps, SHORT_STEPS["sssp-rmat20"])
+                    return {"sssp_rmat20_8src": run_sssp(sub, d, emit=False)}
             run_pagerank(args, args.workload, dist, nested)
         elif args.workload == "batch":
             run_batch_bench(args)
