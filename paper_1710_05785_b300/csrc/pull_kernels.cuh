@@ -4,9 +4,9 @@
 // receive step of Eq. 5, Delta_k <- Delta_k + sum of the messages that
 // reached k, is computed at the receiver: k reads the messages c_j Delta_j
 // of its in-neighbours j through the transpose of the graph and sums them in
-// registers.  No edge needs an atomic; per edge the round reads one source
-// index (streamed) and one message (a random read of an n-entry array that
-// stays in L2 for FP32 messages up to 2^25 vertices).
+// registers.  No edge needs an atomic; per edge the round reads one sender
+// rank (streamed) and one message (a random read of an array with one entry
+// per sender, which stays in L2).
 //
 // Static layout (pull_engine.cu, once per graph content):
 //   crp, csrc - the transpose in CSR form: the senders of every receiver;
@@ -15,12 +15,12 @@
 //     within the group (one byte); every lane takes 4 consecutive edges per
 //     step (one 16-byte load of senders, one 4-byte load of rows), sums the
 //     runs of equal rows among them in registers, and one segmented shuffle
-//     scan over the lanes joins the runs that cross lanes; rows with more
-//     than the layout's cut in-edges keep their edges in a tail region after all the
-//     others (each row's part starting at a multiple of 4 slots) and are
-//   cut into chunks of the layout's chunk size, one warp each: the warp's sum goes
-//     to an FP64 accumulator of the row by one atomic, and the warp that adds
-//     the row's last chunk folds the row;
+//     scan over the lanes joins the runs that cross lanes;
+//   rows with more in-edges than the layout's cut keep their edges in a tail
+//     region after all the others (each row's part starting at a multiple of
+//     4 slots) and are cut into chunks of the layout's chunk size, one warp
+//     each: the warp's sum goes to an FP64 accumulator of the row by one
+//     atomic, and the warp that adds the row's last chunk folds the row;
 //   message slots: a round's messages are stored by sender rank (the
 //     vertices of out-degree > 0 in id order; in R-MAT graphs about half of
 //     all vertices), so that the two message arrays of a round, the one read
