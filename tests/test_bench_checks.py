@@ -41,3 +41,20 @@ def test_residual_bound_is_small_at_the_fixed_point_only():
     bad = v.copy()
     bad[int(np.argmax(v))] *= 1 + 1e-5
     assert bench.linear_residual_bound(g, bad, c, D) > 1e-6
+
+
+def test_traffic_table_holds_every_capture_the_bench_lines_read():
+    # the lines' roofline.traffic comes from these captures; a missing or
+    # renamed key would turn it into null without an error
+    tab = bench.load_traffic()
+    for key in ("k_pull_pagerank_f32_rmat24", "k_push_pagerank_mixed_rmat24",
+                "k_push_sssp_rmat20", "k_vec_pull_ppr64_rmat22"):
+        assert isinstance(tab.get(key), int) and tab[key] > 0, key
+
+
+def test_millisecond_workloads_default_to_regions_the_clock_sampler_sees():
+    # every short workload has its own default step count, long enough for
+    # several 50 ms sampler periods at its per-step time
+    names = set(bench.PR_WORKLOADS) | set(bench.ROW_WORKLOADS) | {"sssp-rmat20"}
+    assert set(bench.SHORT_STEPS) <= names
+    assert all(steps >= 60 for steps in bench.SHORT_STEPS.values())
